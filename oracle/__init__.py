@@ -1,0 +1,17 @@
+"""FP64 CPU oracle for the PSTD quantum-scattering hot path (arXiv 2403.04053).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg (and its ``--impl reference`` arm) may import,
+call or execute anything in this package.  The product path (the CUDA library and
+its Python binding) never does, and this package imports nothing from it: the two
+share no code.  Inputs come from ``paper_2403_04053_gb300.inputs`` (seeded
+generators only) and are passed in as arrays.
+
+Modules
+  pstd_oracle : tables, the leapfrog PSTD update (both TF/SF forms), the running
+                single-frequency DFT on the six virtual planes
+  ntdf_oracle : the near-to-distant-field transform as the literal per-cell mode
+                sum of Eqs. bottomPsi_lm ... Psi, and its far-field limit
+  analytic    : textbook closed forms that pin the oracle (partial waves, Born,
+                spherical wave, leapfrog mode evolution)
+"""

@@ -1,0 +1,324 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+This module holds workload definitions only (grid geometry, potentials, incident
+directions, observation points).  It contains none of the PSTD method's
+arithmetic and imports nothing from the CUDA binding or from ``oracle/``, so both
+sides of a parity test can take their inputs from here.
+
+Units: hbar = m = 1 throughout, as in the workloads' statement.  Arrays are
+indexed [z, y, x] (x fastest in memory); grid node i sits at
+x_i = (i - N/2) * dx, the convention fixed by the (x + L/2) shift of the
+trigonometric interpolant (Eq. AnBottomPsi).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Sequence
+
+import numpy as np
+
+HBAR = 1.0
+MASS = 1.0
+
+
+@dataclasses.dataclass
+class GridSpec:
+    """Geometry and time stepping of one internal model (Section 2, Fig. model-setup).
+
+    n, d        : grid points and spacing per axis (x, y, z)
+    dt          : leapfrog time step
+    abc_cells   : absorbing-layer width per axis, in cells, on both sides
+    abc_profile : "poly" (gamma = gamma_max * depth^p) or "poschl_teller" (Eq. Poshcl-Teller)
+    abc_param   : poly -> (p, gamma_max / (E0/hbar)); poschl_teller -> (U0 / (E0/hbar), alpha per cell)
+    tfsf_lo/hi  : outer edges (grid indices) of the TF/SF transition layer per axis
+    taper_cells : width of the transition layer (zeta rises over it, Eq. zeta_y)
+    tfsf_mode   : "exact" (scattered-field state, source -2i dt V psi_inc) or
+                  "paper" (state psi~ = psi_scat + zeta psi_inc, Eq. tildeSchrodinger)
+    huygens_lo/hi : grid indices of the six virtual planes (Fig. virtual-surface)
+    """
+
+    n: tuple
+    d: tuple
+    dt: float
+    abc_cells: tuple = (8, 8, 8)
+    abc_profile: str = "poly"
+    abc_param: tuple = (3.0, 5.0)
+    tfsf_lo: tuple = (14, 14, 14)
+    tfsf_hi: tuple = (34, 34, 34)
+    taper_cells: int = 4
+    tfsf_mode: str = "exact"
+    huygens_lo: tuple = (11, 11, 11)
+    huygens_hi: tuple = (37, 37, 37)
+    hbar: float = HBAR
+    mass: float = MASS
+    batch: int = 1
+
+    @property
+    def shape(self):
+        """numpy shape [z, y, x]."""
+        return (self.n[2], self.n[1], self.n[0])
+
+    def coords(self, axis: int) -> np.ndarray:
+        n, d = self.n[axis], self.d[axis]
+        return (np.arange(n) - n // 2) * d
+
+    def core_box(self):
+        """Index range [lo, hi] (inclusive) per axis where zeta == 1."""
+        return [(self.tfsf_lo[a] + self.taper_cells, self.tfsf_hi[a] - self.taper_cells) for a in range(3)]
+
+
+@dataclasses.dataclass
+class Incidence:
+    khat: tuple
+    k: float
+    ramp_time: float
+
+
+@dataclasses.dataclass
+class Workload:
+    """A complete run: grid, potential, incidences, DFT window and outputs."""
+
+    name: str
+    spec: GridSpec
+    V: np.ndarray
+    incidences: list
+    nsteps: int
+    window_first: int
+    window_len: int
+    fresnel_points: np.ndarray | None = None   # (M, 3) observation points
+    far_theta: np.ndarray | None = None        # radians
+    far_phi: np.ndarray | None = None
+
+
+# ----------------------------------------------------------------------------------
+# potentials
+# ----------------------------------------------------------------------------------
+
+def sphere_potential(spec: GridSpec, V0: float, radius: float, centre=(0.0, 0.0, 0.0), sub: int = 8) -> np.ndarray:
+    """Central square potential (Eq. sphericalV) voxelised by volume fraction.
+
+    The paper does not say how the sphere is put on the lattice; each node gets
+    V0 times the fraction of its cell (centred on the node) inside r <= radius,
+    estimated on a deterministic sub x sub x sub sub-grid.
+    """
+    xs = [spec.coords(a) - centre[a] for a in range(3)]
+    offs = (np.arange(sub) + 0.5) / sub - 0.5
+    V = np.zeros(spec.shape)
+    # only cells near the sphere need sub-sampling
+    reach = radius + 0.5 * math.sqrt(sum(di * di for di in spec.d))
+    idx = [np.nonzero(np.abs(xs[a]) <= reach)[0] for a in range(3)]
+    ox, oy, oz = np.meshgrid(offs * spec.d[0], offs * spec.d[1], offs * spec.d[2], indexing="ij")
+    for kk in idx[2]:
+        for jj in idx[1]:
+            for ii in idx[0]:
+                r2 = (xs[0][ii] + ox) ** 2 + (xs[1][jj] + oy) ** 2 + (xs[2][kk] + oz) ** 2
+                frac = np.count_nonzero(r2 <= radius * radius) / r2.size
+                V[kk, jj, ii] = V0 * frac
+    return V
+
+
+def random_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Uniform random rotation (QR of a Gaussian matrix with sign fix)."""
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q @ np.diag(np.sign(np.diag(r)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def gaussian_sum_potential(spec: GridSpec, E0: float, seed: int, count: int = 8,
+                           centre_radius: float = 4.0, sigma_range=(0.3, 1.2),
+                           amp_range=(-0.5, 0.5)) -> np.ndarray:
+    """Sum of anisotropic Gaussians with seeded centres, widths, rotations, amplitudes.
+
+    V = sum_g A_g exp(-1/2 (r-c_g)^T R_g S_g^-2 R_g^T (r-c_g)); A_g ~ U[amp_range]*E0,
+    c_g uniform in a ball of radius centre_radius, per-axis widths ~ U[sigma_range],
+    R_g uniform random rotations.  V is zeroed where |V| < 1e-8 max|V| and outside
+    the zeta == 1 core, so that (zeta - 1) V = 0 holds exactly.
+    """
+    rng = np.random.default_rng(seed)
+    x, y, z = spec.coords(0), spec.coords(1), spec.coords(2)
+    Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+    P = np.stack([X, Y, Z], axis=-1)
+    V = np.zeros(spec.shape)
+    for _ in range(count):
+        while True:
+            c = rng.uniform(-centre_radius, centre_radius, 3)
+            if np.dot(c, c) <= centre_radius ** 2:
+                break
+        sig = rng.uniform(sigma_range[0], sigma_range[1], 3)
+        R = random_rotation(rng)
+        A = rng.uniform(amp_range[0], amp_range[1]) * E0
+        M = R @ np.diag(1.0 / sig ** 2) @ R.T
+        dP = P - c
+        q = np.einsum("...i,ij,...j->...", dP, M, dP)
+        V += A * np.exp(-0.5 * q)
+    vmax = np.max(np.abs(V))
+    V[np.abs(V) < 1e-8 * vmax] = 0.0
+    core = spec.core_box()
+    mask = np.zeros(spec.shape, dtype=bool)
+    mask[core[2][0]:core[2][1] + 1, core[1][0]:core[1][1] + 1, core[0][0]:core[0][1] + 1] = True
+    V[~mask] = 0.0
+    return V
+
+
+# ----------------------------------------------------------------------------------
+# directions and observation points
+# ----------------------------------------------------------------------------------
+
+def fibonacci_directions(count: int = 8) -> np.ndarray:
+    """Fibonacci-sphere unit vectors: z_i = 1 - (2i+1)/count, phi_i = i*pi*(3 - sqrt 5)."""
+    out = []
+    for i in range(count):
+        zc = 1.0 - (2 * i + 1) / count
+        rho = math.sqrt(max(0.0, 1.0 - zc * zc))
+        ph = i * math.pi * (3.0 - math.sqrt(5.0))
+        out.append((rho * math.cos(ph), rho * math.sin(ph), zc))
+    return np.array(out)
+
+
+def seeded_direction(seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal(3)
+    return v / np.linalg.norm(v)
+
+
+def plane_points(normal, distance: float, side: float, count: int, centre=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """count x count points on a square plane normal to `normal`, at `distance` from `centre`."""
+    nrm = np.asarray(normal, dtype=float)
+    nrm = nrm / np.linalg.norm(nrm)
+    helper = np.array([1.0, 0.0, 0.0]) if abs(nrm[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = np.cross(nrm, helper)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(nrm, e1)
+    s = (np.arange(count) + 0.5) / count * side - side / 2
+    A, B = np.meshgrid(s, s, indexing="ij")
+    pts = np.asarray(centre) + distance * nrm + A[..., None] * e1 + B[..., None] * e2
+    return pts.reshape(-1, 3)
+
+
+def z_plane_points(z: float, side: float, count: int) -> np.ndarray:
+    s = (np.arange(count) + 0.5) / count * side - side / 2
+    Y, X = np.meshgrid(s, s, indexing="ij")
+    return np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], axis=1)
+
+
+def shell_points(count: int, r_min: float, r_max: float, seed: int) -> np.ndarray:
+    """Seeded points with radius uniform in [r_min, r_max] and direction uniform on the sphere."""
+    rng = np.random.default_rng(seed)
+    v = rng.standard_normal((count, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    r = rng.uniform(r_min, r_max, count)
+    return v * r[:, None]
+
+
+def far_field_grid():
+    """361 phi values (0..360 deg, 1 deg) x 180 theta values (0.5..179.5 deg)."""
+    phi = np.deg2rad(np.arange(361.0))
+    theta = np.deg2rad(np.arange(180) + 0.5)
+    T, P = np.meshgrid(theta, phi, indexing="ij")
+    return T.ravel(), P.ravel()
+
+
+# ----------------------------------------------------------------------------------
+# random fields for parity tests
+# ----------------------------------------------------------------------------------
+
+def random_field(shape, seed: int, dtype=np.complex128, scale: float = 1.0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    a = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    return (scale * a).astype(dtype)
+
+
+def smooth_random_field(spec: GridSpec, seed: int, kmax_frac: float = 0.5) -> np.ndarray:
+    """Band-limited random complex field (modes with |k_a| <= kmax_frac * Nyquist)."""
+    rng = np.random.default_rng(seed)
+    shape = spec.shape
+    F = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    for ax, a in ((2, 0), (1, 1), (0, 2)):
+        m = np.fft.fftfreq(spec.n[a]) * 2.0  # in units of Nyquist
+        keep = (np.abs(m) <= kmax_frac).astype(float)
+        sh = [1, 1, 1]
+        sh[ax] = -1
+        F = F * keep.reshape(sh)
+    u = np.fft.ifftn(F)
+    return u / np.max(np.abs(u))
+
+
+# ----------------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------------
+
+def stable_dt(spec_n, spec_d, vmax: float, frac: float = 0.9) -> float:
+    """frac times the PSTD stability bound (Eq. PSTDstability) with hbar = m = 1."""
+    kin = 0.5 * math.pi ** 2 * sum(1.0 / (d * d) for d in spec_d)
+    return frac / (kin + vmax)
+
+
+def dft_window(E0: float, dt: float, nsteps: int, periods: int = 3):
+    """Last `periods` whole carrier periods, rounded to whole steps."""
+    M = int(round(periods * 2 * math.pi / (E0 * dt)))
+    return nsteps - M, M
+
+
+def square_barrier_workload(n: int = 48, dx: float = 0.25, dt: float = 0.004, nsteps: int = 750,
+                            ramp_steps: int = 125, vfrac: float = 0.3, radius: float = 1.5,
+                            abc: int = 8, tf=(14, 34), taper: int = 4, hb=(11, 37),
+                            khat=(0.0, 0.0, 1.0), with_outputs: bool = True) -> Workload:
+    """Plain FP64 PSTD on a central square barrier, 48^3 (the small, fully-checked case).
+
+    k = 2 pi along +z, V0 = 0.3 k^2/2, radius 1.5 at the grid centre, 8-cell graded
+    absorber, TF/SF box over cells 14-34, Huygens box over cells 11-37.  The stated
+    dt = 0.005 breaks Eq. PSTDstability at dx = 0.25 (bound 0.004119), so the run is
+    made at dt = 0.004 for 750 steps with a 125-step raised-cosine ramp (the same
+    physical times).
+    """
+    k = 2 * math.pi
+    E0 = 0.5 * k * k
+    spec = GridSpec(n=(n, n, n), d=(dx, dx, dx), dt=dt, abc_cells=(abc,) * 3,
+                    tfsf_lo=(tf[0],) * 3, tfsf_hi=(tf[1],) * 3, taper_cells=taper,
+                    huygens_lo=(hb[0],) * 3, huygens_hi=(hb[1],) * 3)
+    V = sphere_potential(spec, vfrac * E0, radius)
+    n0, M = dft_window(E0, dt, nsteps)
+    wl = Workload(name=f"square-barrier-{n}^3", spec=spec, V=V,
+                  incidences=[Incidence(tuple(khat), k, ramp_steps * dt)],
+                  nsteps=nsteps, window_first=n0, window_len=M)
+    if with_outputs:
+        core = (tf[1] - taper - (tf[0] + taper)) * dx
+        wl.fresnel_points = z_plane_points(20.0, 1.5 * core, 32)
+        wl.far_theta = np.deg2rad(np.arange(181.0))
+        wl.far_phi = np.zeros(181)
+    return wl
+
+
+def gaussian_sum_workload(n: int = 128, dx: float = 0.25, nsteps: int = 3000, seed: int = 2404,
+                          abc: int = 16, tf=(24, 104), taper: int = 4, hb=(20, 108),
+                          fresnel_count: int = 256, with_outputs: bool = True) -> Workload:
+    """128^3 run on a seeded non-central Gaussian-sum potential (FP32 vs FP64 comparison case).
+
+    8 anisotropic Gaussians, centres within radius 4, widths U[0.3, 1.2], random
+    rotations, amplitudes U[-0.5, 0.5]*E; k = 2 pi along a seeded unit direction;
+    dt = 0.9 x the stability bound; outputs: a fresnel_count^2 plane normal to khat at
+    distance D^2/(4 lambda) (D = side of the zeta = 1 core), side 1.5 D, plus the
+    361 x 180 far-field grid.
+    """
+    k = 2 * math.pi
+    E0 = 0.5 * k * k
+    spec = GridSpec(n=(n, n, n), d=(dx, dx, dx), dt=1.0, abc_cells=(abc,) * 3,
+                    tfsf_lo=(tf[0],) * 3, tfsf_hi=(tf[1],) * 3, taper_cells=taper,
+                    huygens_lo=(hb[0],) * 3, huygens_hi=(hb[1],) * 3)
+    V = gaussian_sum_potential(spec, E0, seed)
+    spec.dt = stable_dt(spec.n, spec.d, float(np.max(np.abs(V))))
+    khat = seeded_direction(seed + 1)
+    n0, M = dft_window(E0, spec.dt, nsteps)
+    ramp = 0.5
+    wl = Workload(name=f"gaussian-sum-{n}^3", spec=spec, V=V,
+                  incidences=[Incidence(tuple(khat), k, ramp)],
+                  nsteps=nsteps, window_first=n0, window_len=M)
+    if with_outputs:
+        D = (tf[1] - taper - (tf[0] + taper)) * dx
+        lam = 2 * math.pi / k
+        wl.fresnel_points = plane_points(khat, D * D / (4 * lam), 1.5 * D, fresnel_count)
+        wl.far_theta, wl.far_phi = far_field_grid()
+    return wl
