@@ -1,0 +1,335 @@
+"""Benchmark of the PSTD scattering path on GB300.
+
+One step = one pass of the whole hot path over the 128^3 Gaussian-sum workload:
+reset, incident-wave tables, 3000 leapfrog steps with the running DFT on the six
+virtual planes over the last three carrier periods, the surface transform to the
+256 x 256 Fresnel plane and the 361 x 180 far-field cross-section.  FP32 state
+(complex64); the FP64 path is run once outside the timed region for the FP32-vs-FP64
+comparison.  Inputs are synthetic and seeded (paper_2403_04053_gb300.inputs).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PSTD cell-updates/s, FP32 vs FP64 at stated error (1 GB300); adjoint/forward time"
+WORKLOAD = "gaussian-sum-128^3"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ----------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    from paper_2403_04053_gb300 import inputs, pstd
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    wl = inputs.gaussian_sum_workload(nsteps=args.nsteps)
+    spec = wl.spec
+    inc = wl.incidences[0]
+    w0 = spec.hbar * inc.k ** 2 / (2 * spec.mass)
+    ncell = int(np.prod(spec.n))
+    stream = torch.cuda.current_stream()
+    dev = torch.device("cuda", local)
+    V_dev = torch.from_numpy(wl.V).to(dev)
+    pts_dev = torch.from_numpy(wl.fresnel_points).to(dev)
+    th_dev = torch.from_numpy(wl.far_theta).to(dev)
+    ph_dev = torch.from_numpy(wl.far_phi).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def one_pass(g, host=False):
+        g.reset()
+        g.set_incidence(0, inc.khat, inc.k, inc.ramp_time)
+        g.huygens_dft(0, [w0], wl.window_first, wl.window_len)
+        g.step(wl.nsteps)
+        if host:
+            psi = g.transform_to_points(0, 0, wl.fresnel_points)
+            ds, fa = g.cross_section(0, 0, wl.far_theta, wl.far_phi)
+        else:
+            psi = g.transform_to_points(0, 0, pts_dev)
+            ds, fa = g.cross_section(0, 0, th_dev, ph_dev)
+        return psi, ds, fa
+
+    g = pstd.Grid(spec, precision=pstd.F32, stream=stream.cuda_stream)
+    g.set_potential(V_dev)
+    for _ in range(args.warmup):
+        one_pass(g)
+    torch.cuda.synchronize()
+    times = []
+    launches0 = g.launch_count()
+    g.set_timing(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            psi, ds, fa = one_pass(g)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    barrier(world)
+    launches = g.launch_count() - launches0
+    kstats = {name: g.kernel_stats(name) for name in pstd.KERNELS}
+    g.set_timing(False)
+    t_step = reduce_max(sum(times) / len(times), world)
+    value = world * ncell * wl.nsteps / t_step
+
+    # end to end through host buffers: V, points and angles in, psi and dsigma out
+    h2d = wl.V.nbytes + wl.fresnel_points.nbytes + wl.far_theta.nbytes + wl.far_phi.nbytes
+    e2e_times = []
+    for i in range(max(1, min(3, args.steps))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_potential(wl.V)
+        psi_h, ds_h, fa_h = one_pass(g, host=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    d2h = psi_h.nbytes + ds_h.nbytes + fa_h.nbytes
+    t_e2e = reduce_max(sum(e2e_times) / len(e2e_times), world)
+
+    # roofline of the dominant kernel: algorithmic bytes = read psi^n, read psi^{n-1},
+    # write the updated level = 3 complex64 per cell per pass launch
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    top = max(("xpass", "ypass", "zpass"), key=lambda n: kstats[n][1])
+    nl, ms = kstats[top]
+    achieved = 24.0 * ncell / (ms / nl / 1e3) / 1e9
+    roofline = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4), "traffic": None,
+                "avg_launch_us": round(ms / nl * 1e3, 2), "algorithmic_bytes_per_launch": 24 * ncell,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback"}
+    kernel_ms = {n: {"launches": c, "total_ms": round(t, 3)} for n, (c, t) in kstats.items()}
+
+    # FP64 path once (outside the timed region): throughput and the FP32-vs-FP64 error
+    fp64 = None
+    if not args.skip_fp64:
+        g64 = pstd.Grid(spec, precision=pstd.F64, stream=stream.cuda_stream)
+        g64.set_potential(V_dev)
+        g64.set_timing(True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        psi64, ds64, fa64 = one_pass(g64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64 = e0.elapsed_time(e1) / 1e3
+        step_ms = sum(g64.kernel_stats(n)[1] for n in ("xpass", "ypass", "zpass", "plane_dft"))
+        ds32, ds64c = ds.double().cpu().numpy(), ds64.double().cpu().numpy()
+        p32, p64 = psi.cpu().numpy(), psi64.cpu().numpy()
+        fp64 = {"value": ncell * wl.nsteps / t64, "unit": "cell-updates/s",
+                "stepping_only_value": ncell * wl.nsteps / (step_ms / 1e3),
+                "fp32_speedup": round(t64 / t_step, 2),
+                "err_fp32_vs_fp64": {"dsdo_rel_l2": float(np.linalg.norm(ds32 - ds64c) / np.linalg.norm(ds64c)),
+                                     "fresnel_psi_rel_l2": float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64))}}
+        g64.close()
+    g.close()
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c64", "data": "synthetic (seeded Gaussian-sum potential)",
+        "config": {"workload": WORKLOAD, "grid": list(spec.n), "time_steps": wl.nsteps, "batch": 1,
+                   "dft_window_steps": wl.window_len, "fresnel_points": len(wl.fresnel_points),
+                   "far_field_directions": len(wl.far_theta), "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MB write) between timed steps"},
+        "e2e": {"value": world * ncell * wl.nsteps / t_e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "kernels": kernel_ms,
+        "fp64": fp64,
+    }
+    if rank == 0:
+        out["clocks"] = clk.summary()
+        if not args.skip_cpu:
+            out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------------
+# CPU oracle (baseline leg and the reference arm)
+# ----------------------------------------------------------------------------------
+def oracle_sample(wl, seconds: float):
+    """Time the FP64 oracle's leapfrog steps on the full 128^3 grid for about `seconds`."""
+    from oracle import pstd_oracle as po
+    inc = wl.incidences[0]
+    sim = po.Simulation(wl.spec, wl.V, inc.khat, inc.k, inc.ramp_time)
+    sim.n = 500
+    sim.cur = np.full(wl.spec.shape, 1e-3 + 0j)
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        sim.step(1)
+        steps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return int(np.prod(wl.spec.n)) * steps / dt, steps, dt
+
+
+def cpu_baseline(wl, seconds: float):
+    value, steps, dt = oracle_sample(wl, seconds)
+    return {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} FP64 leapfrog steps of the 128^3 workload (numpy FFT, one thread), {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2403_04053_gb300 import inputs
+    wl = inputs.gaussian_sum_workload(nsteps=args.nsteps, with_outputs=False)
+    per = max(2.0, args.cpu_seconds / 4)
+    for _ in range(args.warmup):
+        oracle_sample(wl, 0.1)
+    vals, tot_steps, tot_t = [], 0, 0.0
+    for _ in range(args.steps):
+        v, s, t = oracle_sample(wl, per)
+        vals.append(v)
+        tot_steps += s
+        tot_t += t
+    value = sum(vals) / len(vals)
+    ncell = int(np.prod(wl.spec.n))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_t / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+           "data": "synthetic (seeded Gaussian-sum potential)",
+           "config": {"workload": WORKLOAD, "grid": list(wl.spec.n), "sample": "leapfrog steps only, FP64 oracle"},
+           "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                            "sample": f"{tot_steps} FP64 oracle steps of the 128^3 grid in {tot_t:.1f} s"},
+           "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "cells_per_step": ncell}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    p.add_argument("--nsteps", type=int, default=3000, help="leapfrog steps per pass (the workload's 3000)")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--skip-cpu", action="store_true")
+    p.add_argument("--skip-fp64", action="store_true")
+    args = p.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

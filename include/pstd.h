@@ -1,0 +1,192 @@
+/*
+ * pstd.h -- C ABI of the GB300 PSTD quantum-scattering library.
+ *
+ * The library advances the time-dependent Schroedinger equation on a 3-D grid with
+ * the leapfrog pseudo-spectral time-domain (PSTD) update of Chen, "A General PSTD
+ * Method to Solve Quantum Scattering in the Fresnel and Far-Field Regions by A
+ * Localized Potential of Arbitrary Form" (arXiv 2403.04053), Eq. PSTDupdating,
+ * injects plane waves with total-field/scattered-field sources (Section 2.2),
+ * absorbs outgoing waves with a masking layer (Eqs. expmask, Gamma), accumulates
+ * the running single-frequency DFT of psi and d psi/dn on six virtual planes
+ * (Eqs. psiphasor, dpsiphasor) and carries it to arbitrary exterior points and to
+ * the far field with the quantum surface-equivalence transform (Eqs. NTDF,
+ * bottomPsi_lm ... Psi).
+ *
+ * Conventions
+ *  - Every call returns a pstd_status.  Nothing aborts or throws across the ABI.
+ *    pstd_last_error() gives a message for the most recent failure on a grid (or,
+ *    with NULL, for a failed pstd_create_grid on the calling thread).
+ *  - The library owns every device buffer of a grid.  The caller owns every array
+ *    it passes; `mem` says whether a pointer is host (PSTD_MEM_HOST) or device
+ *    (PSTD_MEM_DEVICE) memory.  Device pointers must be on the grid's device.
+ *  - Calls are asynchronous on the grid's CUDA stream (pstd_grid_desc.stream,
+ *    NULL = the legacy default stream) unless they return host data: calls that
+ *    write host memory synchronise the stream before they return.  Device errors
+ *    of an asynchronous call surface at the next synchronising call.
+ *  - Host scalars and coordinates are double.  Complex arrays are interleaved
+ *    (re, im).  Real-space arrays are ordered [z][y][x] (x fastest) with node i at
+ *    x_i = (i - n/2) d (the convention of Eq. AnBottomPsi's (x + L/2) shift);
+ *    batch members are outermost.
+ *  - Units: hbar and mass are given in the descriptor; energies E = hbar^2 k^2 / 2m.
+ */
+#ifndef PSTD_H
+#define PSTD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PSTD_OK = 0,
+    PSTD_EINVAL = 1,      /* bad argument, geometry, size or call order detail */
+    PSTD_ENOMEM = 2,      /* device allocation failed */
+    PSTD_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+    PSTD_EUNSTABLE = 4,   /* dt above the PSTD stability bound (Eq. PSTDstability) */
+    PSTD_ESTATE = 5,      /* call not valid in the grid's current state */
+    PSTD_ENONFINITE = 6,  /* the state became NaN/Inf (detected on the device) */
+    PSTD_ETIMEOUT = 7     /* a bounded device wait gave up */
+} pstd_status;
+
+enum { PSTD_F32 = 0, PSTD_F64 = 1 };                       /* arithmetic precision of the state */
+enum { PSTD_MEM_HOST = 0, PSTD_MEM_DEVICE = 1 };
+enum { PSTD_DTYPE_F32 = 0, PSTD_DTYPE_F64 = 1 };
+enum { PSTD_ABC_POLY = 0, PSTD_ABC_POSCHL_TELLER = 1 };     /* absorbing-layer profile */
+enum { PSTD_TFSF_EXACT = 0, PSTD_TFSF_PAPER = 1 };          /* TF/SF source form */
+enum { PSTD_ENV_CW_RAMP = 0 };                              /* incident-wave envelope */
+enum { PSTD_FIELD_CURRENT = 0, PSTD_FIELD_PREVIOUS = 1, PSTD_FIELD_SCATTERED = 2 };
+enum { PSTD_MAX_FREQ = 4, PSTD_MAX_BATCH = 64 };
+
+typedef struct pstd_grid pstd_grid;   /* opaque */
+
+/* Geometry of one internal model (Section 2, Fig. model-setup).
+ *  n[3], d[3]      points and spacing along x, y, z.  Each n must be one of
+ *                  8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384.
+ *  dt, hbar, mass  leapfrog step and units.
+ *  precision       PSTD_F32 (complex64 state) or PSTD_F64 (complex128 state).
+ *  batch           number of incident waves advanced together against one V (1..PSTD_MAX_BATCH).
+ *  abc_cells[3]    absorbing-layer width per axis (cells, both ends; 0 = periodic axis).
+ *  abc_profile     PSTD_ABC_POLY: gamma = abc_param[1] (E0/hbar) * depth^abc_param[0]
+ *                  PSTD_ABC_POSCHL_TELLER: gamma = abc_param[0] (E0/hbar) / cosh^2(abc_param[1] d)
+ *                  (Eq. Poshcl-Teller, d in cells from the outermost surface).  E0 is the
+ *                  energy of the incident wave of batch member 0.
+ *  tfsf_lo/hi[3], taper_cells   outer edges of the TF/SF transition layer and its width
+ *                  (zeta rises over (lo, lo + taper), Eq. zeta_y); the potential must vanish
+ *                  outside the zeta == 1 core.
+ *  tfsf_mode       PSTD_TFSF_EXACT: the state is the scattered field, the incident wave
+ *                  enters through -2i dt V psi_inc / hbar (zero leakage at V = 0);
+ *                  PSTD_TFSF_PAPER: the state is psi~ = psi_scat + zeta psi_inc and the
+ *                  source of Eq. tildeSchrodinger acts in the transition layer.
+ *  huygens_lo/hi[3] node indices of the six virtual planes (Fig. virtual-surface); they must
+ *                  lie outside the TF/SF box and inside the absorbing layer's inner edge.
+ *  stream          cudaStream_t for all work of the grid (NULL = default stream).
+ */
+typedef struct {
+    int n[3];
+    double d[3];
+    double dt, hbar, mass;
+    int precision;
+    int batch;
+    int abc_cells[3];
+    int abc_profile;
+    double abc_param[2];
+    int tfsf_lo[3], tfsf_hi[3];
+    int taper_cells;
+    int tfsf_mode;
+    int huygens_lo[3], huygens_hi[3];
+    void* stream;
+} pstd_grid_desc;
+
+/* Validate the geometry (sizes, nesting of absorber / virtual planes / TF-SF box),
+ * check dt against Eq. PSTDstability with V = 0, allocate the device state (two time
+ * levels per batch member) and tables.  *out receives the new grid.
+ * EINVAL bad descriptor, EUNSTABLE dt too large, ENOMEM, ECUDA. */
+pstd_status pstd_create_grid(const pstd_grid_desc* desc, pstd_grid** out);
+
+/* Free every device buffer of the grid (synchronises its stream).  NULL is accepted. */
+pstd_status pstd_destroy_grid(pstd_grid* g);
+
+/* Real potential V on the full grid, [z][y][x], dtype PSTD_DTYPE_F32/F64, host or device.
+ * V must be zero where zeta < 1 ((zeta - 1) V = 0, Section 2.2.2), else EINVAL; dt must
+ * satisfy Eq. PSTDstability with |V|max, else EUNSTABLE.  The library keeps V on the
+ * bounding box of its support, rounded to the grid precision. */
+pstd_status pstd_set_potential(pstd_grid* g, const void* V, int mem, int dtype);
+
+/* Incident plane wave of batch member b (Eqs. khat, Oinc, inc_d):
+ *   psi_inc(r, t) = a(t) exp(i k khat . (r - r_O) - i E t / hbar),  E = hbar^2 k^2 / 2m,
+ * r_O the corner of the TF/SF box first met by the wavefront, a(t) the raised-cosine
+ * switch-on (1 - cos(pi t / ramp_time)) / 2 for t < ramp_time (envelope PSTD_ENV_CW_RAMP).
+ * Also sets the dispersion factor eta = sinc(E dt / hbar) of member b (Eq. numdis2).
+ * khat need not be normalised (it is).  EINVAL for b out of range, k <= 0, khat = 0. */
+pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double k, int envelope, double ramp_time);
+
+/* Zero both time levels, the step counter and every DFT accumulator of all members. */
+pstd_status pstd_reset(pstd_grid* g);
+
+/* Running DFT window of member b (Eqs. psiphasor, dpsiphasor, incpsiphasor): while the
+ * step index n of the current state is in [first_step, first_step + n_steps), each
+ * pstd_step adds psi^n e^{i omega t_n} and (d psi^n / d a) e^{i omega t_n} on the six
+ * planes to double-precision accumulators (a = the plane's normal axis, spectral
+ * derivative), for each of the nfreq (<= PSTD_MAX_FREQ) angular frequencies.  Clears
+ * member b's accumulators.  b = -1 configures every member. */
+pstd_status pstd_huygens_dft(pstd_grid* g, int b, const double* omega, int nfreq, long first_step, long n_steps);
+
+/* Advance every batch member by nsteps leapfrog steps (Eq. PSTDupdating with the mask
+ * of Eq. expmask).  Asynchronous; ESTATE if a member has no incidence. */
+pstd_status pstd_step(pstd_grid* g, long nsteps);
+
+/* Scattered wave function at M points xyz[3*i + {0,1,2}] from the DFT of member b at
+ * frequency index f, scaled by the incident phasor at r_O (Eqs. scaledphsiphasor,
+ * scaleddpsiphasor): the per-cell semi-analytic surface integral of Eqs. bottomPsi_lm,
+ * topPsi_lm, backfrontPsi_mn, leftrightPsi_ln summed per Eq. Psi, each cell integral
+ * evaluated by tensor Gauss-Legendre quadrature of the trigonometric interpolant
+ * (Eq. AnBottomPsi) times the linearised Green's phase.  out_psi: M complex128.
+ * `mem` applies to both xyz and out_psi.  ESTATE if the window has not completed. */
+pstd_status pstd_transform_to_points(pstd_grid* g, int b, int f, const double* xyz, long M, void* out_psi, int mem);
+
+/* Far-field amplitude f(theta, phi) = lim r e^{-ikr} Psi(r rhat) (the r -> infinity limit of
+ * the same per-cell integrals) and dsigma/dOmega = |f|^2 at M directions.  out_dsdo: M
+ * doubles; out_f: M complex128 or NULL.  `mem` applies to theta, phi, out_dsdo, out_f. */
+pstd_status pstd_cross_section(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M,
+                               double* out_dsdo, void* out_f, int mem);
+
+/* Copy a state of member b out: PSTD_FIELD_CURRENT (psi^n), PSTD_FIELD_PREVIOUS
+ * (psi^{n-1}) or PSTD_FIELD_SCATTERED (psi^n minus zeta psi_inc^n in the PAPER form, the
+ * state itself in the EXACT form).  out: n[0]*n[1]*n[2] complex values of the grid
+ * precision (complex64 for PSTD_F32, complex128 for PSTD_F64). */
+pstd_status pstd_get_field(pstd_grid* g, int b, int which, void* out, int mem);
+
+/* Load both time levels of member b (same layout and precision as pstd_get_field) and
+ * set the step index to n: checkpoint restore, and one-step parity tests. */
+pstd_status pstd_set_field(pstd_grid* g, int b, const void* prev, const void* cur, long n, int mem);
+
+/* The six scaled plane phasor pairs of member b, frequency f, as complex128, in face
+ * order 2*axis + side (axis x, y, z; side 0 = low, 1 = high); each face gives its psi
+ * plane then its d psi / d axis plane, each [slow][fast] over the two in-plane axes
+ * (x-normal: [z][y], y-normal: [z][x], z-normal: [y][x]). */
+pstd_status pstd_get_phasors(pstd_grid* g, int b, int f, void* out, int mem);
+
+/* Wait for the grid's stream; ENONFINITE if a step produced NaN/Inf since the last check. */
+pstd_status pstd_synchronize(pstd_grid* g);
+
+/* Step index n of the current state. */
+pstd_status pstd_get_step(pstd_grid* g, long* n);
+
+/* Sufficient stability bound of Eq. PSTDstability for the descriptor's spacing and units. */
+pstd_status pstd_stability_dt_max(const pstd_grid_desc* desc, double vmax, double* out_dt);
+
+/* Per-kernel timing with CUDA events on the grid's stream (off by default).  Kernel ids:
+ * 0 x-pass, 1 y-pass, 2 z-pass, 3 plane DFT, 4 transform/node preparation, 5 point transform,
+ * 6 far field.  pstd_kernel_stats returns the launches and summed milliseconds since the
+ * last pstd_set_timing(g, 1) (synchronises).  pstd_launch_count counts every kernel the
+ * grid launched since creation. */
+pstd_status pstd_set_timing(pstd_grid* g, int enable);
+pstd_status pstd_kernel_stats(pstd_grid* g, int kernel_id, long* launches, double* total_ms);
+pstd_status pstd_launch_count(pstd_grid* g, long* count);
+
+/* Message of the last failure on g (or of the last failed pstd_create_grid when g is NULL). */
+const char* pstd_last_error(const pstd_grid* g);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSTD_H */

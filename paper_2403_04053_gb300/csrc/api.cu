@@ -1,0 +1,1161 @@
+// C ABI of the PSTD library (include/pstd.h): grid objects, host-side tables in double
+// precision, the step loop, the running-DFT bookkeeping and the transform drivers.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pstd_internal.h"
+
+using namespace pstd;
+using cd = std::complex<double>;
+
+namespace {
+
+thread_local std::string g_create_error;
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kSizes[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384};
+constexpr int kKernelIds = 7;
+
+bool supported_size(int n)
+{
+    for (int s : kSizes)
+        if (s == n) return true;
+    return false;
+}
+
+struct MemberHost {
+    bool has_inc = false;
+    double khat[3] = {0, 0, 1};
+    double k = 0, E = 0, w0 = 0, eta = 1, ramp = 0;
+    double rO[3] = {0, 0, 0};
+    int nfreq = 0;
+    double omega[PSTD_MAX_FREQ] = {0, 0, 0, 0};
+    long long first = 0, len = 0;
+    long long accumulated = 0;
+    cd inc_phasor[PSTD_MAX_FREQ];
+};
+
+struct TimedLaunch {
+    int kernel;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct pstd_grid {
+    pstd_grid_desc desc{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    int prec = PSTD_F32;
+    size_t csize = 8, rsize = 4;
+    long long ncell = 0;
+    int batch = 1;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    long long n = 0;
+    void* tw[3] = {};
+    void* kin[3] = {};
+    void* mask[3] = {};
+    void* zeta[3] = {};
+    void* zeta1[3] = {};
+    void* zeta2[3] = {};
+    void* phase[3] = {};
+    void* dw[3] = {};
+    void* V = nullptr;
+    int vlo[3] = {0, 0, 0}, vhi[3] = {0, 0, 0};
+    double vmax = 0;
+    bool mask_ready = false;
+    MemberDev* mem_dev = nullptr;
+    std::vector<MemberHost> mem;
+    // running DFT accumulators [member][freq][face: psi plane, dpsi plane]
+    double2* acc = nullptr;
+    int acc_freq_cap = 0;
+    long long face_off[6] = {}, face_size[6] = {};
+    long long acc_freq_stride = 0;
+    long long phasor_version = 0;
+    int* flag = nullptr;
+    // transform
+    int G = 8;
+    std::vector<double> gl_x, gl_w;
+    double* gl_w_dev = nullptr;
+    FaceGeom faces[6];
+    long long ncells = 0;
+    double2* MbT[6] = {};
+    double2* Mc[6] = {};
+    double2* T1 = nullptr;
+    double2* OutP = nullptr;
+    double2* OutD = nullptr;
+    void* rec = nullptr;
+    int rec_member = -1, rec_freq = -1;
+    long long rec_version = -1;
+    double2* partial = nullptr;
+    size_t partial_cap = 0;
+    double* pts_dev = nullptr;
+    size_t pts_cap = 0;
+    double2* out_dev = nullptr;
+    size_t out_cap = 0;
+    double* dsdo_dev = nullptr;
+    size_t dsdo_cap = 0;
+    // instrumentation
+    bool timing = false;
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> event_pool;
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+pstd_status fail(pstd_grid* g, pstd_status s, const std::string& msg)
+{
+    if (g) g->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+pstd_status cuda_fail(pstd_grid* g, cudaError_t e, const char* where)
+{
+    return fail(g, PSTD_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(g, call)                                             \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail((g), e_, #call); \
+    } while (0)
+
+template <typename T> cudaError_t dalloc(T** p, size_t bytes)
+{
+    return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+double coord(const pstd_grid_desc& d, int axis, int i) { return (i - d.n[axis] / 2) * d.d[axis]; }
+
+double wavenumber(int n, double d, int m)
+{
+    const int ms = m < (n + 1) / 2 ? m : m - n;   // -N/2..N/2-1 (note after Eq. PSTDupdating)
+    return 2.0 * kPi * ms / (n * d);
+}
+
+// upload a host vector of doubles as the grid precision (real) or as complex
+pstd_status upload_real(pstd_grid* g, void** dst, const std::vector<double>& h)
+{
+    if (!*dst) CK(g, dalloc(dst, h.size() * g->rsize));
+    if (g->prec == PSTD_F64) {
+        CK(g, cudaMemcpy(*dst, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(h.begin(), h.end());
+        CK(g, cudaMemcpy(*dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return PSTD_OK;
+}
+
+pstd_status upload_complex(pstd_grid* g, void** dst, const std::vector<cd>& h, size_t offset_elems = 0,
+                           size_t total_elems = 0)
+{
+    if (!*dst) CK(g, dalloc(dst, (total_elems ? total_elems : h.size()) * g->csize));
+    if (g->prec == PSTD_F64) {
+        CK(g, cudaMemcpy(static_cast<char*>(*dst) + offset_elems * 16, h.data(), h.size() * 16, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float2> f(h.size());
+        for (size_t i = 0; i < h.size(); ++i) f[i] = make_float2((float)h[i].real(), (float)h[i].imag());
+        CK(g, cudaMemcpy(static_cast<char*>(*dst) + offset_elems * 8, f.data(), f.size() * 8, cudaMemcpyHostToDevice));
+    }
+    return PSTD_OK;
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_G.
+void gauss_legendre(int G, std::vector<double>& x, std::vector<double>& w)
+{
+    x.assign(G, 0.0);
+    w.assign(G, 0.0);
+    for (int i = 0; i < G; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (G + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int l = 2; l <= G; ++l) {
+                const double p2 = ((2.0 * l - 1.0) * z * p1 - (l - 1.0) * p0) / l;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = G * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int l = 2; l <= G; ++l) {
+            const double p2 = ((2.0 * l - 1.0) * z * p1 - (l - 1.0) * p0) / l;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = G * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = -z;   // ascending; x[G-1-i] = -x[i]
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// absorption rate per node along one axis (Eq. Poshcl-Teller or the graded polynomial)
+std::vector<double> absorber_gamma(const pstd_grid_desc& d, int axis, double E0)
+{
+    const int n = d.n[axis], w = d.abc_cells[axis];
+    std::vector<double> g(n, 0.0);
+    if (w <= 0) return g;
+    const double unit = E0 / d.hbar;
+    for (int i = 0; i < n; ++i) {
+        if (d.abc_profile == PSTD_ABC_POLY) {
+            const int depth = std::max(std::max(w - i, i - (n - 1 - w)), 0);
+            g[i] = d.abc_param[1] * unit * std::pow((double)depth / w, d.abc_param[0]);
+        } else {
+            const int dist = std::min(i, n - 1 - i);
+            if (dist < w) {
+                const double ch = std::cosh(d.abc_param[1] * dist);
+                g[i] = d.abc_param[0] * unit / (ch * ch);
+            }
+        }
+    }
+    return g;
+}
+
+double xi(double r) { return r - 2.0 / (3.0 * kPi) * std::sin(2 * kPi * r) + 1.0 / (12.0 * kPi) * std::sin(4 * kPi * r); }
+double dxi(double r) { return 1.0 - 4.0 / 3.0 * std::cos(2 * kPi * r) + 1.0 / 3.0 * std::cos(4 * kPi * r); }
+double d2xi(double r) { return 8.0 * kPi / 3.0 * std::sin(2 * kPi * r) - 4.0 * kPi / 3.0 * std::sin(4 * kPi * r); }
+
+void zeta_tables(const pstd_grid_desc& d, int axis, std::vector<double>& z, std::vector<double>& z1, std::vector<double>& z2)
+{
+    const int n = d.n[axis], lo = d.tfsf_lo[axis], hi = d.tfsf_hi[axis], t = d.taper_cells;
+    const double w = t * d.d[axis];
+    z.assign(n, 0.0);
+    z1.assign(n, 0.0);
+    z2.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        if (i > lo && i < lo + t) {
+            const double r = double(i - lo) / t;
+            z[i] = xi(r); z1[i] = dxi(r) / w; z2[i] = d2xi(r) / (w * w);
+        } else if (i >= lo + t && i <= hi - t) {
+            z[i] = 1.0;
+        } else if (i > hi - t && i < hi) {
+            const double r = double(i - (hi - t)) / t;
+            z[i] = 1.0 - xi(r); z1[i] = -dxi(r) / w; z2[i] = -d2xi(r) / (w * w);
+        }
+    }
+}
+
+cudaEvent_t take_event(pstd_grid* g)
+{
+    if (!g->event_pool.empty()) {
+        cudaEvent_t e = g->event_pool.back();
+        g->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct Timer {
+    pstd_grid* g;
+    int id;
+    cudaEvent_t a = nullptr;
+    Timer(pstd_grid* g_, int id_) : g(g_), id(id_)
+    {
+        if (g->timing) {
+            a = take_event(g);
+            cudaEventRecord(a, g->stream);
+        }
+    }
+    ~Timer()
+    {
+        ++g->launches;
+        if (g->timing && a) {
+            cudaEvent_t b = take_event(g);
+            cudaEventRecord(b, g->stream);
+            g->timed.push_back({id, a, b});
+        }
+    }
+};
+
+pstd_status check_member(pstd_grid* g, int b)
+{
+    if (b < 0 || b >= g->batch) return fail(g, PSTD_EINVAL, "batch member out of range");
+    return PSTD_OK;
+}
+
+pstd_status copy_in(pstd_grid* g, void* dst, const void* src, size_t bytes, int mem)
+{
+    if (mem == PSTD_MEM_HOST) CK(g, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, g->stream));
+    else if (mem == PSTD_MEM_DEVICE) CK(g, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, g->stream));
+    else return fail(g, PSTD_EINVAL, "mem must be PSTD_MEM_HOST or PSTD_MEM_DEVICE");
+    return PSTD_OK;
+}
+
+pstd_status copy_out(pstd_grid* g, void* dst, const void* src, size_t bytes, int mem)
+{
+    if (mem == PSTD_MEM_HOST) {
+        CK(g, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, g->stream));
+        CK(g, cudaStreamSynchronize(g->stream));
+    } else if (mem == PSTD_MEM_DEVICE) {
+        CK(g, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, g->stream));
+    } else {
+        return fail(g, PSTD_EINVAL, "mem must be PSTD_MEM_HOST or PSTD_MEM_DEVICE");
+    }
+    return PSTD_OK;
+}
+
+template <typename T> pstd_status ensure(pstd_grid* g, T** p, size_t& cap, size_t bytes)
+{
+    if (cap >= bytes && *p) return PSTD_OK;
+    if (*p) {
+        CK(g, cudaStreamSynchronize(g->stream));
+        cudaFree(*p);
+        *p = nullptr;
+        cap = 0;
+    }
+    cudaError_t e = dalloc(p, bytes);
+    if (e != cudaSuccess) return fail(g, PSTD_ENOMEM, "device allocation failed");
+    cap = bytes;
+    return PSTD_OK;
+}
+
+pstd_status validate(const pstd_grid_desc* d)
+{
+    if (!d) return fail(nullptr, PSTD_EINVAL, "null descriptor");
+    for (int a = 0; a < 3; ++a) {
+        if (!supported_size(d->n[a])) return fail(nullptr, PSTD_EINVAL, "n must be one of 8,12,16,24,32,48,64,96,128,192,256,384");
+        if (!(d->d[a] > 0)) return fail(nullptr, PSTD_EINVAL, "spacing must be positive");
+        const int n = d->n[a], w = d->abc_cells[a];
+        if (w < 0 || 2 * w >= n) return fail(nullptr, PSTD_EINVAL, "absorber wider than the grid");
+        if (d->taper_cells < 1) return fail(nullptr, PSTD_EINVAL, "taper_cells must be >= 1");
+        if (!(d->huygens_lo[a] >= w && d->huygens_lo[a] <= d->tfsf_lo[a] &&
+              d->tfsf_lo[a] + d->taper_cells <= d->tfsf_hi[a] - d->taper_cells && d->tfsf_hi[a] <= d->huygens_hi[a] &&
+              d->huygens_hi[a] <= n - 1 - w && d->huygens_lo[a] < d->huygens_hi[a]))
+            return fail(nullptr, PSTD_EINVAL,
+                        "need abc <= huygens_lo <= tfsf_lo, tfsf_lo + taper <= tfsf_hi - taper, tfsf_hi <= huygens_hi <= n-1-abc");
+    }
+    if (!(d->dt > 0) || !(d->hbar > 0) || !(d->mass > 0)) return fail(nullptr, PSTD_EINVAL, "dt, hbar, mass must be positive");
+    if (d->precision != PSTD_F32 && d->precision != PSTD_F64) return fail(nullptr, PSTD_EINVAL, "precision");
+    if (d->batch < 1 || d->batch > PSTD_MAX_BATCH) return fail(nullptr, PSTD_EINVAL, "batch out of range");
+    if (d->abc_profile != PSTD_ABC_POLY && d->abc_profile != PSTD_ABC_POSCHL_TELLER) return fail(nullptr, PSTD_EINVAL, "abc_profile");
+    if (d->tfsf_mode != PSTD_TFSF_EXACT && d->tfsf_mode != PSTD_TFSF_PAPER) return fail(nullptr, PSTD_EINVAL, "tfsf_mode");
+    return PSTD_OK;
+}
+
+double dt_bound(const pstd_grid_desc& d, double vmax)
+{
+    double s = 0;
+    for (int a = 0; a < 3; ++a) s += 1.0 / (d.d[a] * d.d[a]);
+    return d.hbar / (d.hbar * d.hbar * kPi * kPi / (2.0 * d.mass) * s + std::fabs(vmax));
+}
+
+pstd_status upload_members(pstd_grid* g)
+{
+    std::vector<MemberDev> h(g->batch);
+    for (int b = 0; b < g->batch; ++b) {
+        const MemberHost& m = g->mem[b];
+        MemberDev& o = h[b];
+        std::memset(&o, 0, sizeof(o));
+        o.w0 = m.w0;
+        o.ramp = m.ramp;
+        o.eta = m.eta;
+        for (int a = 0; a < 3; ++a) o.k[a] = m.k * m.khat[a];
+        o.nfreq = m.nfreq;
+        for (int f = 0; f < PSTD_MAX_FREQ; ++f) o.omega[f] = m.omega[f];
+    }
+    CK(g, cudaMemcpyAsync(g->mem_dev, h.data(), sizeof(MemberDev) * g->batch, cudaMemcpyHostToDevice, g->stream));
+    CK(g, cudaStreamSynchronize(g->stream));
+    return PSTD_OK;
+}
+
+template <typename R> StepArgs<R> step_args(pstd_grid* g)
+{
+    using C = typename StepArgs<R>::C;
+    StepArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.cur = static_cast<const C*>(g->buf[g->cur]);
+    a.prev = static_cast<C*>(g->buf[g->cur ^ 1]);
+    a.nx = g->desc.n[0]; a.ny = g->desc.n[1]; a.nz = g->desc.n[2];
+    a.ncell = g->ncell;
+    for (int ax = 0; ax < 3; ++ax) {
+        a.tw[ax] = static_cast<const C*>(g->tw[ax]);
+        a.kin[ax] = static_cast<const R*>(g->kin[ax]);
+        a.mask[ax] = static_cast<const R*>(g->mask[ax]);
+        a.phase[ax] = static_cast<const C*>(g->phase[ax]);
+        a.zeta[ax] = static_cast<const R*>(g->zeta[ax]);
+        a.zeta1[ax] = static_cast<const R*>(g->zeta1[ax]);
+        a.zeta2[ax] = static_cast<const R*>(g->zeta2[ax]);
+        a.tf_lo[ax] = g->desc.tfsf_lo[ax];
+        a.tf_hi[ax] = g->desc.tfsf_hi[ax];
+        a.vlo[ax] = g->vlo[ax];
+        a.vhi[ax] = g->vhi[ax];
+    }
+    a.V = static_cast<const R*>(g->V);
+    a.mem = g->mem_dev;
+    a.step = g->n;
+    a.dt = g->desc.dt; a.hbar = g->desc.hbar; a.mass = g->desc.mass;
+    a.mode = g->desc.tfsf_mode;
+    a.flag = g->flag;
+    return a;
+}
+
+template <typename R> pstd_status run_dft(pstd_grid* g, unsigned long long mask)
+{
+    using C = typename DftArgs<R>::C;
+    DftArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.cur = static_cast<const C*>(g->buf[g->cur]);
+    a.nx = g->desc.n[0]; a.ny = g->desc.n[1]; a.nz = g->desc.n[2];
+    a.ncell = g->ncell;
+    a.acc = g->acc;
+    a.acc_freq_stride = g->acc_freq_stride;
+    a.acc_member_stride = g->acc_freq_stride * g->acc_freq_cap;
+    for (int f = 0; f < 6; ++f) { a.face_off[f] = g->face_off[f]; a.face_size[f] = g->face_size[f]; }
+    a.mem = g->mem_dev;
+    a.member_mask = mask;
+    a.step = g->n;
+    a.dt = g->desc.dt;
+    for (int ax = 0; ax < 3; ++ax) {
+        a.axis = ax;
+        a.h[0] = g->desc.huygens_lo[ax];
+        a.h[1] = g->desc.huygens_hi[ax];
+        a.dw = static_cast<const C*>(g->dw[ax]);
+        Timer t(g, 3);
+        CK(g, launch_plane_dft<R>(a, g->batch, g->stream));
+    }
+    return PSTD_OK;
+}
+
+template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps)
+{
+    for (long s = 0; s < nsteps; ++s) {
+        unsigned long long mask = 0;
+        for (int b = 0; b < g->batch; ++b) {
+            const MemberHost& m = g->mem[b];
+            if (m.nfreq > 0 && g->n >= m.first && g->n < m.first + m.len) mask |= 1ull << b;
+        }
+        if (mask) {
+            pstd_status st = run_dft<R>(g, mask);
+            if (st != PSTD_OK) return st;
+            const double t = g->n * g->desc.dt;
+            for (int b = 0; b < g->batch; ++b) {
+                if (!((mask >> b) & 1ull)) continue;
+                MemberHost& m = g->mem[b];
+                const double env = (m.ramp <= 0 || t >= m.ramp) ? 1.0 : (t <= 0 ? 0.0 : 0.5 * (1.0 - std::cos(kPi * t / m.ramp)));
+                const cd inc = env * std::exp(cd(0.0, -m.w0 * t));   // psi_inc at r_O (Eq. incpsiphasor)
+                for (int f = 0; f < m.nfreq; ++f) m.inc_phasor[f] += inc * std::exp(cd(0.0, m.omega[f] * t));
+                ++m.accumulated;
+            }
+            ++g->phasor_version;
+        }
+        StepArgs<R> a = step_args<R>(g);
+        {
+            Timer t(g, 0);
+            CK(g, launch_xpass<R>(a, g->batch, g->stream));
+        }
+        {
+            Timer t(g, 1);
+            CK(g, launch_ypass<R>(a, g->batch, g->stream));
+        }
+        {
+            Timer t(g, 2);
+            CK(g, launch_zpass<R>(a, g->batch, g->stream));
+        }
+        g->cur ^= 1;
+        ++g->n;
+    }
+    return PSTD_OK;
+}
+
+// -------------------------------------------------------------------------------------
+// transform preparation
+// -------------------------------------------------------------------------------------
+pstd_status setup_transform(pstd_grid* g)
+{
+    if (g->MbT[0]) return PSTD_OK;
+    const pstd_grid_desc& d = g->desc;
+    g->G = g->prec == PSTD_F64 ? 8 : 6;
+    gauss_legendre(g->G, g->gl_x, g->gl_w);
+    const int G = g->G;
+    CK(g, dalloc(&g->gl_w_dev, sizeof(double) * G));
+    CK(g, cudaMemcpy(g->gl_w_dev, g->gl_w.data(), sizeof(double) * G, cudaMemcpyHostToDevice));
+    long long cell0 = 0;
+    size_t t1max = 0, outmax = 0;
+    for (int f = 0; f < 6; ++f) {
+        const int a = f / 2, s = f % 2;
+        FaceGeom& F = g->faces[f];
+        F.axis = a;
+        F.b = a == 0 ? 1 : 0;
+        F.c = a == 2 ? 1 : 2;
+        F.sigma = s == 0 ? -1.0 : 1.0;
+        F.plane = coord(d, a, s == 0 ? d.huygens_lo[a] : d.huygens_hi[a]);
+        F.db = d.d[F.b];
+        F.dc = d.d[F.c];
+        F.cb0 = coord(d, F.b, d.huygens_lo[F.b]) + 0.5 * F.db;
+        F.cc0 = coord(d, F.c, d.huygens_lo[F.c]) + 0.5 * F.dc;
+        F.L = d.huygens_hi[F.b] - d.huygens_lo[F.b];
+        F.M = d.huygens_hi[F.c] - d.huygens_lo[F.c];
+        F.Nb = d.n[F.b];
+        F.Nc = d.n[F.c];
+        F.cell0 = cell0;
+        cell0 += (long long)F.L * F.M;
+        // trigonometric interpolation weights w(xi - i) = (1/N) sum_{i'=-N/2}^{N/2-1} e^{2 pi i i' (xi - i)/N}
+        auto interp = [&](int N, int lo, int cells, bool transposed, std::vector<cd>& out) {
+            out.assign((size_t)N * cells * G, cd(0, 0));
+            for (int l = 0; l < cells; ++l)
+                for (int gq = 0; gq < G; ++gq) {
+                    const double xi_ = lo + l + 0.5 + 0.5 * g->gl_x[gq];
+                    for (int i = 0; i < N; ++i) {
+                        const double th = 2.0 * kPi * (xi_ - i) / N;
+                        // geometric sum e^{-i th N/2} (e^{i th N} - 1) / (e^{i th} - 1)
+                        const cd num = std::exp(cd(0, th * N)) - 1.0;
+                        const cd den = std::exp(cd(0, th)) - 1.0;
+                        const cd v = std::exp(cd(0, -th * (N / 2))) * num / den / double(N);
+                        const size_t row = (size_t)l * G + gq;
+                        if (transposed) out[(size_t)i * cells * G + row] = v;
+                        else out[row * N + i] = v;
+                    }
+                }
+        };
+        std::vector<cd> mb, mc;
+        interp(F.Nb, d.huygens_lo[F.b], F.L, true, mb);    // [Nb][L G]
+        interp(F.Nc, d.huygens_lo[F.c], F.M, false, mc);   // [M G][Nc]
+        CK(g, dalloc(&g->MbT[f], mb.size() * 16));
+        CK(g, dalloc(&g->Mc[f], mc.size() * 16));
+        CK(g, cudaMemcpy(g->MbT[f], mb.data(), mb.size() * 16, cudaMemcpyHostToDevice));
+        CK(g, cudaMemcpy(g->Mc[f], mc.data(), mc.size() * 16, cudaMemcpyHostToDevice));
+        t1max = std::max(t1max, (size_t)F.Nc * F.L * G);
+        outmax = std::max(outmax, (size_t)F.M * G * F.L * G);
+    }
+    g->ncells = cell0;
+    CK(g, dalloc(&g->T1, t1max * 16));
+    CK(g, dalloc(&g->OutP, outmax * 16));
+    CK(g, dalloc(&g->OutD, outmax * 16));
+    if (dalloc(&g->rec, (size_t)g->ncells * 2 * G * G * g->csize) != cudaSuccess)
+        return fail(g, PSTD_ENOMEM, "transform records");
+    return PSTD_OK;
+}
+
+pstd_status check_window(pstd_grid* g, int b, int f)
+{
+    pstd_status st = check_member(g, b);
+    if (st != PSTD_OK) return st;
+    const MemberHost& m = g->mem[b];
+    if (f < 0 || f >= m.nfreq) return fail(g, PSTD_EINVAL, "frequency index out of range");
+    if (m.len <= 0 || m.accumulated < m.len) return fail(g, PSTD_ESTATE, "the DFT window has not completed");
+    if (std::abs(m.inc_phasor[f]) == 0.0) return fail(g, PSTD_ESTATE, "incident phasor at r_O is zero");
+    return PSTD_OK;
+}
+
+template <typename R> pstd_status prepare_records(pstd_grid* g, int b, int f)
+{
+    pstd_status st = setup_transform(g);
+    if (st != PSTD_OK) return st;
+    if (g->rec_member == b && g->rec_freq == f && g->rec_version == g->phasor_version) return PSTD_OK;
+    const MemberHost& m = g->mem[b];
+    const cd scale = 1.0 / m.inc_phasor[f];   // Eqs. scaledphsiphasor, scaleddpsiphasor
+    const int G = g->G;
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const double2* base = g->acc + (long long)b * g->acc_freq_stride * g->acc_freq_cap + (long long)f * g->acc_freq_stride;
+    for (int fi = 0; fi < 6; ++fi) {
+        const FaceGeom& F = g->faces[fi];
+        const int LG = F.L * G, MG = F.M * G;
+        for (int q = 0; q < 2; ++q) {
+            const double2* P = base + g->face_off[fi] + q * g->face_size[fi];   // [Nc][Nb]
+            double2* out = q == 0 ? g->OutP : g->OutD;
+            Timer t(g, 4);
+            CK(g, launch_zgemm(F.Nc, LG, F.Nb, P, F.Nb, g->MbT[fi], LG, g->T1, LG, make_double2(scale.real(), scale.imag()),
+                               g->stream));
+            CK(g, launch_zgemm(MG, LG, F.Nc, g->Mc[fi], F.Nc, g->T1, LG, out, LG, make_double2(1.0, 0.0), g->stream));
+        }
+        Timer t(g, 4);
+        CK(g, launch_pack_records<R>(g->OutP, g->OutD, F.L, F.M, G, g->gl_w_dev, 0.25 * F.db * F.dc, F.cell0,
+                                     static_cast<C*>(g->rec), g->stream));
+    }
+    g->rec_member = b;
+    g->rec_freq = f;
+    g->rec_version = g->phasor_version;
+    return PSTD_OK;
+}
+
+template <typename R>
+pstd_status run_transform(pstd_grid* g, int b, int f, const double* pts, const double* theta, const double* phi, long M,
+                          double2* out, double* dsdo, bool far)
+{
+    pstd_status st = prepare_records<R>(g, b, f);
+    if (st != PSTD_OK) return st;
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    TransformArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.rec = static_cast<const C*>(g->rec);
+    a.ncells = g->ncells;
+    for (int fi = 0; fi < 6; ++fi) a.face[fi] = g->faces[fi];
+    a.pts = pts;
+    a.theta = theta;
+    a.phi = phi;
+    a.M = M;
+    a.k = g->mem[b].k;
+    for (int q = 0; q < g->G; ++q) a.gl_node[q] = g->gl_x[q];
+    const long long per_block = 256;
+    const long long blocks = (M + per_block - 1) / per_block;
+    const int CH = sizeof(R) == 4 ? 32 : 16;
+    const long long chunks = (g->ncells + CH - 1) / CH;
+    long long splits = std::max(1LL, std::min(chunks, (2LL * 152 + blocks - 1) / blocks));
+    splits = std::min(splits, 4096LL);
+    long long cps = ((g->ncells + splits - 1) / splits + CH - 1) / CH * CH;
+    splits = (g->ncells + cps - 1) / cps;
+    a.cells_per_split = cps;
+    st = ensure(g, &g->partial, g->partial_cap, (size_t)splits * M * sizeof(double2));
+    if (st != PSTD_OK) return st;
+    a.partial = g->partial;
+    {
+        Timer t(g, far ? 6 : 5);
+        CK(g, launch_transform<R>(a, g->G, (int)splits, far, g->stream));
+    }
+    {
+        Timer t(g, far ? 6 : 5);
+        CK(g, launch_reduce_partials(g->partial, (int)splits, M, out, dsdo, g->stream));
+    }
+    return PSTD_OK;
+}
+
+}  // namespace
+
+// =====================================================================================
+// C ABI
+// =====================================================================================
+extern "C" {
+
+pstd_status pstd_create_grid(const pstd_grid_desc* desc, pstd_grid** out)
+{
+    if (!out) return fail(nullptr, PSTD_EINVAL, "null output pointer");
+    *out = nullptr;
+    pstd_status st = validate(desc);
+    if (st != PSTD_OK) return st;
+    if (desc->dt > dt_bound(*desc, 0.0)) return fail(nullptr, PSTD_EUNSTABLE, "dt above the stability bound (Eq. PSTDstability)");
+    pstd_grid* g = new pstd_grid();
+    g->desc = *desc;
+    if (cudaGetDevice(&g->dev) != cudaSuccess) {
+        delete g;
+        return fail(nullptr, PSTD_ECUDA, "no CUDA device");
+    }
+    g->stream = static_cast<cudaStream_t>(desc->stream);
+    g->prec = desc->precision;
+    g->rsize = g->prec == PSTD_F64 ? 8 : 4;
+    g->csize = 2 * g->rsize;
+    g->ncell = (long long)desc->n[0] * desc->n[1] * desc->n[2];
+    g->batch = desc->batch;
+    g->mem.assign(g->batch, MemberHost());
+    const size_t sbytes = (size_t)g->batch * g->ncell * g->csize;
+    auto cleanup_fail = [&](pstd_status s, const char* msg) {
+        g_create_error = g->err.empty() ? msg : g->err;
+        pstd_destroy_grid(g);
+        return s;
+    };
+    for (int i = 0; i < 2; ++i)
+        if (dalloc(&g->buf[i], sbytes) != cudaSuccess) return cleanup_fail(PSTD_ENOMEM, "state allocation failed");
+    if (dalloc(&g->flag, sizeof(int)) != cudaSuccess || dalloc(&g->mem_dev, sizeof(MemberDev) * g->batch) != cudaSuccess)
+        return cleanup_fail(PSTD_ENOMEM, "allocation failed");
+    // 1-D tables (double precision on the host, rounded once to the grid precision)
+    for (int a = 0; a < 3; ++a) {
+        const int n = desc->n[a];
+        std::vector<cd> tw(n);
+        std::vector<double> kin(n), ones(n, 1.0), z, z1, z2;
+        for (int m = 0; m < n; ++m) {
+            tw[m] = std::exp(cd(0.0, -2.0 * kPi * m / n));
+            const double km = wavenumber(n, desc->d[a], m);
+            kin[m] = desc->dt * desc->hbar / desc->mass * km * km / n;
+        }
+        zeta_tables(*desc, a, z, z1, z2);
+        // spectral-derivative weights for the two virtual planes normal to this axis
+        std::vector<cd> dw(2 * (size_t)n);
+        for (int s = 0; s < 2; ++s) {
+            const int h = s == 0 ? desc->huygens_lo[a] : desc->huygens_hi[a];
+            for (int q = 0; q < n; ++q) {
+                cd acc(0, 0);
+                for (int m = 0; m < n; ++m) {
+                    const double km = wavenumber(n, desc->d[a], m);
+                    acc += cd(0.0, km) * std::exp(cd(0.0, 2.0 * kPi * (double)m * (h - q) / n));
+                }
+                dw[(size_t)s * n + q] = acc / double(n);
+            }
+        }
+        if (upload_complex(g, &g->tw[a], tw) || upload_real(g, &g->kin[a], kin) || upload_real(g, &g->mask[a], ones) ||
+            upload_real(g, &g->zeta[a], z) || upload_real(g, &g->zeta1[a], z1) || upload_real(g, &g->zeta2[a], z2) ||
+            upload_complex(g, &g->dw[a], dw) ||
+            upload_complex(g, &g->phase[a], std::vector<cd>((size_t)n * g->batch, cd(1.0, 0.0))))
+            return cleanup_fail(PSTD_ENOMEM, "table allocation failed");
+    }
+    // one dummy potential element so the pointer is never null
+    if (upload_real(g, &g->V, std::vector<double>(1, 0.0)) != PSTD_OK) return cleanup_fail(PSTD_ENOMEM, "allocation failed");
+    // face geometry for the DFT accumulators: plane sizes in face order
+    long long off = 0;
+    for (int f = 0; f < 6; ++f) {
+        const int a = f / 2;
+        const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+        g->face_size[f] = (long long)desc->n[b] * desc->n[c];
+        g->face_off[f] = off;
+        off += 2 * g->face_size[f];
+    }
+    g->acc_freq_stride = off;
+    if (upload_members(g) != PSTD_OK) return cleanup_fail(PSTD_ECUDA, "member upload failed");
+    pstd_status r = pstd_reset(g);
+    if (r != PSTD_OK) return cleanup_fail(r, "reset failed");
+    *out = g;
+    return PSTD_OK;
+}
+
+pstd_status pstd_destroy_grid(pstd_grid* g)
+{
+    if (!g) return PSTD_OK;
+    DeviceGuard dg(g->dev);
+    cudaStreamSynchronize(g->stream);
+    for (void* p : {g->buf[0], g->buf[1], g->V, (void*)g->mem_dev, (void*)g->acc, (void*)g->flag, (void*)g->gl_w_dev,
+                    (void*)g->T1, (void*)g->OutP, (void*)g->OutD, g->rec, (void*)g->partial, (void*)g->pts_dev,
+                    (void*)g->out_dev, (void*)g->dsdo_dev})
+        if (p) cudaFree(p);
+    for (int a = 0; a < 3; ++a)
+        for (void* p : {g->tw[a], g->kin[a], g->mask[a], g->zeta[a], g->zeta1[a], g->zeta2[a], g->phase[a], g->dw[a]})
+            if (p) cudaFree(p);
+    for (int f = 0; f < 6; ++f) {
+        if (g->MbT[f]) cudaFree(g->MbT[f]);
+        if (g->Mc[f]) cudaFree(g->Mc[f]);
+    }
+    for (auto& t : g->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
+    for (auto e : g->event_pool) cudaEventDestroy(e);
+    delete g;
+    return PSTD_OK;
+}
+
+pstd_status pstd_reset(pstd_grid* g)
+{
+    if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
+    DeviceGuard dg(g->dev);
+    const size_t sbytes = (size_t)g->batch * g->ncell * g->csize;
+    CK(g, cudaMemsetAsync(g->buf[0], 0, sbytes, g->stream));
+    CK(g, cudaMemsetAsync(g->buf[1], 0, sbytes, g->stream));
+    CK(g, cudaMemsetAsync(g->flag, 0, sizeof(int), g->stream));
+    if (g->acc) CK(g, cudaMemsetAsync(g->acc, 0, sizeof(double2) * g->acc_freq_stride * g->acc_freq_cap * g->batch, g->stream));
+    for (auto& m : g->mem) {
+        m.accumulated = 0;
+        for (auto& p : m.inc_phasor) p = cd(0, 0);
+    }
+    g->n = 0;
+    g->cur = 0;
+    ++g->phasor_version;
+    return PSTD_OK;
+}
+
+pstd_status pstd_set_potential(pstd_grid* g, const void* V, int mem, int dtype)
+{
+    if (!g || !V) return fail(g, PSTD_EINVAL, "null argument");
+    DeviceGuard dg(g->dev);
+    if (dtype != PSTD_DTYPE_F32 && dtype != PSTD_DTYPE_F64) return fail(g, PSTD_EINVAL, "dtype");
+    const pstd_grid_desc& d = g->desc;
+    const size_t n = (size_t)g->ncell;
+    std::vector<double> h(n);
+    if (mem == PSTD_MEM_HOST) {
+        if (dtype == PSTD_DTYPE_F64) std::memcpy(h.data(), V, n * 8);
+        else for (size_t i = 0; i < n; ++i) h[i] = static_cast<const float*>(V)[i];
+    } else if (mem == PSTD_MEM_DEVICE) {
+        CK(g, cudaStreamSynchronize(g->stream));
+        if (dtype == PSTD_DTYPE_F64) CK(g, cudaMemcpy(h.data(), V, n * 8, cudaMemcpyDeviceToHost));
+        else {
+            std::vector<float> f(n);
+            CK(g, cudaMemcpy(f.data(), V, n * 4, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < n; ++i) h[i] = f[i];
+        }
+    } else {
+        return fail(g, PSTD_EINVAL, "mem");
+    }
+    int lo[3] = {d.n[0], d.n[1], d.n[2]}, hi[3] = {-1, -1, -1};
+    double vmax = 0;
+    int core_lo[3], core_hi[3];
+    for (int a = 0; a < 3; ++a) {
+        core_lo[a] = d.tfsf_lo[a] + d.taper_cells;
+        core_hi[a] = d.tfsf_hi[a] - d.taper_cells;
+    }
+    for (int k = 0; k < d.n[2]; ++k)
+        for (int j = 0; j < d.n[1]; ++j)
+            for (int i = 0; i < d.n[0]; ++i) {
+                const double v = h[((size_t)k * d.n[1] + j) * d.n[0] + i];
+                if (!std::isfinite(v)) return fail(g, PSTD_EINVAL, "V is not finite");
+                if (v == 0.0) continue;
+                if (i < core_lo[0] || i > core_hi[0] || j < core_lo[1] || j > core_hi[1] || k < core_lo[2] || k > core_hi[2])
+                    return fail(g, PSTD_EINVAL, "V must vanish outside the zeta == 1 core ((zeta - 1) V = 0)");
+                lo[0] = std::min(lo[0], i); hi[0] = std::max(hi[0], i);
+                lo[1] = std::min(lo[1], j); hi[1] = std::max(hi[1], j);
+                lo[2] = std::min(lo[2], k); hi[2] = std::max(hi[2], k);
+                vmax = std::max(vmax, std::fabs(v));
+            }
+    if (d.dt > dt_bound(d, vmax)) return fail(g, PSTD_EUNSTABLE, "dt above the stability bound with this |V|max (Eq. PSTDstability)");
+    std::vector<double> box;
+    if (hi[0] < 0) {   // V == 0 everywhere
+        for (int a = 0; a < 3; ++a) { g->vlo[a] = 0; g->vhi[a] = 0; }
+        box.assign(1, 0.0);
+    } else {
+        for (int a = 0; a < 3; ++a) { g->vlo[a] = lo[a]; g->vhi[a] = hi[a] + 1; }
+        const int bx = g->vhi[0] - g->vlo[0], by = g->vhi[1] - g->vlo[1], bz = g->vhi[2] - g->vlo[2];
+        box.resize((size_t)bx * by * bz);
+        for (int k = 0; k < bz; ++k)
+            for (int j = 0; j < by; ++j)
+                for (int i = 0; i < bx; ++i)
+                    box[((size_t)k * by + j) * bx + i] = h[((size_t)(k + lo[2]) * d.n[1] + (j + lo[1])) * d.n[0] + (i + lo[0])];
+    }
+    CK(g, cudaStreamSynchronize(g->stream));
+    if (g->V) { cudaFree(g->V); g->V = nullptr; }
+    pstd_status st = upload_real(g, &g->V, box);
+    if (st != PSTD_OK) return st;
+    g->vmax = vmax;
+    return PSTD_OK;
+}
+
+pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double k, int envelope, double ramp_time)
+{
+    if (!g || !khat) return fail(g, PSTD_EINVAL, "null argument");
+    DeviceGuard dg(g->dev);
+    pstd_status st = check_member(g, b);
+    if (st != PSTD_OK) return st;
+    if (envelope != PSTD_ENV_CW_RAMP) return fail(g, PSTD_EINVAL, "envelope");
+    const double nrm = std::sqrt(khat[0] * khat[0] + khat[1] * khat[1] + khat[2] * khat[2]);
+    if (!(k > 0) || !(nrm > 0) || !(ramp_time >= 0)) return fail(g, PSTD_EINVAL, "k, khat or ramp_time");
+    const pstd_grid_desc& d = g->desc;
+    MemberHost& m = g->mem[b];
+    m.has_inc = true;
+    for (int a = 0; a < 3; ++a) m.khat[a] = khat[a] / nrm;
+    m.k = k;
+    m.E = d.hbar * d.hbar * k * k / (2.0 * d.mass);
+    m.w0 = m.E / d.hbar;
+    const double x = m.E * d.dt / d.hbar;
+    m.eta = x == 0 ? 1.0 : std::sin(x) / x;   // Eq. numdis2
+    m.ramp = ramp_time;
+    // first-contact corner: the TF/SF box corner minimising khat . r (Eq. Oinc)
+    double best = 0;
+    bool first = true;
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+                const double c[3] = {coord(d, 0, cx ? d.tfsf_hi[0] : d.tfsf_lo[0]), coord(d, 1, cy ? d.tfsf_hi[1] : d.tfsf_lo[1]),
+                                     coord(d, 2, cz ? d.tfsf_hi[2] : d.tfsf_lo[2])};
+                const double v = m.khat[0] * c[0] + m.khat[1] * c[1] + m.khat[2] * c[2];
+                if (first || v < best - 1e-12) {
+                    best = v;
+                    first = false;
+                    for (int a = 0; a < 3; ++a) m.rO[a] = c[a];
+                }
+            }
+    for (int a = 0; a < 3; ++a) {
+        const int n = d.n[a];
+        std::vector<cd> ph(n);
+        for (int i = 0; i < n; ++i) ph[i] = std::exp(cd(0.0, k * m.khat[a] * (coord(d, a, i) - m.rO[a])));
+        st = upload_complex(g, &g->phase[a], ph, (size_t)b * n, (size_t)n * g->batch);
+        if (st != PSTD_OK) return st;
+    }
+    if (b == 0) {   // absorber strength is expressed in units of member 0's E / hbar
+        for (int a = 0; a < 3; ++a) {
+            std::vector<double> gam = absorber_gamma(d, a, m.E), msk(d.n[a]);
+            for (int i = 0; i < d.n[a]; ++i) msk[i] = std::exp(-gam[i] * d.dt);
+            st = upload_real(g, &g->mask[a], msk);
+            if (st != PSTD_OK) return st;
+        }
+        g->mask_ready = true;
+    }
+    return upload_members(g);
+}
+
+pstd_status pstd_huygens_dft(pstd_grid* g, int b, const double* omega, int nfreq, long first_step, long n_steps)
+{
+    if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
+    DeviceGuard dg(g->dev);
+    if (nfreq < 0 || nfreq > PSTD_MAX_FREQ || (nfreq > 0 && !omega)) return fail(g, PSTD_EINVAL, "nfreq");
+    if (first_step < 0 || n_steps < 0) return fail(g, PSTD_EINVAL, "window");
+    if (b < -1 || b >= g->batch) return fail(g, PSTD_EINVAL, "batch member out of range");
+    if (nfreq > g->acc_freq_cap) {
+        CK(g, cudaStreamSynchronize(g->stream));
+        if (g->acc) cudaFree(g->acc);
+        g->acc = nullptr;
+        const size_t bytes = sizeof(double2) * g->acc_freq_stride * nfreq * g->batch;
+        if (dalloc(&g->acc, bytes) != cudaSuccess) return fail(g, PSTD_ENOMEM, "DFT accumulators");
+        CK(g, cudaMemsetAsync(g->acc, 0, bytes, g->stream));
+        g->acc_freq_cap = nfreq;
+        for (auto& m : g->mem) { m.accumulated = 0; for (auto& p : m.inc_phasor) p = cd(0, 0); }
+    }
+    for (int mb = 0; mb < g->batch; ++mb) {
+        if (b >= 0 && mb != b) continue;
+        MemberHost& m = g->mem[mb];
+        m.nfreq = nfreq;
+        for (int f = 0; f < PSTD_MAX_FREQ; ++f) m.omega[f] = f < nfreq ? omega[f] : 0.0;
+        m.first = first_step;
+        m.len = n_steps;
+        m.accumulated = 0;
+        for (auto& p : m.inc_phasor) p = cd(0, 0);
+        if (g->acc)
+            CK(g, cudaMemsetAsync(g->acc + (size_t)mb * g->acc_freq_stride * g->acc_freq_cap, 0,
+                                  sizeof(double2) * g->acc_freq_stride * g->acc_freq_cap, g->stream));
+    }
+    ++g->phasor_version;
+    return upload_members(g);
+}
+
+pstd_status pstd_step(pstd_grid* g, long nsteps)
+{
+    if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
+    if (nsteps < 0) return fail(g, PSTD_EINVAL, "nsteps");
+    DeviceGuard dg(g->dev);
+    for (int b = 0; b < g->batch; ++b)
+        if (!g->mem[b].has_inc) return fail(g, PSTD_ESTATE, "every batch member needs pstd_set_incidence before stepping");
+    return g->prec == PSTD_F64 ? run_steps<double>(g, nsteps) : run_steps<float>(g, nsteps);
+}
+
+pstd_status pstd_transform_to_points(pstd_grid* g, int b, int f, const double* xyz, long M, void* out_psi, int mem)
+{
+    if (!g || (M > 0 && (!xyz || !out_psi))) return fail(g, PSTD_EINVAL, "null argument");
+    if (M < 0) return fail(g, PSTD_EINVAL, "M");
+    DeviceGuard dg(g->dev);
+    pstd_status st = check_window(g, b, f);
+    if (st != PSTD_OK) return st;
+    if (M == 0) return PSTD_OK;
+    if (mem != PSTD_MEM_HOST && mem != PSTD_MEM_DEVICE) return fail(g, PSTD_EINVAL, "mem");
+    const double* pts = xyz;
+    double2* out = static_cast<double2*>(out_psi);
+    if (mem == PSTD_MEM_HOST) {
+        st = ensure(g, &g->pts_dev, g->pts_cap, sizeof(double) * 3 * M);
+        if (st != PSTD_OK) return st;
+        st = ensure(g, &g->out_dev, g->out_cap, sizeof(double2) * M);
+        if (st != PSTD_OK) return st;
+        CK(g, cudaMemcpyAsync(g->pts_dev, xyz, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, g->stream));
+        pts = g->pts_dev;
+        out = g->out_dev;
+    }
+    st = g->prec == PSTD_F64 ? run_transform<double>(g, b, f, pts, nullptr, nullptr, M, out, nullptr, false)
+                             : run_transform<float>(g, b, f, pts, nullptr, nullptr, M, out, nullptr, false);
+    if (st != PSTD_OK) return st;
+    if (mem == PSTD_MEM_HOST) return copy_out(g, out_psi, g->out_dev, sizeof(double2) * M, PSTD_MEM_HOST);
+    return PSTD_OK;
+}
+
+pstd_status pstd_cross_section(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M, double* out_dsdo,
+                               void* out_f, int mem)
+{
+    if (!g || (M > 0 && (!theta || !phi || !out_dsdo))) return fail(g, PSTD_EINVAL, "null argument");
+    if (M < 0) return fail(g, PSTD_EINVAL, "M");
+    DeviceGuard dg(g->dev);
+    pstd_status st = check_window(g, b, f);
+    if (st != PSTD_OK) return st;
+    if (M == 0) return PSTD_OK;
+    if (mem != PSTD_MEM_HOST && mem != PSTD_MEM_DEVICE) return fail(g, PSTD_EINVAL, "mem");
+    const double *th = theta, *ph = phi;
+    double2* fo = static_cast<double2*>(out_f);
+    double* ds = out_dsdo;
+    if (mem == PSTD_MEM_HOST) {
+        st = ensure(g, &g->pts_dev, g->pts_cap, sizeof(double) * 2 * M);
+        if (st != PSTD_OK) return st;
+        st = ensure(g, &g->out_dev, g->out_cap, sizeof(double2) * M);
+        if (st != PSTD_OK) return st;
+        st = ensure(g, &g->dsdo_dev, g->dsdo_cap, sizeof(double) * M);
+        if (st != PSTD_OK) return st;
+        CK(g, cudaMemcpyAsync(g->pts_dev, theta, sizeof(double) * M, cudaMemcpyHostToDevice, g->stream));
+        CK(g, cudaMemcpyAsync(g->pts_dev + M, phi, sizeof(double) * M, cudaMemcpyHostToDevice, g->stream));
+        th = g->pts_dev;
+        ph = g->pts_dev + M;
+        fo = g->out_dev;
+        ds = g->dsdo_dev;
+    } else if (!fo) {
+        st = ensure(g, &g->out_dev, g->out_cap, sizeof(double2) * M);
+        if (st != PSTD_OK) return st;
+        fo = g->out_dev;
+    }
+    st = g->prec == PSTD_F64 ? run_transform<double>(g, b, f, nullptr, th, ph, M, fo, ds, true)
+                             : run_transform<float>(g, b, f, nullptr, th, ph, M, fo, ds, true);
+    if (st != PSTD_OK) return st;
+    if (mem == PSTD_MEM_HOST) {
+        CK(g, cudaMemcpyAsync(out_dsdo, g->dsdo_dev, sizeof(double) * M, cudaMemcpyDeviceToHost, g->stream));
+        if (out_f) CK(g, cudaMemcpyAsync(out_f, g->out_dev, sizeof(double2) * M, cudaMemcpyDeviceToHost, g->stream));
+        CK(g, cudaStreamSynchronize(g->stream));
+    }
+    return PSTD_OK;
+}
+
+pstd_status pstd_get_field(pstd_grid* g, int b, int which, void* out, int mem)
+{
+    if (!g || !out) return fail(g, PSTD_EINVAL, "null argument");
+    DeviceGuard dg(g->dev);
+    pstd_status st = check_member(g, b);
+    if (st != PSTD_OK) return st;
+    const size_t bytes = (size_t)g->ncell * g->csize;
+    if (which == PSTD_FIELD_CURRENT || which == PSTD_FIELD_SCATTERED) {
+        const char* src = static_cast<const char*>(g->buf[g->cur]) + (size_t)b * bytes;
+        st = copy_out(g, out, src, bytes, mem);
+        if (st != PSTD_OK || which == PSTD_FIELD_CURRENT || g->desc.tfsf_mode == PSTD_TFSF_EXACT) return st;
+        // PAPER form: subtract zeta psi_inc^n on the host copy
+        if (mem != PSTD_MEM_HOST) return fail(g, PSTD_EINVAL, "PSTD_FIELD_SCATTERED of the PAPER form needs host memory");
+        const pstd_grid_desc& d = g->desc;
+        const MemberHost& m = g->mem[b];
+        std::vector<double> z[3], z1, z2;
+        for (int a = 0; a < 3; ++a) zeta_tables(d, a, z[a], z1, z2);
+        const double t = g->n * d.dt;
+        const double env = (m.ramp <= 0 || t >= m.ramp) ? 1.0 : (t <= 0 ? 0.0 : 0.5 * (1.0 - std::cos(kPi * t / m.ramp)));
+        const cd s = env * std::exp(cd(0.0, -m.w0 * t));
+        for (int k = 0; k < d.n[2]; ++k)
+            for (int j = 0; j < d.n[1]; ++j)
+                for (int i = 0; i < d.n[0]; ++i) {
+                    const double zz = z[0][i] * z[1][j] * z[2][k];
+                    if (zz == 0.0) continue;
+                    const double r[3] = {coord(d, 0, i), coord(d, 1, j), coord(d, 2, k)};
+                    double ph = 0;
+                    for (int a = 0; a < 3; ++a) ph += m.k * m.khat[a] * (r[a] - m.rO[a]);
+                    const cd v = zz * s * std::exp(cd(0.0, ph));
+                    const size_t idx = ((size_t)k * d.n[1] + j) * d.n[0] + i;
+                    if (g->prec == PSTD_F64) {
+                        double* o = static_cast<double*>(out) + 2 * idx;
+                        o[0] -= v.real(); o[1] -= v.imag();
+                    } else {
+                        float* o = static_cast<float*>(out) + 2 * idx;
+                        o[0] -= (float)v.real(); o[1] -= (float)v.imag();
+                    }
+                }
+        return PSTD_OK;
+    }
+    if (which == PSTD_FIELD_PREVIOUS) {
+        const char* src = static_cast<const char*>(g->buf[g->cur ^ 1]) + (size_t)b * bytes;
+        return copy_out(g, out, src, bytes, mem);
+    }
+    return fail(g, PSTD_EINVAL, "which");
+}
+
+pstd_status pstd_set_field(pstd_grid* g, int b, const void* prev, const void* cur, long n, int mem)
+{
+    if (!g || !prev || !cur) return fail(g, PSTD_EINVAL, "null argument");
+    DeviceGuard dg(g->dev);
+    pstd_status st = check_member(g, b);
+    if (st != PSTD_OK) return st;
+    if (n < 0) return fail(g, PSTD_EINVAL, "n");
+    const size_t bytes = (size_t)g->ncell * g->csize;
+    st = copy_in(g, static_cast<char*>(g->buf[g->cur]) + (size_t)b * bytes, cur, bytes, mem);
+    if (st != PSTD_OK) return st;
+    st = copy_in(g, static_cast<char*>(g->buf[g->cur ^ 1]) + (size_t)b * bytes, prev, bytes, mem);
+    if (st != PSTD_OK) return st;
+    g->n = n;
+    ++g->phasor_version;
+    if (mem == PSTD_MEM_HOST) CK(g, cudaStreamSynchronize(g->stream));
+    return PSTD_OK;
+}
+
+pstd_status pstd_get_phasors(pstd_grid* g, int b, int f, void* out, int mem)
+{
+    if (!g || !out) return fail(g, PSTD_EINVAL, "null argument");
+    DeviceGuard dg(g->dev);
+    pstd_status st = check_window(g, b, f);
+    if (st != PSTD_OK) return st;
+    // scale on the host (small): copy raw, divide by the incident phasor at r_O
+    const size_t count = (size_t)g->acc_freq_stride;
+    std::vector<cd> h(count);
+    const double2* src = g->acc + (size_t)b * g->acc_freq_stride * g->acc_freq_cap + (size_t)f * g->acc_freq_stride;
+    CK(g, cudaMemcpyAsync(h.data(), src, count * 16, cudaMemcpyDeviceToHost, g->stream));
+    CK(g, cudaStreamSynchronize(g->stream));
+    const cd s = 1.0 / g->mem[b].inc_phasor[f];
+    for (auto& v : h) v *= s;
+    if (mem == PSTD_MEM_HOST) {
+        std::memcpy(out, h.data(), count * 16);
+        return PSTD_OK;
+    }
+    if (mem == PSTD_MEM_DEVICE) {
+        CK(g, cudaMemcpyAsync(out, h.data(), count * 16, cudaMemcpyHostToDevice, g->stream));
+        CK(g, cudaStreamSynchronize(g->stream));
+        return PSTD_OK;
+    }
+    return fail(g, PSTD_EINVAL, "mem");
+}
+
+pstd_status pstd_synchronize(pstd_grid* g)
+{
+    if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
+    DeviceGuard dg(g->dev);
+    CK(g, cudaStreamSynchronize(g->stream));
+    int flag = 0;
+    CK(g, cudaMemcpy(&flag, g->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & 1) {
+        CK(g, cudaMemset(g->flag, 0, sizeof(int)));
+        return fail(g, PSTD_ENONFINITE, "the state became non-finite");
+    }
+    return PSTD_OK;
+}
+
+pstd_status pstd_get_step(pstd_grid* g, long* n)
+{
+    if (!g || !n) return fail(g, PSTD_EINVAL, "null argument");
+    *n = (long)g->n;
+    return PSTD_OK;
+}
+
+pstd_status pstd_stability_dt_max(const pstd_grid_desc* desc, double vmax, double* out_dt)
+{
+    if (!desc || !out_dt) return fail(nullptr, PSTD_EINVAL, "null argument");
+    for (int a = 0; a < 3; ++a)
+        if (!(desc->d[a] > 0)) return fail(nullptr, PSTD_EINVAL, "spacing");
+    if (!(desc->hbar > 0) || !(desc->mass > 0)) return fail(nullptr, PSTD_EINVAL, "hbar, mass");
+    *out_dt = dt_bound(*desc, vmax);
+    return PSTD_OK;
+}
+
+pstd_status pstd_set_timing(pstd_grid* g, int enable)
+{
+    if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
+    DeviceGuard dg(g->dev);
+    CK(g, cudaStreamSynchronize(g->stream));
+    for (auto& t : g->timed) { g->event_pool.push_back(t.a); g->event_pool.push_back(t.b); }
+    g->timed.clear();
+    g->timing = enable != 0;
+    return PSTD_OK;
+}
+
+pstd_status pstd_kernel_stats(pstd_grid* g, int kernel_id, long* launches, double* total_ms)
+{
+    if (!g || !launches || !total_ms) return fail(g, PSTD_EINVAL, "null argument");
+    if (kernel_id < 0 || kernel_id >= kKernelIds) return fail(g, PSTD_EINVAL, "kernel id");
+    DeviceGuard dg(g->dev);
+    CK(g, cudaStreamSynchronize(g->stream));
+    long c = 0;
+    double ms = 0;
+    for (auto& t : g->timed) {
+        if (t.kernel != kernel_id) continue;
+        float e = 0;
+        CK(g, cudaEventElapsedTime(&e, t.a, t.b));
+        ms += e;
+        ++c;
+    }
+    *launches = c;
+    *total_ms = ms;
+    return PSTD_OK;
+}
+
+pstd_status pstd_launch_count(pstd_grid* g, long* count)
+{
+    if (!g || !count) return fail(g, PSTD_EINVAL, "null argument");
+    *count = (long)g->launches;
+    return PSTD_OK;
+}
+
+const char* pstd_last_error(const pstd_grid* g)
+{
+    return g ? g->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// Internal declarations shared by the C ABI (api.cu) and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "pstd.h"
+
+namespace pstd {
+
+// Per-member constants read by the kernels (device array, uploaded by pstd_set_incidence).
+struct MemberDev {
+    double w0;      // E / hbar of the incident wave
+    double ramp;    // raised-cosine switch-on time
+    double eta;     // sinc(E dt / hbar), Eq. numdis2
+    double k[3];    // wave vector k * khat
+    double omega[PSTD_MAX_FREQ];   // DFT angular frequencies
+    int nfreq;
+    int dft_active; // set per step by the host (bit mask passed separately)
+};
+
+// Everything the step passes need; one struct per grid, passed by value.
+template <typename R> struct StepArgs {
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const C* cur;
+    C* prev;
+    int nx, ny, nz;
+    long long ncell;
+    const C* tw[3];          // w_N^m = e^{-2 pi i m / N} per axis
+    const R* kin[3];         // dt hbar k_m^2 / (m N) per axis, FFT index order
+    const R* mask[3];        // exp(-gamma dt) per axis
+    const R* V;              // potential on its support box [vlo, vhi)
+    int vlo[3], vhi[3];
+    const C* phase[3];       // exp(i k_a (x_a - r_O,a)) per member per axis: [b * n_a + i]
+    const R* zeta[3];        // taper and its first two derivatives per axis (PAPER form)
+    const R* zeta1[3];
+    const R* zeta2[3];
+    int tf_lo[3], tf_hi[3];
+    const MemberDev* mem;
+    long long step;          // n: index of the current state
+    double dt, hbar, mass;
+    int mode;                // PSTD_TFSF_EXACT / PSTD_TFSF_PAPER
+    int* flag;               // bit 0: non-finite value written
+};
+
+// Plane DFT arguments (one launch per axis).
+template <typename R> struct DftArgs {
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const C* cur;
+    int nx, ny, nz;
+    long long ncell;
+    int axis;
+    int h[2];                 // node indices of the two planes normal to `axis`
+    const C* dw;              // [2][N_axis] spectral-derivative weights for the two planes
+    double2* acc;             // accumulators, see Grid::acc_offset
+    long long acc_member_stride;   // doubles2 per member
+    long long acc_freq_stride;     // per frequency
+    long long face_off[6];         // offset of face (psi plane) within a frequency block
+    long long face_size[6];
+    const MemberDev* mem;
+    unsigned long long member_mask;
+    long long step;
+    double dt;
+};
+
+template <typename R> cudaError_t launch_xpass(const StepArgs<R>& a, int batch, cudaStream_t s);
+template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, int batch, cudaStream_t s);
+template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, int batch, cudaStream_t s);
+template <typename R> cudaError_t launch_plane_dft(const DftArgs<R>& a, int batch, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------
+// surface-equivalence transform
+// ---------------------------------------------------------------------------------
+struct FaceGeom {
+    int axis, b, c;           // normal axis, fast and slow in-plane axes
+    double sigma;             // -1 low face, +1 high face
+    double plane;             // coordinate of the plane along `axis`
+    double db, dc;            // in-plane spacings
+    double cb0, cc0;          // centre coordinates of the first surface cell along b, c
+    int L, M;                 // surface cells along b, c
+    int Nb, Nc;               // plane size
+    long long cell0;          // index of the face's first cell in the global cell order
+};
+
+template <typename R> struct TransformArgs {
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const C* rec;             // per cell: G*G psi node values then G*G dpsi node values (weights folded in)
+    long long ncells;
+    FaceGeom face[6];
+    const double* pts;        // M x 3 points (or directions for the far field)
+    const double* theta;      // far field: angles (when pts == nullptr)
+    const double* phi;
+    long long M;
+    double k;
+    double gl_node[16];       // Gauss-Legendre nodes on [-1, 1]
+    long long cells_per_split;
+    double2* partial;         // [split][M]
+};
+
+template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, int G, int splits, bool far,
+                                                  cudaStream_t s);
+cudaError_t launch_reduce_partials(const double2* partial, int splits, long long M, double2* out,
+                                   double* dsdo, cudaStream_t s);
+// complex double GEMM C[MxN] = alpha * A[MxK] B[KxN] (row-major, leading dims given)
+cudaError_t launch_zgemm(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb, double2* C,
+                         int ldc, double2 alpha, cudaStream_t s);
+// gather node values into cell records: rec[(cell0 + m L + l) * 2GG + q GG + h G + g] = Out[(m G + h) * (L G) + l G + g] * w_g w_h * cw
+template <typename R> cudaError_t launch_pack_records(const double2* out_psi, const double2* out_dpsi, int L, int M,
+                                                     int G, const double* glw, double cw, long long cell0,
+                                                     typename std::conditional<sizeof(R) == 4, float2, double2>::type* rec,
+                                                     cudaStream_t s);
+
+}  // namespace pstd

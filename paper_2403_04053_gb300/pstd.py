@@ -1,0 +1,300 @@
+"""Python binding of the C ABI in include/pstd.h (argument marshalling only).
+
+Every computation runs in libpstd.so on the GPU; this module converts arguments
+(numpy arrays for host memory, torch CUDA tensors for device memory), calls the
+C entry points of the same names and turns status codes into exceptions.  There is
+no CPU fallback: if the library is missing or fails to load, the import raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_long, c_void_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpstd.so")
+
+F32, F64 = 0, 1
+MEM_HOST, MEM_DEVICE = 0, 1
+DTYPE_F32, DTYPE_F64 = 0, 1
+ABC_POLY, ABC_POSCHL_TELLER = 0, 1
+TFSF_EXACT, TFSF_PAPER = 0, 1
+ENV_CW_RAMP = 0
+FIELD_CURRENT, FIELD_PREVIOUS, FIELD_SCATTERED = 0, 1, 2
+MAX_FREQ = 4
+
+STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ESTATE", 6: "ENONFINITE", 7: "ETIMEOUT"}
+KERNELS = {"xpass": 0, "ypass": 1, "zpass": 2, "plane_dft": 3, "prepare": 4, "transform": 5, "far_field": 6}
+
+
+class PstdError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        self.code = STATUS.get(status, str(status))
+        super().__init__(f"{where}: PSTD_{self.code}: {message}")
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("n", c_int * 3), ("d", c_double * 3), ("dt", c_double), ("hbar", c_double), ("mass", c_double),
+        ("precision", c_int), ("batch", c_int), ("abc_cells", c_int * 3), ("abc_profile", c_int),
+        ("abc_param", c_double * 2), ("tfsf_lo", c_int * 3), ("tfsf_hi", c_int * 3), ("taper_cells", c_int),
+        ("tfsf_mode", c_int), ("huygens_lo", c_int * 3), ("huygens_hi", c_int * 3), ("stream", c_void_p),
+    ]
+
+
+_SIGS = {
+    "pstd_create_grid": (c_int, [POINTER(GridDesc), POINTER(c_void_p)]),
+    "pstd_destroy_grid": (c_int, [c_void_p]),
+    "pstd_set_potential": (c_int, [c_void_p, c_void_p, c_int, c_int]),
+    "pstd_set_incidence": (c_int, [c_void_p, c_int, POINTER(c_double), c_double, c_int, c_double]),
+    "pstd_reset": (c_int, [c_void_p]),
+    "pstd_huygens_dft": (c_int, [c_void_p, c_int, POINTER(c_double), c_int, c_long, c_long]),
+    "pstd_step": (c_int, [c_void_p, c_long]),
+    "pstd_transform_to_points": (c_int, [c_void_p, c_int, c_int, c_void_p, c_long, c_void_p, c_int]),
+    "pstd_cross_section": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_long, c_void_p, c_void_p, c_int]),
+    "pstd_get_field": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
+    "pstd_set_field": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_int]),
+    "pstd_get_phasors": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
+    "pstd_synchronize": (c_int, [c_void_p]),
+    "pstd_get_step": (c_int, [c_void_p, POINTER(c_long)]),
+    "pstd_stability_dt_max": (c_int, [POINTER(GridDesc), c_double, POINTER(c_double)]),
+    "pstd_set_timing": (c_int, [c_void_p, c_int]),
+    "pstd_kernel_stats": (c_int, [c_void_p, c_int, POINTER(c_long), POINTER(c_double)]),
+    "pstd_launch_count": (c_int, [c_void_p, POINTER(c_long)]),
+    "pstd_last_error": (ctypes.c_char_p, [c_void_p]),
+}
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpstd.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str, handle=None):
+    if status != 0:
+        msg = load_library().pstd_last_error(handle)
+        raise PstdError(status, where, msg.decode() if msg else "")
+
+
+def _default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+def _is_cuda_tensor(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(getattr(x, "is_cuda"))
+
+
+def _ptr(x, dtype=None):
+    """(pointer, mem, keep-alive) for a numpy array (host) or a torch CUDA tensor (device)."""
+    if _is_cuda_tensor(x):
+        if not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return c_void_p(x.data_ptr()), MEM_DEVICE, x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data_as(c_void_p), MEM_HOST, a
+
+
+def make_desc(spec, precision: int = F32, batch: int = 1, stream=None) -> GridDesc:
+    """Fill a pstd_grid_desc from a GridSpec-like object (see paper_2403_04053_gb300.inputs)."""
+    d = GridDesc()
+    d.n[:] = list(spec.n)
+    d.d[:] = list(spec.d)
+    d.dt, d.hbar, d.mass = spec.dt, spec.hbar, spec.mass
+    d.precision = precision
+    d.batch = batch
+    d.abc_cells[:] = list(spec.abc_cells)
+    d.abc_profile = ABC_POLY if spec.abc_profile == "poly" else ABC_POSCHL_TELLER
+    d.abc_param[:] = list(spec.abc_param)
+    d.tfsf_lo[:] = list(spec.tfsf_lo)
+    d.tfsf_hi[:] = list(spec.tfsf_hi)
+    d.taper_cells = spec.taper_cells
+    d.tfsf_mode = TFSF_EXACT if spec.tfsf_mode == "exact" else TFSF_PAPER
+    d.huygens_lo[:] = list(spec.huygens_lo)
+    d.huygens_hi[:] = list(spec.huygens_hi)
+    d.stream = stream
+    return d
+
+
+def stability_dt_max(spec, vmax: float) -> float:
+    out = c_double()
+    _check(load_library().pstd_stability_dt_max(byref(make_desc(spec)), vmax, byref(out)), "pstd_stability_dt_max")
+    return out.value
+
+
+class Grid:
+    """One pstd_grid: the state of `batch` incident waves on one internal model."""
+
+    def __init__(self, spec, precision: int = F32, batch: int = 1, stream="default"):
+        self.lib = load_library()
+        self.spec = spec
+        self.precision = precision
+        self.batch = batch
+        self.shape = tuple(spec.shape)
+        self.ncell = int(np.prod(self.shape))
+        self.cdtype = np.complex64 if precision == F32 else np.complex128
+        self.stream = _default_stream() if stream == "default" else stream
+        self.desc = make_desc(spec, precision, batch, self.stream)
+        h = c_void_p()
+        _check(self.lib.pstd_create_grid(byref(self.desc), byref(h)), "pstd_create_grid", None)
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pstd_destroy_grid(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _c(self, status, where):
+        _check(status, where, self.h)
+
+    # -- set-up ---------------------------------------------------------------------
+    def set_potential(self, V):
+        if _is_cuda_tensor(V):
+            dtype = DTYPE_F64 if str(V.dtype).endswith("float64") else DTYPE_F32
+            p, mem, keep = _ptr(V)
+        else:
+            V = np.ascontiguousarray(V)
+            dtype = DTYPE_F32 if V.dtype == np.float32 else DTYPE_F64
+            p, mem, keep = _ptr(V, np.float32 if dtype == DTYPE_F32 else np.float64)
+        self._c(self.lib.pstd_set_potential(self.h, p, mem, dtype), "pstd_set_potential")
+
+    def set_incidence(self, b: int, khat, k: float, ramp_time: float, envelope: int = ENV_CW_RAMP):
+        kh = (c_double * 3)(*[float(v) for v in khat])
+        self._c(self.lib.pstd_set_incidence(self.h, b, kh, float(k), envelope, float(ramp_time)), "pstd_set_incidence")
+
+    def reset(self):
+        self._c(self.lib.pstd_reset(self.h), "pstd_reset")
+
+    def huygens_dft(self, b: int, omegas, first_step: int, n_steps: int):
+        om = (c_double * max(1, len(omegas)))(*[float(w) for w in omegas])
+        self._c(self.lib.pstd_huygens_dft(self.h, b, om, len(omegas), int(first_step), int(n_steps)), "pstd_huygens_dft")
+
+    # -- stepping -------------------------------------------------------------------
+    def step(self, nsteps: int = 1):
+        self._c(self.lib.pstd_step(self.h, int(nsteps)), "pstd_step")
+
+    def synchronize(self):
+        self._c(self.lib.pstd_synchronize(self.h), "pstd_synchronize")
+
+    def get_step(self) -> int:
+        n = c_long()
+        self._c(self.lib.pstd_get_step(self.h, byref(n)), "pstd_get_step")
+        return n.value
+
+    # -- fields ---------------------------------------------------------------------
+    def get_field(self, b: int = 0, which: int = FIELD_CURRENT, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=self.cdtype)
+        p, mem, keep = (c_void_p(out.data_ptr()), MEM_DEVICE, out) if _is_cuda_tensor(out) else (out.ctypes.data_as(c_void_p), MEM_HOST, out)
+        self._c(self.lib.pstd_get_field(self.h, b, which, p, mem), "pstd_get_field")
+        return out
+
+    def set_field(self, b: int, prev, cur, n: int):
+        pp, mp, k1 = _ptr(prev, self.cdtype)
+        pc, mc, k2 = _ptr(cur, self.cdtype)
+        if mp != mc:
+            raise ValueError("prev and cur must both be host arrays or both device tensors")
+        self._c(self.lib.pstd_set_field(self.h, b, pp, pc, int(n), mp), "pstd_set_field")
+
+    def get_phasors(self, b: int = 0, f: int = 0):
+        """Six (psi, d psi / d axis) plane pairs (complex128), face order 2*axis + side."""
+        nx, ny, nz = self.spec.n
+        shapes = [(nz, ny), (nz, ny), (nz, nx), (nz, nx), (ny, nx), (ny, nx)]
+        total = sum(2 * s[0] * s[1] for s in shapes)
+        buf = np.empty(total, dtype=np.complex128)
+        self._c(self.lib.pstd_get_phasors(self.h, b, f, buf.ctypes.data_as(c_void_p), MEM_HOST), "pstd_get_phasors")
+        out, off = [], 0
+        for s in shapes:
+            m = s[0] * s[1]
+            out.append((buf[off:off + m].reshape(s), buf[off + m:off + 2 * m].reshape(s)))
+            off += 2 * m
+        return out
+
+    # -- transforms -----------------------------------------------------------------
+    def transform_to_points(self, b: int, f: int, xyz, out=None):
+        if _is_cuda_tensor(xyz):
+            import torch
+            M = xyz.shape[0]
+            if out is None:
+                out = torch.empty(M, dtype=torch.complex128, device=xyz.device)
+            self._c(self.lib.pstd_transform_to_points(self.h, b, f, c_void_p(xyz.data_ptr()), M, c_void_p(out.data_ptr()), MEM_DEVICE),
+                    "pstd_transform_to_points")
+            return out
+        pts = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        res = np.empty(len(pts), dtype=np.complex128) if out is None else out
+        self._c(self.lib.pstd_transform_to_points(self.h, b, f, pts.ctypes.data_as(c_void_p), len(pts),
+                                                  res.ctypes.data_as(c_void_p), MEM_HOST), "pstd_transform_to_points")
+        return res
+
+    def cross_section(self, b: int, f: int, theta, phi):
+        """(dsigma/dOmega, f) at the given directions."""
+        if _is_cuda_tensor(theta):
+            import torch
+            M = theta.shape[0]
+            ds = torch.empty(M, dtype=torch.float64, device=theta.device)
+            fa = torch.empty(M, dtype=torch.complex128, device=theta.device)
+            self._c(self.lib.pstd_cross_section(self.h, b, f, c_void_p(theta.data_ptr()), c_void_p(phi.data_ptr()), M,
+                                                c_void_p(ds.data_ptr()), c_void_p(fa.data_ptr()), MEM_DEVICE), "pstd_cross_section")
+            return ds, fa
+        th = np.ascontiguousarray(theta, dtype=np.float64).ravel()
+        ph = np.ascontiguousarray(phi, dtype=np.float64).ravel()
+        ds = np.empty(len(th))
+        fa = np.empty(len(th), dtype=np.complex128)
+        self._c(self.lib.pstd_cross_section(self.h, b, f, th.ctypes.data_as(c_void_p), ph.ctypes.data_as(c_void_p), len(th),
+                                            ds.ctypes.data_as(c_void_p), fa.ctypes.data_as(c_void_p), MEM_HOST), "pstd_cross_section")
+        return ds, fa
+
+    # -- instrumentation ------------------------------------------------------------
+    def set_timing(self, enable: bool):
+        self._c(self.lib.pstd_set_timing(self.h, 1 if enable else 0), "pstd_set_timing")
+
+    def kernel_stats(self, name: str):
+        n, ms = c_long(), c_double()
+        self._c(self.lib.pstd_kernel_stats(self.h, KERNELS[name], byref(n), byref(ms)), "pstd_kernel_stats")
+        return n.value, ms.value
+
+    def launch_count(self) -> int:
+        n = c_long()
+        self._c(self.lib.pstd_launch_count(self.h, byref(n)), "pstd_launch_count")
+        return n.value
+
+
+def setup_workload(grid: Grid, wl, b: int = 0, inc_index: int = 0, nfreq_omegas=None):
+    """Potential, incidence and DFT window of a Workload (inputs.Workload) on member b."""
+    inc = wl.incidences[inc_index]
+    grid.set_potential(wl.V)
+    grid.set_incidence(b, inc.khat, inc.k, inc.ramp_time)
+    w0 = wl.spec.hbar * inc.k ** 2 / (2 * wl.spec.mass)
+    grid.huygens_dft(b, nfreq_omegas or [w0], wl.window_first, wl.window_len)

@@ -1,0 +1,350 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (relative L2 unless stated), from the arithmetic:
+  * FP64 path: 1e-12 after one step, 1e-10 after a full 750-step run (round-off of
+    the two FFT orders growing along the run), transforms 1e-10 (the G = 8 cell
+    quadrature reproduces the paper's sinc sum to ~1e-14 on these grids).
+  * FP32 path: 2e-6 after one step, 2e-4 on psi after a full run and 1e-3 on
+    cross-sections (single-precision round-off of ~6e-8 per operation over the
+    FFT depth and the run).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import analytic as an
+from oracle import ntdf_oracle as no
+from oracle import pstd_oracle as po
+from paper_2403_04053_gb300 import inputs, pstd
+
+pytestmark = pytest.mark.gpu
+
+K = 2 * math.pi
+E0 = 0.5 * K * K
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def ragged_spec(mode="exact"):
+    # x spans one partial 32-lane tile, y one full tile, z two tiles with a ragged tail
+    return inputs.GridSpec(n=(24, 32, 48), d=(0.25, 0.3, 0.2), dt=0.002, abc_cells=(4, 5, 6), tfsf_lo=(9, 12, 17),
+                           tfsf_hi=(15, 20, 31), taper_cells=2, huygens_lo=(7, 9, 14), huygens_hi=(17, 23, 34),
+                           tfsf_mode=mode)
+
+
+def random_core_V(spec, seed, amp=3.0):
+    rng = np.random.default_rng(seed)
+    V = np.zeros(spec.shape)
+    c = spec.core_box()
+    V[c[2][0]:c[2][1] + 1, c[1][0]:c[1][1] + 1, c[0][0]:c[0][1] + 1] = rng.uniform(
+        -amp, amp, (c[2][1] - c[2][0] + 1, c[1][1] - c[1][0] + 1, c[0][1] - c[0][0] + 1))
+    return V
+
+
+# ----------------------------------------------------------------------------------
+# one step from random states, several grid shapes
+# ----------------------------------------------------------------------------------
+ONE_STEP_SPECS = {
+    "ragged-24x32x48": lambda mode: ragged_spec(mode),
+    "cube-48": lambda mode: inputs.GridSpec(n=(48,) * 3, d=(0.25,) * 3, dt=0.004, tfsf_mode=mode),
+    "mixed-96x16x64": lambda mode: inputs.GridSpec(n=(96, 16, 64), d=(0.2, 0.35, 0.25), dt=0.002, abc_cells=(8, 2, 6),
+                                                   tfsf_lo=(30, 5, 20), tfsf_hi=(66, 11, 44), taper_cells=3,
+                                                   huygens_lo=(20, 3, 12), huygens_hi=(76, 13, 52), tfsf_mode=mode),
+    "radix3-12x192x8": lambda mode: inputs.GridSpec(n=(12, 192, 8), d=(0.3, 0.1, 0.4), dt=0.001, abc_cells=(2, 16, 1),
+                                                    tfsf_lo=(4, 60, 3), tfsf_hi=(8, 132, 5), taper_cells=1,
+                                                    huygens_lo=(3, 40, 2), huygens_hi=(9, 150, 6), tfsf_mode=mode),
+}
+
+
+@pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-12), (pstd.F32, 2e-6)])
+@pytest.mark.parametrize("mode", ["exact", "paper"])
+@pytest.mark.parametrize("name", list(ONE_STEP_SPECS))
+def test_one_step_matches_oracle(name, mode, prec, tol):
+    spec = ONE_STEP_SPECS[name](mode)
+    V = random_core_V(spec, 3)
+    khat = (0.3, -0.5, 0.81)
+    prev = inputs.random_field(spec.shape, 5)
+    cur = inputs.random_field(spec.shape, 6)
+    sim = po.Simulation(spec, V, khat, K, 0.05)
+    sim.prev, sim.cur, sim.n = prev.copy(), cur.copy(), 17
+    sim.step(1)
+    cd = np.complex128 if prec == pstd.F64 else np.complex64
+    with pstd.Grid(spec, precision=prec) as g:
+        g.set_potential(V)
+        g.set_incidence(0, khat, K, 0.05)
+        g.set_field(0, prev.astype(cd), cur.astype(cd), 17)
+        g.step(1)
+        g.synchronize()
+        assert g.get_step() == 18
+        got = g.get_field(0)
+        assert rel(got, sim.cur) < tol
+        # the previous level is the old current one, untouched
+        assert np.array_equal(g.get_field(0, pstd.FIELD_PREVIOUS), cur.astype(cd))
+
+
+# ----------------------------------------------------------------------------------
+# short runs with the running DFT, transforms and the far field
+# ----------------------------------------------------------------------------------
+@pytest.fixture(scope="module", params=["exact", "paper"])
+def short_run(request):
+    spec = ragged_spec(request.param)
+    V = random_core_V(spec, 1)
+    khat, w0 = (0.3, -0.5, 0.81), K * K / 2
+    win = (20, 40)
+    om = [w0, 0.93 * w0]
+    sim = po.Simulation(spec, V, khat, K, 0.05, window=win, omegas=om)
+    sim.step(60)
+    pts = np.array([[3.0, -2.0, 5.5], [-4.0, 6.0, 1.0], [0.5, 0.2, -9.0], [30.0, 10.0, 40.0], [-200.0, 50.0, 120.0]])
+    th = np.deg2rad(np.array([0.0, 33.0, 90.0, 140.0, 180.0]))
+    ph = np.deg2rad(np.array([0.0, 20.0, 200.0, 300.0, 10.0]))
+    ref = {f: (sim.scaled_phasors(f), no.transform_to_points(spec, K, sim.scaled_phasors(f), pts),
+               no.cross_section(spec, K, sim.scaled_phasors(f), th, ph)) for f in range(2)}
+    return dict(spec=spec, V=V, khat=khat, win=win, om=om, sim=sim, pts=pts, th=th, ph=ph, ref=ref)
+
+
+@pytest.mark.parametrize("prec,tol_state,tol_out", [(pstd.F64, 1e-12, 1e-10), (pstd.F32, 2e-5, 2e-4)])
+def test_short_run_dft_transform_far_field(short_run, prec, tol_state, tol_out):
+    r = short_run
+    with pstd.Grid(r["spec"], precision=prec) as g:
+        g.set_potential(r["V"])
+        g.set_incidence(0, r["khat"], K, 0.05)
+        g.huygens_dft(0, r["om"], *r["win"])
+        g.step(60)
+        g.synchronize()
+        assert rel(g.get_field(0), r["sim"].cur) < tol_state
+        if r["spec"].tfsf_mode == "paper":
+            assert rel(g.get_field(0, pstd.FIELD_SCATTERED), r["sim"].scattered_field()) < tol_state
+        for f in range(2):
+            phs, psi_ref, (ds_ref, f_ref) = r["ref"][f]
+            for (gp, gd), (rp, rd) in zip(g.get_phasors(0, f), phs):
+                assert rel(gp, rp) < 10 * tol_state and rel(gd, rd) < 10 * tol_state
+            psi = g.transform_to_points(0, f, r["pts"])
+            assert np.max(np.abs(psi - psi_ref) / np.abs(psi_ref)) < tol_out
+            ds, fa = g.cross_section(0, f, r["th"], r["ph"])
+            assert np.max(np.abs(fa - f_ref) / np.abs(f_ref)) < tol_out
+            assert np.max(np.abs(ds - ds_ref) / ds_ref) < 2 * tol_out
+
+
+# ----------------------------------------------------------------------------------
+# the full 48^3 square-barrier run (750 steps)
+# ----------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def barrier_run():
+    wl = inputs.square_barrier_workload()
+    inc = wl.incidences[0]
+    sim = po.Simulation(wl.spec, wl.V, inc.khat, inc.k, inc.ramp_time, window=(wl.window_first, wl.window_len))
+    sim.step(wl.nsteps)
+    phs = sim.scaled_phasors(0)
+    ds, f = no.cross_section(wl.spec, K, phs, wl.far_theta, wl.far_phi)
+    sub = wl.fresnel_points[::97]
+    psi = no.transform_to_points(wl.spec, K, phs, sub)
+    return wl, sim, ds, f, sub, psi
+
+
+def _run_gpu(wl, prec):
+    g = pstd.Grid(wl.spec, precision=prec)
+    pstd.setup_workload(g, wl)
+    g.step(wl.nsteps)
+    g.synchronize()
+    return g
+
+
+def test_square_barrier_full_run_fp64(barrier_run):
+    wl, sim, ds_ref, f_ref, sub, psi_ref = barrier_run
+    with _run_gpu(wl, pstd.F64) as g:
+        assert rel(g.get_field(0), sim.cur) < 1e-10
+        ds, f = g.cross_section(0, 0, wl.far_theta, wl.far_phi)
+        assert rel(f, f_ref) < 1e-10
+        assert rel(g.transform_to_points(0, 0, sub), psi_ref) < 1e-10
+        # and the physics: within 3% of the analytic partial waves (voxelised sphere)
+        pw = np.abs(an.partial_wave_amplitude(wl.far_theta, K, 0.3 * E0, 1.5)) ** 2
+        assert rel(ds, pw) < 3e-2
+        # the full 32 x 32 Fresnel plane at z = 20 runs and is finite
+        full = g.transform_to_points(0, 0, wl.fresnel_points)
+        assert full.shape == (1024,) and np.all(np.isfinite(full))
+
+
+def test_square_barrier_full_run_fp32_against_fp64_oracle(barrier_run):
+    wl, sim, ds_ref, f_ref, sub, psi_ref = barrier_run
+    with _run_gpu(wl, pstd.F32) as g:
+        assert rel(g.get_field(0), sim.cur) < 2e-4
+        ds, f = g.cross_section(0, 0, wl.far_theta, wl.far_phi)
+        assert rel(ds, ds_ref) < 1e-3
+        assert rel(g.transform_to_points(0, 0, sub), psi_ref) < 1e-3
+
+
+# ----------------------------------------------------------------------------------
+# the 128^3 Gaussian-sum geometry, in the launch configuration the benchmark times
+# ----------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def big():
+    wl = inputs.gaussian_sum_workload(with_outputs=False)
+    return wl
+
+
+@pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-12), (pstd.F32, 2e-6)])
+def test_128_cubed_one_step_elementwise(big, prec, tol):
+    wl = big
+    inc = wl.incidences[0]
+    prev = inputs.smooth_random_field(wl.spec, 7)
+    cur = inputs.smooth_random_field(wl.spec, 8)
+    sim = po.Simulation(wl.spec, wl.V, inc.khat, inc.k, inc.ramp_time)
+    sim.prev, sim.cur, sim.n = prev.copy(), cur.copy(), 200
+    sim.step(1)
+    cd = np.complex128 if prec == pstd.F64 else np.complex64
+    with pstd.Grid(wl.spec, precision=prec) as g:
+        g.set_potential(wl.V)
+        g.set_incidence(0, inc.khat, inc.k, inc.ramp_time)
+        g.set_field(0, prev.astype(cd), cur.astype(cd), 200)
+        g.step(1)
+        got = g.get_field(0)
+    assert rel(got, sim.cur) < tol
+    assert np.max(np.abs(got - sim.cur)) < 20 * tol * np.max(np.abs(sim.cur))
+
+
+@pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-10), (pstd.F32, 1e-4)])
+def test_128_cubed_sampled_transform(big, prec, tol):
+    """Phasors from a short 128^3 run; the surface transform at sampled Fresnel-plane points and
+    far-field directions against the oracle's literal mode sum on the GPU's own phasors."""
+    wl = big
+    inc = wl.incidences[0]
+    w0 = K * K / 2
+    with pstd.Grid(wl.spec, precision=prec) as g:
+        g.set_potential(wl.V)
+        g.set_incidence(0, inc.khat, inc.k, 0.05)
+        g.huygens_dft(0, [w0], 20, 30)
+        g.step(50)
+        phs = g.get_phasors(0, 0)
+        D = 18.0
+        pts = inputs.plane_points(inc.khat, D * D / 4, 1.5 * D, 256)[[0, 33000, 65535]]
+        psi = g.transform_to_points(0, 0, pts)
+        th = np.deg2rad([5.0, 91.0, 170.0])
+        ph = np.deg2rad([10.0, 250.0, 0.0])
+        ds, f = g.cross_section(0, 0, th, ph)
+    ref = no.transform_to_points(wl.spec, K, phs, pts)
+    _, fref = no.cross_section(wl.spec, K, phs, th, ph)
+    assert np.max(np.abs(psi - ref) / np.abs(ref)) < tol
+    assert np.max(np.abs(f - fref) / np.abs(fref)) < tol
+
+
+# ----------------------------------------------------------------------------------
+# edge cases and ABI behaviour
+# ----------------------------------------------------------------------------------
+def test_exact_form_leaks_nothing_at_zero_potential():
+    wl = inputs.square_barrier_workload(with_outputs=False)
+    for prec in (pstd.F32, pstd.F64):
+        with pstd.Grid(wl.spec, precision=prec) as g:
+            g.set_potential(np.zeros(wl.spec.shape))
+            g.set_incidence(0, (0.36, 0.48, 0.8), K, 0.5)
+            g.step(300)
+            assert np.count_nonzero(g.get_field(0)) == 0
+
+
+def test_batched_members_equal_separate_runs():
+    spec = ragged_spec()
+    V = random_core_V(spec, 2)
+    dirs = [(0.3, -0.5, 0.81), (-0.6, 0.0, 0.8)]
+    w0 = K * K / 2
+    outs = []
+    for b, kh in enumerate(dirs):
+        with pstd.Grid(spec, precision=pstd.F32) as g:
+            g.set_potential(V)
+            g.set_incidence(0, kh, K, 0.05)
+            g.huygens_dft(0, [w0], 10, 20)
+            g.step(30)
+            outs.append((g.get_field(0), g.transform_to_points(0, 0, [[5.0, 5.0, 9.0]])))
+    with pstd.Grid(spec, precision=pstd.F32, batch=2) as g:
+        g.set_potential(V)
+        for b, kh in enumerate(dirs):
+            g.set_incidence(b, kh, K, 0.05)
+        g.huygens_dft(-1, [w0], 10, 20)
+        g.step(30)
+        for b in range(2):
+            assert np.array_equal(g.get_field(b), outs[b][0])
+            assert np.array_equal(g.transform_to_points(b, 0, [[5.0, 5.0, 9.0]]), outs[b][1])
+
+
+def test_device_buffers_match_host_buffers():
+    import torch
+    spec = ragged_spec()
+    V = random_core_V(spec, 4)
+    w0 = K * K / 2
+    pts = np.array([[3.0, -2.0, 5.5], [30.0, 10.0, 40.0]])
+    th, ph = np.deg2rad([10.0, 100.0]), np.deg2rad([5.0, 60.0])
+    with pstd.Grid(spec, precision=pstd.F64) as g:
+        g.set_potential(torch.from_numpy(V).cuda())
+        g.set_incidence(0, (0, 0, 1), K, 0.05)
+        g.huygens_dft(0, [w0], 10, 20)
+        g.step(30)
+        a = g.transform_to_points(0, 0, pts)
+        b = g.transform_to_points(0, 0, torch.from_numpy(pts).cuda()).cpu().numpy()
+        assert np.array_equal(a, b)
+        ds, f = g.cross_section(0, 0, th, ph)
+        ds2, f2 = g.cross_section(0, 0, torch.from_numpy(th).cuda(), torch.from_numpy(ph).cuda())
+        assert np.array_equal(f, f2.cpu().numpy()) and np.array_equal(ds, ds2.cpu().numpy())
+        out = torch.empty(spec.shape, dtype=torch.complex128, device="cuda")
+        g.get_field(0, out=out)
+        assert np.array_equal(out.cpu().numpy(), g.get_field(0))
+
+
+def test_runs_are_bitwise_deterministic():
+    spec = ragged_spec()
+    V = random_core_V(spec, 5)
+    res = []
+    for _ in range(2):
+        with pstd.Grid(spec, precision=pstd.F32) as g:
+            g.set_potential(V)
+            g.set_incidence(0, (0.3, -0.5, 0.81), K, 0.05)
+            g.huygens_dft(0, [K * K / 2], 10, 20)
+            g.step(30)
+            res.append((g.get_field(0), g.cross_section(0, 0, [0.3], [0.2])[1]))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_nonfinite_state_is_reported():
+    spec = ragged_spec()
+    with pstd.Grid(spec, precision=pstd.F32) as g:
+        g.set_incidence(0, (0, 0, 1), K, 0.05)
+        bad = np.zeros(spec.shape, dtype=np.complex64)
+        bad[10, 10, 10] = np.nan
+        g.set_field(0, bad, bad, 0)
+        g.step(1)
+        with pytest.raises(pstd.PstdError) as e:
+            g.synchronize()
+        assert e.value.code == "ENONFINITE"
+        g.synchronize()   # the flag is cleared once reported
+
+
+def test_call_order_errors():
+    spec = ragged_spec()
+    with pstd.Grid(spec, precision=pstd.F32) as g:
+        with pytest.raises(pstd.PstdError) as e:
+            g.step(1)
+        assert e.value.code == "ESTATE"
+        g.set_incidence(0, (0, 0, 1), K, 0.05)
+        g.huygens_dft(0, [K * K / 2], 5, 10)
+        g.step(8)
+        with pytest.raises(pstd.PstdError) as e:
+            g.transform_to_points(0, 0, [[5.0, 5.0, 5.0]])
+        assert e.value.code == "ESTATE"
+        with pytest.raises(pstd.PstdError) as e:
+            g.set_potential(np.ones(spec.shape))
+        assert e.value.code == "EINVAL"
+        with pytest.raises(pstd.PstdError) as e:
+            g.cross_section(0, 3, [0.1], [0.1])
+        assert e.value.code == "EINVAL"
+
+
+def test_timing_and_launch_counts():
+    spec = ragged_spec()
+    with pstd.Grid(spec, precision=pstd.F32) as g:
+        g.set_incidence(0, (0, 0, 1), K, 0.05)
+        g.set_timing(True)
+        g.step(5)
+        for name in ("xpass", "ypass", "zpass"):
+            n, ms = g.kernel_stats(name)
+            assert n == 5 and ms > 0
+        assert g.launch_count() == 15
