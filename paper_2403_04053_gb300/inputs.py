@@ -257,8 +257,8 @@ def stable_dt(spec_n, spec_d, vmax: float, frac: float = 0.9) -> float:
 
 
 def dft_window(E0: float, dt: float, nsteps: int, periods: int = 3):
-    """Last `periods` whole carrier periods, rounded to whole steps."""
-    M = int(round(periods * 2 * math.pi / (E0 * dt)))
+    """Last `periods` whole carrier periods, rounded to whole steps (the whole run if shorter)."""
+    M = min(int(round(periods * 2 * math.pi / (E0 * dt))), nsteps)
     return nsteps - M, M
 
 
