@@ -149,6 +149,20 @@ pstd_status pstd_transform_to_points(pstd_grid* g, int b, int f, const double* x
 pstd_status pstd_cross_section(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M,
                                double* out_dsdo, void* out_f, int mem);
 
+/* Allocation-free variant of pstd_cross_section, for callers that cannot allocate device
+ * memory once running (a fixed, fully reserved memory budget, or a latency-critical loop
+ * that cannot afford an allocation or the synchronisation a free implies).  The paper has
+ * no counterpart: this is a deployment convenience.  theta, phi, out_dsdo and out_f (may be
+ * NULL) are DEVICE pointers; M <= 1048576, else PSTD_EINVAL.  The only scratch, the
+ * transform's partial sums, sits in a 16 MiB file-scope device array that every device
+ * loading the library holds until exit; the first call on a device looks up its address
+ * (make that first call before any stream capture).  All calls on a device share the
+ * array and it keeps the last call's contents; calls whose kernels overlap on the GPU race
+ * on it and must be serialised.  The grid's surface records must exist: PSTD_ESTATE until
+ * pstd_cross_section or pstd_transform_to_points has run once on the grid. */
+pstd_status pstd_cross_section_noalloc(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M,
+                                       double* out_dsdo, void* out_f);
+
 /* Copy a state of member b out: PSTD_FIELD_CURRENT (psi^n), PSTD_FIELD_PREVIOUS
  * (psi^{n-1}) or PSTD_FIELD_SCATTERED (psi^n minus zeta psi_inc^n in the PAPER form, the
  * state itself in the EXACT form).  out: n[0]*n[1]*n[2] complex values of the grid

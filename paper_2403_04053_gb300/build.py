@@ -1,6 +1,6 @@
 """Build the in-tree CUDA library libpstd.so for sm_103a with nvcc.
 
-Four translation units are compiled in parallel and linked against the shared CUDA
+Five translation units are compiled in parallel and linked against the shared CUDA
 runtime (so the process shares one runtime with PyTorch).  No CMake, no torch
 extension machinery: the library exposes a plain C ABI (include/pstd.h).
 """
@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpstd.so")
-SOURCES = ["api.cu", "common.cu", "kernels_f32.cu", "kernels_f64.cu"]
+SOURCES = ["api.cu", "common.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -638,6 +638,68 @@ pstd_status run_transform(pstd_grid* g, int b, int f, const double* pts, const d
 
 }  // namespace
 
+namespace pstd {
+
+int grid_device(const pstd_grid* g) { return g->dev; }
+
+pstd_status grid_error(pstd_grid* g, pstd_status s, const char* msg) { return fail(g, s, msg); }
+
+// Far field of member b, frequency f, with the per-split partial sums written to a
+// caller-provided device buffer of `scratch_elems` double2 entries instead of the grid's
+// own: nothing is allocated.  The grid's surface records must already exist (they are
+// created by the first pstd_transform_to_points / pstd_cross_section call on the grid).
+template <typename R>
+pstd_status far_field_into_scratch_r(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M,
+                                     double* out_dsdo, double2* out_f, double2* scratch, long long scratch_elems)
+{
+    if (!g->MbT[0] || !g->rec)
+        return fail(g, PSTD_ESTATE, "surface records not set up: call pstd_cross_section or pstd_transform_to_points once first");
+    pstd_status st = prepare_records<R>(g, b, f);
+    if (st != PSTD_OK) return st;
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    TransformArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.rec = static_cast<const C*>(g->rec);
+    a.ncells = g->ncells;
+    for (int fi = 0; fi < 6; ++fi) a.face[fi] = g->faces[fi];
+    a.theta = theta;
+    a.phi = phi;
+    a.M = M;
+    a.k = g->mem[b].k;
+    for (int q = 0; q < g->G; ++q) a.gl_node[q] = g->gl_x[q];
+    const long long blocks = (M + 255) / 256;
+    const int CH = sizeof(R) == 4 ? 32 : 16;
+    const long long chunks = (g->ncells + CH - 1) / CH;
+    long long splits = std::max(1LL, std::min(chunks, (2LL * 152 + blocks - 1) / blocks));
+    splits = std::min(splits, std::max(1LL, scratch_elems / (long long)M));
+    long long cps = ((g->ncells + splits - 1) / splits + CH - 1) / CH * CH;
+    splits = (g->ncells + cps - 1) / cps;
+    if (splits * (long long)M > scratch_elems) return fail(g, PSTD_EINVAL, "directions exceed the scratch capacity");
+    a.cells_per_split = cps;
+    a.partial = scratch;
+    {
+        Timer t(g, 6);
+        CK(g, launch_transform<R>(a, g->G, (int)splits, true, g->stream));
+    }
+    {
+        Timer t(g, 6);
+        CK(g, launch_reduce_partials(scratch, (int)splits, M, out_f, out_dsdo, g->stream));
+    }
+    return PSTD_OK;
+}
+
+pstd_status far_field_into_scratch(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M,
+                                   double* out_dsdo, double2* out_f, double2* scratch, long long scratch_elems)
+{
+    DeviceGuard dg(g->dev);
+    pstd_status st = check_window(g, b, f);
+    if (st != PSTD_OK) return st;
+    return g->prec == PSTD_F64 ? far_field_into_scratch_r<double>(g, b, f, theta, phi, M, out_dsdo, out_f, scratch, scratch_elems)
+                               : far_field_into_scratch_r<float>(g, b, f, theta, phi, M, out_dsdo, out_f, scratch, scratch_elems);
+}
+
+}  // namespace pstd
+
 // =====================================================================================
 // C ABI
 // =====================================================================================

@@ -113,4 +113,10 @@ template <typename R> cudaError_t launch_pack_records(const double2* out_psi, co
                                                      typename std::conditional<sizeof(R) == 4, float2, double2>::type* rec,
                                                      cudaStream_t s);
 
+// used by the allocation-free far-field entry point (noalloc.cu)
+int grid_device(const pstd_grid* g);
+pstd_status grid_error(pstd_grid* g, pstd_status s, const char* msg);
+pstd_status far_field_into_scratch(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M,
+                                   double* out_dsdo, double2* out_f, double2* scratch, long long scratch_elems);
+
 }  // namespace pstd

@@ -54,6 +54,7 @@ _SIGS = {
     "pstd_step": (c_int, [c_void_p, c_long]),
     "pstd_transform_to_points": (c_int, [c_void_p, c_int, c_int, c_void_p, c_long, c_void_p, c_int]),
     "pstd_cross_section": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_long, c_void_p, c_void_p, c_int]),
+    "pstd_cross_section_noalloc": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_long, c_void_p, c_void_p]),
     "pstd_get_field": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
     "pstd_set_field": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_int]),
     "pstd_get_phasors": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
@@ -275,6 +276,14 @@ class Grid:
         self._c(self.lib.pstd_cross_section(self.h, b, f, th.ctypes.data_as(c_void_p), ph.ctypes.data_as(c_void_p), len(th),
                                             ds.ctypes.data_as(c_void_p), fa.ctypes.data_as(c_void_p), MEM_HOST), "pstd_cross_section")
         return ds, fa
+
+    def cross_section_noalloc(self, b: int, f: int, theta, phi, out_dsdo, out_f=None):
+        """pstd_cross_section_noalloc: device tensors in and out, no device allocation."""
+        self._c(self.lib.pstd_cross_section_noalloc(self.h, b, f, c_void_p(theta.data_ptr()), c_void_p(phi.data_ptr()),
+                                                    int(theta.shape[0]), c_void_p(out_dsdo.data_ptr()),
+                                                    c_void_p(out_f.data_ptr()) if out_f is not None else None),
+                "pstd_cross_section_noalloc")
+        return out_dsdo, out_f
 
     # -- instrumentation ------------------------------------------------------------
     def set_timing(self, enable: bool):
