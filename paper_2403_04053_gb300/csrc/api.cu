@@ -78,6 +78,10 @@ struct pstd_grid {
     long long face_off[6] = {}, face_size[6] = {};
     long long acc_freq_stride = 0;
     long long phasor_version = 0;
+    double2* dft_phase = nullptr;          // [member][freq][window step] e^{+i omega t_n}
+    size_t dft_phase_cap = 0;
+    long long dft_phase_len = 0;           // window steps per frequency (max over members)
+    long long* window_first_dev = nullptr; // per member
     int* flag = nullptr;
     // transform
     int G = 8;
@@ -432,6 +436,10 @@ template <typename R> pstd_status run_dft(pstd_grid* g, unsigned long long mask)
     a.member_mask = mask;
     a.step = g->n;
     a.dt = g->desc.dt;
+    a.phase = g->dft_phase;
+    a.phase_len = g->dft_phase_len;
+    a.phase_member_stride = g->dft_phase_len * PSTD_MAX_FREQ;
+    a.window_first = g->window_first_dev;
     for (int ax = 0; ax < 3; ++ax) {
         a.axis = ax;
         a.h[0] = g->desc.huygens_lo[ax];
@@ -466,6 +474,14 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps)
             ++g->phasor_version;
         }
         StepArgs<R> a = step_args<R>(g);
+        {
+            const double t = g->n * g->desc.dt;
+            for (int b = 0; b < g->batch; ++b) {
+                const MemberHost& m = g->mem[b];
+                const double env = (m.ramp <= 0 || t >= m.ramp) ? 1.0 : (t <= 0 ? 0.0 : 0.5 * (1.0 - std::cos(kPi * t / m.ramp)));
+                a.tfac[b] = make_double2(env * std::cos(m.w0 * t), -env * std::sin(m.w0 * t));
+            }
+        }
         {
             Timer t(g, 0);
             CK(g, launch_xpass<R>(a, g->batch, g->stream));
@@ -790,6 +806,7 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     DeviceGuard dg(g->dev);
     cudaStreamSynchronize(g->stream);
     for (void* p : {g->buf[0], g->buf[1], g->V, (void*)g->mem_dev, (void*)g->acc, (void*)g->flag, (void*)g->gl_w_dev,
+                    (void*)g->dft_phase, (void*)g->window_first_dev,
                     (void*)g->T1, (void*)g->OutP, (void*)g->OutD, g->rec, (void*)g->partial, (void*)g->pts_dev,
                     (void*)g->out_dev, (void*)g->dsdo_dev})
         if (p) cudaFree(p);
@@ -973,6 +990,29 @@ pstd_status pstd_huygens_dft(pstd_grid* g, int b, const double* omega, int nfreq
                                   sizeof(double2) * g->acc_freq_stride * g->acc_freq_cap, g->stream));
     }
     ++g->phasor_version;
+    // e^{+i omega_f t_n} for every member, frequency and window step, in double precision
+    long long len = 1;
+    for (const auto& m : g->mem) len = std::max(len, m.len);
+    const size_t entries = (size_t)g->batch * PSTD_MAX_FREQ * len;
+    std::vector<double2> tab(entries, make_double2(0.0, 0.0));
+    std::vector<long long> first(g->batch, 0);
+    for (int mb = 0; mb < g->batch; ++mb) {
+        const MemberHost& m = g->mem[mb];
+        first[mb] = m.first;
+        for (int f = 0; f < m.nfreq; ++f)
+            for (long long s2 = 0; s2 < m.len; ++s2) {
+                const double t = (m.first + s2) * g->desc.dt;
+                tab[((size_t)mb * PSTD_MAX_FREQ + f) * len + s2] = make_double2(std::cos(m.omega[f] * t), std::sin(m.omega[f] * t));
+            }
+    }
+    CK(g, cudaStreamSynchronize(g->stream));
+    pstd_status st = ensure(g, &g->dft_phase, g->dft_phase_cap, entries * sizeof(double2));
+    if (st != PSTD_OK) return st;
+    if (!g->window_first_dev && dalloc(&g->window_first_dev, sizeof(long long) * g->batch) != cudaSuccess)
+        return fail(g, PSTD_ENOMEM, "window table");
+    CK(g, cudaMemcpy(g->dft_phase, tab.data(), entries * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(g, cudaMemcpy(g->window_first_dev, first.data(), sizeof(long long) * g->batch, cudaMemcpyHostToDevice));
+    g->dft_phase_len = len;
     return upload_members(g);
 }
 

@@ -44,6 +44,7 @@ template <typename R> struct StepArgs {
     double dt, hbar, mass;
     int mode;                // PSTD_TFSF_EXACT / PSTD_TFSF_PAPER
     int* flag;               // bit 0: non-finite value written
+    double2 tfac[PSTD_MAX_BATCH];   // a(t_n) e^{-i w0 t_n} per member, evaluated on the host in FP64
 };
 
 // Plane DFT arguments (one launch per axis).
@@ -64,6 +65,10 @@ template <typename R> struct DftArgs {
     unsigned long long member_mask;
     long long step;
     double dt;
+    const double2* phase;          // e^{+i omega_f t_n}: [member][freq][window step], built on the host
+    long long phase_member_stride;  // entries per member
+    long long phase_len;            // window steps per frequency
+    const long long* window_first;  // per member
 };
 
 template <typename R> cudaError_t launch_xpass(const StepArgs<R>& a, int batch, cudaStream_t s);
