@@ -189,8 +189,8 @@ pstd_status pstd_get_step(pstd_grid* g, long* n);
 pstd_status pstd_stability_dt_max(const pstd_grid_desc* desc, double vmax, double* out_dt);
 
 /* Per-kernel timing with CUDA events on the grid's stream (off by default).  Kernel ids:
- * 0 x-pass, 1 y-pass, 2 z-pass, 3 plane DFT, 4 transform/node preparation, 5 point transform,
- * 6 far field.  pstd_kernel_stats returns the launches and summed milliseconds since the
+ * 0 x-pass, 1 y-pass, 2 z-pass (on DFT-window steps these also accumulate the running DFT),
+ * 3 unused, 4 transform/node preparation, 5 point transform, 6 far field, 7 V-term and TF/SF source.  pstd_kernel_stats returns the launches and summed milliseconds since the
  * last pstd_set_timing(g, 1) (synchronises).  pstd_launch_count counts every kernel the
  * grid launched since creation. */
 pstd_status pstd_set_timing(pstd_grid* g, int enable);

@@ -19,7 +19,7 @@ namespace {
 thread_local std::string g_create_error;
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kSizes[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384};
-constexpr int kKernelIds = 7;
+constexpr int kKernelIds = 8;
 
 bool supported_size(int n)
 {
@@ -78,6 +78,8 @@ struct pstd_grid {
     long long face_off[6] = {}, face_size[6] = {};
     long long acc_freq_stride = 0;
     long long phasor_version = 0;
+    double2* tfac = nullptr;               // [step of the call][member] a(t_n) e^{-i w0 t_n}
+    size_t tfac_cap = 0;
     double2* dft_phase = nullptr;          // [member][freq][window step] e^{+i omega t_n}
     size_t dft_phase_cap = 0;
     long long dft_phase_len = 0;           // window steps per frequency (max over members)
@@ -97,6 +99,13 @@ struct pstd_grid {
     void* rec = nullptr;
     int rec_member = -1, rec_freq = -1;
     long long rec_version = -1;
+    double2* Fdft[6][2] = {};               // per face: DFT matrices along b (Nb x Nb) and c (Nc x Nc)
+    double2* specP = nullptr;               // per-face 2-D spectra in double (scratch for the preparation)
+    double2* specD = nullptr;
+    void* ct = nullptr;                     // far-field spectra, working precision, faces back to back
+    long long ct_off[6] = {};
+    int ct_member = -1, ct_freq = -1;
+    long long ct_version = -1;
     double2* partial = nullptr;
     size_t partial_cap = 0;
     double* pts_dev = nullptr;
@@ -420,7 +429,7 @@ template <typename R> StepArgs<R> step_args(pstd_grid* g)
     return a;
 }
 
-template <typename R> pstd_status run_dft(pstd_grid* g, unsigned long long mask)
+template <typename R> DftArgs<R> dft_args(pstd_grid* g, unsigned long long mask, int axis)
 {
     using C = typename DftArgs<R>::C;
     DftArgs<R> a;
@@ -440,28 +449,48 @@ template <typename R> pstd_status run_dft(pstd_grid* g, unsigned long long mask)
     a.phase_len = g->dft_phase_len;
     a.phase_member_stride = g->dft_phase_len * PSTD_MAX_FREQ;
     a.window_first = g->window_first_dev;
-    for (int ax = 0; ax < 3; ++ax) {
-        a.axis = ax;
-        a.h[0] = g->desc.huygens_lo[ax];
-        a.h[1] = g->desc.huygens_hi[ax];
-        a.dw = static_cast<const C*>(g->dw[ax]);
-        Timer t(g, 3);
-        CK(g, launch_plane_dft<R>(a, g->batch, g->stream));
+    a.axis = axis;
+    a.h[0] = g->desc.huygens_lo[axis];
+    a.h[1] = g->desc.huygens_hi[axis];
+    a.dw = static_cast<const C*>(g->dw[axis]);
+    return a;
+}
+
+// incident time factors a(t_n) e^{-i w0 t_n} for steps [n0, n0 + nsteps) of every member, in
+// double precision, uploaded in stream order (the previous call's kernels finish first)
+pstd_status upload_time_factors(pstd_grid* g, long long n0, long nsteps)
+{
+    std::vector<double2> tab((size_t)std::max(1L, nsteps) * g->batch);
+    for (long s = 0; s < nsteps; ++s) {
+        const double t = (n0 + s) * g->desc.dt;
+        for (int b = 0; b < g->batch; ++b) {
+            const MemberHost& m = g->mem[b];
+            const double env = (m.ramp <= 0 || t >= m.ramp) ? 1.0 : (t <= 0 ? 0.0 : 0.5 * (1.0 - std::cos(kPi * t / m.ramp)));
+            tab[(size_t)s * g->batch + b] = make_double2(env * std::cos(m.w0 * t), -env * std::sin(m.w0 * t));
+        }
     }
+    pstd_status st = ensure(g, &g->tfac, g->tfac_cap, tab.size() * sizeof(double2));
+    if (st != PSTD_OK) return st;
+    CK(g, cudaMemcpyAsync(g->tfac, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice, g->stream));
     return PSTD_OK;
 }
 
 template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps)
 {
+    const long long n0 = g->n;
+    pstd_status st0 = upload_time_factors(g, n0, nsteps);
+    if (st0 != PSTD_OK) return st0;
     for (long s = 0; s < nsteps; ++s) {
         unsigned long long mask = 0;
         for (int b = 0; b < g->batch; ++b) {
             const MemberHost& m = g->mem[b];
             if (m.nfreq > 0 && g->n >= m.first && g->n < m.first + m.len) mask |= 1ull << b;
         }
+        DftArgs<R> dx, dy, dz;
         if (mask) {
-            pstd_status st = run_dft<R>(g, mask);
-            if (st != PSTD_OK) return st;
+            dx = dft_args<R>(g, mask, 0);
+            dy = dft_args<R>(g, mask, 1);
+            dz = dft_args<R>(g, mask, 2);
             const double t = g->n * g->desc.dt;
             for (int b = 0; b < g->batch; ++b) {
                 if (!((mask >> b) & 1ull)) continue;
@@ -474,25 +503,24 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps)
             ++g->phasor_version;
         }
         StepArgs<R> a = step_args<R>(g);
-        {
-            const double t = g->n * g->desc.dt;
-            for (int b = 0; b < g->batch; ++b) {
-                const MemberHost& m = g->mem[b];
-                const double env = (m.ramp <= 0 || t >= m.ramp) ? 1.0 : (t <= 0 ? 0.0 : 0.5 * (1.0 - std::cos(kPi * t / m.ramp)));
-                a.tfac[b] = make_double2(env * std::cos(m.w0 * t), -env * std::sin(m.w0 * t));
-            }
+        a.tfac = g->tfac;
+        a.tfac_base = n0;
+        a.batch = g->batch;
+        if (g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0]) {
+            Timer t(g, 7);
+            CK(g, launch_source<R>(a, g->batch, g->stream));
         }
         {
             Timer t(g, 0);
-            CK(g, launch_xpass<R>(a, g->batch, g->stream));
+            CK(g, launch_xpass<R>(a, mask ? &dx : nullptr, g->batch, g->stream));
         }
         {
             Timer t(g, 1);
-            CK(g, launch_ypass<R>(a, g->batch, g->stream));
+            CK(g, launch_ypass<R>(a, mask ? &dy : nullptr, g->batch, g->stream));
         }
         {
             Timer t(g, 2);
-            CK(g, launch_zpass<R>(a, g->batch, g->stream));
+            CK(g, launch_zpass<R>(a, mask ? &dz : nullptr, g->batch, g->stream));
         }
         g->cur ^= 1;
         ++g->n;
@@ -513,7 +541,7 @@ pstd_status setup_transform(pstd_grid* g)
     CK(g, dalloc(&g->gl_w_dev, sizeof(double) * G));
     CK(g, cudaMemcpy(g->gl_w_dev, g->gl_w.data(), sizeof(double) * G, cudaMemcpyHostToDevice));
     long long cell0 = 0;
-    size_t t1max = 0, outmax = 0;
+    size_t t1max = 0, outmax = 0, specmax = 0;
     for (int f = 0; f < 6; ++f) {
         const int a = f / 2, s = f % 2;
         FaceGeom& F = g->faces[f];
@@ -530,6 +558,8 @@ pstd_status setup_transform(pstd_grid* g)
         F.M = d.huygens_hi[F.c] - d.huygens_lo[F.c];
         F.Nb = d.n[F.b];
         F.Nc = d.n[F.c];
+        F.lo_b = d.huygens_lo[F.b];
+        F.lo_c = d.huygens_lo[F.c];
         F.cell0 = cell0;
         cell0 += (long long)F.L * F.M;
         // trigonometric interpolation weights w(xi - i) = (1/N) sum_{i'=-N/2}^{N/2-1} e^{2 pi i i' (xi - i)/N}
@@ -557,10 +587,27 @@ pstd_status setup_transform(pstd_grid* g)
         CK(g, dalloc(&g->Mc[f], mc.size() * 16));
         CK(g, cudaMemcpy(g->MbT[f], mb.data(), mb.size() * 16, cudaMemcpyHostToDevice));
         CK(g, cudaMemcpy(g->Mc[f], mc.data(), mc.size() * 16, cudaMemcpyHostToDevice));
-        t1max = std::max(t1max, (size_t)F.Nc * F.L * G);
+        t1max = std::max(t1max, (size_t)F.Nc * std::max(F.L * G, F.Nb));
         outmax = std::max(outmax, (size_t)F.M * G * F.L * G);
+        // DFT matrices e^{-2 pi i u v / N} for the plane spectra of the far field
+        for (int q = 0; q < 2; ++q) {
+            const int N = q == 0 ? F.Nb : F.Nc;
+            std::vector<cd> fm((size_t)N * N);
+            for (int u = 0; u < N; ++u)
+                for (int v = 0; v < N; ++v) fm[(size_t)u * N + v] = std::exp(cd(0.0, -2.0 * kPi * (double)((long long)u * v % N) / N));
+            CK(g, dalloc(&g->Fdft[f][q], fm.size() * 16));
+            CK(g, cudaMemcpy(g->Fdft[f][q], fm.data(), fm.size() * 16, cudaMemcpyHostToDevice));
+        }
+        g->ct_off[f] = f == 0 ? 0 : g->ct_off[f - 1] + 2LL * g->faces[f - 1].Nb * g->faces[f - 1].Nc;
+        specmax = std::max(specmax, (size_t)F.Nb * F.Nc);
     }
     g->ncells = cell0;
+    CK(g, dalloc(&g->specP, specmax * 16));
+    CK(g, dalloc(&g->specD, specmax * 16));
+    {
+        const long long ctn = g->ct_off[5] + 2LL * g->faces[5].Nb * g->faces[5].Nc;
+        if (dalloc(&g->ct, (size_t)ctn * g->csize) != cudaSuccess) return fail(g, PSTD_ENOMEM, "far-field spectra");
+    }
     CK(g, dalloc(&g->T1, t1max * 16));
     CK(g, dalloc(&g->OutP, outmax * 16));
     CK(g, dalloc(&g->OutD, outmax * 16));
@@ -611,9 +658,71 @@ template <typename R> pstd_status prepare_records(pstd_grid* g, int b, int f)
     return PSTD_OK;
 }
 
+// far field: per face, the 2-D DFT of the scaled plane phasors, C = F_c P F_b, transposed into
+// the working precision with 1/(N_b N_c) folded in
+template <typename R> pstd_status prepare_far(pstd_grid* g, int b, int f)
+{
+    pstd_status st = setup_transform(g);
+    if (st != PSTD_OK) return st;
+    if (g->ct_member == b && g->ct_freq == f && g->ct_version == g->phasor_version) return PSTD_OK;
+    const cd scale = 1.0 / g->mem[b].inc_phasor[f];   // Eqs. scaledphsiphasor, scaleddpsiphasor
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const double2* base = g->acc + (long long)b * g->acc_freq_stride * g->acc_freq_cap + (long long)f * g->acc_freq_stride;
+    for (int fi = 0; fi < 6; ++fi) {
+        const FaceGeom& F = g->faces[fi];
+        for (int q = 0; q < 2; ++q) {
+            const double2* P = base + g->face_off[fi] + q * g->face_size[fi];   // [Nc][Nb]
+            double2* spec = q == 0 ? g->specP : g->specD;
+            Timer t(g, 4);
+            CK(g, launch_zgemm(F.Nc, F.Nb, F.Nb, P, F.Nb, g->Fdft[fi][0], F.Nb, g->T1, F.Nb,
+                               make_double2(scale.real(), scale.imag()), g->stream));
+            CK(g, launch_zgemm(F.Nc, F.Nb, F.Nc, g->Fdft[fi][1], F.Nc, g->T1, F.Nb, spec, F.Nb, make_double2(1.0, 0.0), g->stream));
+        }
+        Timer t(g, 4);
+        CK(g, launch_spectrum_pack<R>(g->specP, g->specD, F.Nb, F.Nc, 1.0 / ((double)F.Nb * F.Nc),
+                                      static_cast<C*>(g->ct) + g->ct_off[fi], g->stream));
+    }
+    g->ct_member = b;
+    g->ct_freq = f;
+    g->ct_version = g->phasor_version;
+    return PSTD_OK;
+}
+
 template <typename R>
-pstd_status run_transform(pstd_grid* g, int b, int f, const double* pts, const double* theta, const double* phi, long M,
-                          double2* out, double* dsdo, bool far)
+pstd_status run_far(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M, double2* out, double* dsdo,
+                    double2* scratch, long long scratch_elems)
+{
+    pstd_status st = prepare_far<R>(g, b, f);
+    if (st != PSTD_OK) return st;
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    FarArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.ct = static_cast<const C*>(g->ct);
+    for (int fi = 0; fi < 6; ++fi) { a.ct_off[fi] = g->ct_off[fi]; a.face[fi] = g->faces[fi]; }
+    a.theta = theta;
+    a.phi = phi;
+    a.M = M;
+    a.k = g->mem[b].k;
+    // few directions: one CTA per (direction block, face) for parallelism; many: faces summed in-CTA
+    const long long blocks = (M + 31) / 32;
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev);
+    a.face_split = (blocks < 2LL * nsm && 6LL * M <= scratch_elems) ? 6 : 1;
+    if ((long long)a.face_split * M > scratch_elems) return fail(g, PSTD_EINVAL, "directions exceed the scratch capacity");
+    a.partial = scratch;
+    {
+        Timer t(g, 6);
+        CK(g, launch_farfield<R>(a, g->stream));
+    }
+    {
+        Timer t(g, 6);
+        CK(g, launch_reduce_partials(scratch, a.face_split, M, out, dsdo, g->stream));
+    }
+    return PSTD_OK;
+}
+
+template <typename R>
+pstd_status run_transform(pstd_grid* g, int b, int f, const double* pts, long M, double2* out)
 {
     pstd_status st = prepare_records<R>(g, b, f);
     if (st != PSTD_OK) return st;
@@ -624,16 +733,18 @@ pstd_status run_transform(pstd_grid* g, int b, int f, const double* pts, const d
     a.ncells = g->ncells;
     for (int fi = 0; fi < 6; ++fi) a.face[fi] = g->faces[fi];
     a.pts = pts;
-    a.theta = theta;
-    a.phi = phi;
     a.M = M;
     a.k = g->mem[b].k;
     for (int q = 0; q < g->G; ++q) a.gl_node[q] = g->gl_x[q];
-    const long long per_block = 256;
+    const long long per_block = 128;
     const long long blocks = (M + per_block - 1) / per_block;
     const int CH = sizeof(R) == 4 ? 32 : 16;
     const long long chunks = (g->ncells + CH - 1) / CH;
-    long long splits = std::max(1LL, std::min(chunks, (2LL * 152 + blocks - 1) / blocks));
+    // split the surface cells so that about four waves of resident CTAs (7 per SM) run
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev);
+    const long long target = 4LL * 7 * nsm;
+    long long splits = std::max(1LL, std::min(chunks, (target + blocks - 1) / blocks));
     splits = std::min(splits, 4096LL);
     long long cps = ((g->ncells + splits - 1) / splits + CH - 1) / CH * CH;
     splits = (g->ncells + cps - 1) / cps;
@@ -642,12 +753,12 @@ pstd_status run_transform(pstd_grid* g, int b, int f, const double* pts, const d
     if (st != PSTD_OK) return st;
     a.partial = g->partial;
     {
-        Timer t(g, far ? 6 : 5);
-        CK(g, launch_transform<R>(a, g->G, (int)splits, far, g->stream));
+        Timer t(g, 5);
+        CK(g, launch_transform<R>(a, g->G, (int)splits, g->stream));
     }
     {
-        Timer t(g, far ? 6 : 5);
-        CK(g, launch_reduce_partials(g->partial, (int)splits, M, out, dsdo, g->stream));
+        Timer t(g, 5);
+        CK(g, launch_reduce_partials(g->partial, (int)splits, M, out, nullptr, g->stream));
     }
     return PSTD_OK;
 }
@@ -660,48 +771,17 @@ int grid_device(const pstd_grid* g) { return g->dev; }
 
 pstd_status grid_error(pstd_grid* g, pstd_status s, const char* msg) { return fail(g, s, msg); }
 
-// Far field of member b, frequency f, with the per-split partial sums written to a
+// Far field of member b, frequency f, with the per-face partial sums written to a
 // caller-provided device buffer of `scratch_elems` double2 entries instead of the grid's
-// own: nothing is allocated.  The grid's surface records must already exist (they are
+// own: nothing is allocated.  The grid's transform buffers must already exist (they are
 // created by the first pstd_transform_to_points / pstd_cross_section call on the grid).
 template <typename R>
 pstd_status far_field_into_scratch_r(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M,
                                      double* out_dsdo, double2* out_f, double2* scratch, long long scratch_elems)
 {
-    if (!g->MbT[0] || !g->rec)
+    if (!g->MbT[0] || !g->rec || !g->ct)
         return fail(g, PSTD_ESTATE, "surface records not set up: call pstd_cross_section or pstd_transform_to_points once first");
-    pstd_status st = prepare_records<R>(g, b, f);
-    if (st != PSTD_OK) return st;
-    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
-    TransformArgs<R> a;
-    std::memset(&a, 0, sizeof(a));
-    a.rec = static_cast<const C*>(g->rec);
-    a.ncells = g->ncells;
-    for (int fi = 0; fi < 6; ++fi) a.face[fi] = g->faces[fi];
-    a.theta = theta;
-    a.phi = phi;
-    a.M = M;
-    a.k = g->mem[b].k;
-    for (int q = 0; q < g->G; ++q) a.gl_node[q] = g->gl_x[q];
-    const long long blocks = (M + 255) / 256;
-    const int CH = sizeof(R) == 4 ? 32 : 16;
-    const long long chunks = (g->ncells + CH - 1) / CH;
-    long long splits = std::max(1LL, std::min(chunks, (2LL * 152 + blocks - 1) / blocks));
-    splits = std::min(splits, std::max(1LL, scratch_elems / (long long)M));
-    long long cps = ((g->ncells + splits - 1) / splits + CH - 1) / CH * CH;
-    splits = (g->ncells + cps - 1) / cps;
-    if (splits * (long long)M > scratch_elems) return fail(g, PSTD_EINVAL, "directions exceed the scratch capacity");
-    a.cells_per_split = cps;
-    a.partial = scratch;
-    {
-        Timer t(g, 6);
-        CK(g, launch_transform<R>(a, g->G, (int)splits, true, g->stream));
-    }
-    {
-        Timer t(g, 6);
-        CK(g, launch_reduce_partials(scratch, (int)splits, M, out_f, out_dsdo, g->stream));
-    }
-    return PSTD_OK;
+    return run_far<R>(g, b, f, theta, phi, M, out_f, out_dsdo, scratch, scratch_elems);
 }
 
 pstd_status far_field_into_scratch(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M,
@@ -806,7 +886,7 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     DeviceGuard dg(g->dev);
     cudaStreamSynchronize(g->stream);
     for (void* p : {g->buf[0], g->buf[1], g->V, (void*)g->mem_dev, (void*)g->acc, (void*)g->flag, (void*)g->gl_w_dev,
-                    (void*)g->dft_phase, (void*)g->window_first_dev,
+                    (void*)g->dft_phase, (void*)g->window_first_dev, (void*)g->tfac,
                     (void*)g->T1, (void*)g->OutP, (void*)g->OutD, g->rec, (void*)g->partial, (void*)g->pts_dev,
                     (void*)g->out_dev, (void*)g->dsdo_dev})
         if (p) cudaFree(p);
@@ -816,7 +896,11 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     for (int f = 0; f < 6; ++f) {
         if (g->MbT[f]) cudaFree(g->MbT[f]);
         if (g->Mc[f]) cudaFree(g->Mc[f]);
+        for (int q = 0; q < 2; ++q)
+            if (g->Fdft[f][q]) cudaFree(g->Fdft[f][q]);
     }
+    for (void* p : {(void*)g->specP, (void*)g->specD, g->ct})
+        if (p) cudaFree(p);
     for (auto& t : g->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto e : g->event_pool) cudaEventDestroy(e);
     delete g;
@@ -1046,8 +1130,7 @@ pstd_status pstd_transform_to_points(pstd_grid* g, int b, int f, const double* x
         pts = g->pts_dev;
         out = g->out_dev;
     }
-    st = g->prec == PSTD_F64 ? run_transform<double>(g, b, f, pts, nullptr, nullptr, M, out, nullptr, false)
-                             : run_transform<float>(g, b, f, pts, nullptr, nullptr, M, out, nullptr, false);
+    st = g->prec == PSTD_F64 ? run_transform<double>(g, b, f, pts, M, out) : run_transform<float>(g, b, f, pts, M, out);
     if (st != PSTD_OK) return st;
     if (mem == PSTD_MEM_HOST) return copy_out(g, out_psi, g->out_dev, sizeof(double2) * M, PSTD_MEM_HOST);
     return PSTD_OK;
@@ -1084,8 +1167,10 @@ pstd_status pstd_cross_section(pstd_grid* g, int b, int f, const double* theta, 
         if (st != PSTD_OK) return st;
         fo = g->out_dev;
     }
-    st = g->prec == PSTD_F64 ? run_transform<double>(g, b, f, nullptr, th, ph, M, fo, ds, true)
-                             : run_transform<float>(g, b, f, nullptr, th, ph, M, fo, ds, true);
+    st = ensure(g, &g->partial, g->partial_cap, sizeof(double2) * 6 * (size_t)M);
+    if (st != PSTD_OK) return st;
+    st = g->prec == PSTD_F64 ? run_far<double>(g, b, f, th, ph, M, fo, ds, g->partial, 6LL * M)
+                             : run_far<float>(g, b, f, th, ph, M, fo, ds, g->partial, 6LL * M);
     if (st != PSTD_OK) return st;
     if (mem == PSTD_MEM_HOST) {
         CK(g, cudaMemcpyAsync(out_dsdo, g->dsdo_dev, sizeof(double) * M, cudaMemcpyDeviceToHost, g->stream));

@@ -1,13 +1,15 @@
-// Double-precision instantiations of the step, plane-DFT and transform kernels.
+// Double-precision instantiations of the step (with the fused running DFT) and transform kernels.
 #include "ntdf_kernels.cuh"
 #include "step_kernels.cuh"
 
 namespace pstd {
-template cudaError_t launch_xpass<double>(const StepArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_ypass<double>(const StepArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_zpass<double>(const StepArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_plane_dft<double>(const DftArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_transform<double>(const TransformArgs<double>&, int, int, bool, cudaStream_t);
+template cudaError_t launch_xpass<double>(const StepArgs<double>&, const DftArgs<double>*, int, cudaStream_t);
+template cudaError_t launch_ypass<double>(const StepArgs<double>&, const DftArgs<double>*, int, cudaStream_t);
+template cudaError_t launch_zpass<double>(const StepArgs<double>&, const DftArgs<double>*, int, cudaStream_t);
+template cudaError_t launch_source<double>(const StepArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_transform<double>(const TransformArgs<double>&, int, int, cudaStream_t);
+template cudaError_t launch_farfield<double>(const FarArgs<double>&, cudaStream_t);
+template cudaError_t launch_spectrum_pack<double>(const double2*, const double2*, int, int, double, double2*, cudaStream_t);
 template cudaError_t launch_pack_records<double>(const double2*, const double2*, int, int, int, const double*, double,
                                                 long long, double2*, cudaStream_t);
 }  // namespace pstd

@@ -1,6 +1,8 @@
-// Near-to-distant-field transform (Section 3): per surface cell, the integral of the
-// trigonometric interpolant psi_an (Eq. AnBottomPsi) times the linearised Green's
-// phase e^{-ik Rhat . dr'} (the approximation behind Eqs. bottomPsi_lm ... leftrightPsi_ln),
+// Near-to-distant-field transform (Section 3).
+//
+// Points (transform_kernel): per surface cell, the integral of the trigonometric
+// interpolant psi_an (Eq. AnBottomPsi) times the linearised Green's phase
+// e^{-ik Rhat . dr'} (the approximation behind Eqs. bottomPsi_lm ... leftrightPsi_ln),
 //
 //   Psi_cell(r) = -sigma/(4 pi) e^{ikR}/R  int_cell [d_a psi_an + (ik - 1/R) Rhat_a psi_an] e^{-ik Rhat . dr'} dS',
 //
@@ -10,8 +12,17 @@
 // nodes factors into e_g(axis b) f_h(axis c).  The distance is split as
 // R = R0 + dR, R0 = |r - face centre| in double precision and
 // dR = (|dc|^2 - 2 d0 . dc) / (R + R0) in the working precision, so single-precision
-// phases stay accurate at kR ~ 10^3.  Far field: e^{ikR}/R -> e^{-ik rhat . r_c} and
-// Rhat -> rhat, (ik - 1/R) -> ik.
+// phases stay accurate at kR ~ 10^3.
+//
+// Far field (farfield_kernel): in the r -> infinity limit the per-cell phase is exactly
+// linear across the whole face, so the sum over cells of the per-cell sinc sums of
+// Eq. bottomPsi_lm factorises.  With C the 2-D DFT of the plane (Eq. AnBottomPsi),
+//   f_face = -sigma D_b D_c / (4 pi N_b N_c) e^{-ik rhat_a a_plane}
+//            sum_{i',j'} C[j', i'] at_{i'} bt_{j'} [d_a-plane ... ]
+//   at_{i'} = sum_l (-1)^{i'} e^{2 pi i i' x^c_l / L_b} sinc(pi i'/N_b - k D_b rhat_b / 2) e^{-ik rhat_b x^c_l}
+//           = n sinc(n phi / 2) e^{i (k rhat_b L_b / 2 + phi (lo + hi) / 2)},  phi = 2 pi i'/N_b - k rhat_b D_b,
+// n = hi - lo surface cells along b (and bt likewise along c): the paper's far-field sum in
+// closed form, N_b N_c multiply-adds per direction and face.
 #pragma once
 
 #include <type_traits>
@@ -50,9 +61,7 @@ template <typename R> __device__ __forceinline__ void sincos_mid(R x, R* s, R* c
 }
 
 constexpr int kTransformThreads = 128;
-// observation points per thread: near field 1 (keeps registers low enough for 4 resident
-// CTAs), far field 2 (the node phases are per point and face, so records are reused)
-template <bool FAR> __host__ __device__ constexpr int transform_pt() { return FAR ? 2 : 1; }
+constexpr int kTransformPT = 1;   // one point per thread keeps registers low enough for 7 resident CTAs
 
 // Cell records hold, for psi and for d psi/d a, the node values (quadrature weights and
 // cell Jacobian folded in) regrouped over the mirrored Gauss-Legendre nodes
@@ -99,14 +108,14 @@ __device__ __forceinline__ void node_sum(const C* __restrict__ rec, const declty
     id_out = cadd(id_out, cadd(ida[0], ida[1]));
 }
 
-template <typename R, int G, bool FAR>
-__global__ void __launch_bounds__(kTransformThreads) transform_kernel(TransformArgs<R> a)
+template <typename R, int G>
+__global__ void __launch_bounds__(kTransformThreads) transform_kernel(const __grid_constant__ TransformArgs<R> a)
 {
     using C = typename TransformArgs<R>::C;
     constexpr int H = G / 2;
     constexpr int REC = 2 * G * G;
     constexpr int CH = sizeof(R) == 4 ? 32 : 16;
-    constexpr int PT = transform_pt<FAR>();
+    constexpr int PT = kTransformPT;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* srec = reinterpret_cast<C*>(smraw);
     const double k = a.k;
@@ -119,14 +128,7 @@ __global__ void __launch_bounds__(kTransformThreads) transform_kernel(TransformA
         pidx[i] = (long long)blockIdx.x * (kTransformThreads * PT) + i * kTransformThreads + threadIdx.x;
         valid[i] = pidx[i] < a.M;
         const long long p = valid[i] ? pidx[i] : 0;
-        if (FAR) {
-            double st, ct, sp, cp;
-            sincos(a.theta[p], &st, &ct);
-            sincos(a.phi[p], &sp, &cp);
-            px[i] = st * cp; py[i] = st * sp; pz[i] = ct;
-        } else {
-            px[i] = a.pts[3 * p + 0]; py[i] = a.pts[3 * p + 1]; pz[i] = a.pts[3 * p + 2];
-        }
+        px[i] = a.pts[3 * p + 0]; py[i] = a.pts[3 * p + 1]; pz[i] = a.pts[3 * p + 2];
     }
     double accx[PT], accy[PT];
 #pragma unroll
@@ -147,36 +149,22 @@ __global__ void __launch_bounds__(kTransformThreads) transform_kernel(TransformA
         const double cbm = F.cb0 + 0.5 * (F.L - 1) * F.db;
         const double ccm = F.cc0 + 0.5 * (F.M - 1) * F.dc;
         const R hkb = R(0.5 * k * F.db), hkc = R(0.5 * k * F.dc);
-        // per point: d0 = r - c0 (components along a, b, c) and R0, e^{ikR0} (near), or the
-        // direction, e^{-ik rhat . c0} and the node phases (far: the same for every cell)
+        // per point: d0 = r - c0 (components along a, b, c), R0 and e^{ikR0}
         R d0a[PT], d0b[PT], d0c[PT];
         R R0[PT];
         C ph0[PT];
-        R fcb[PT][H], fsb[PT][H], fcc[PT][H], fsc[PT][H];
 #pragma unroll
         for (int i = 0; i < PT; ++i) {
             const double pa = F.axis == 0 ? px[i] : F.axis == 1 ? py[i] : pz[i];
             const double pb = F.b == 0 ? px[i] : F.b == 1 ? py[i] : pz[i];
             const double pc = F.c == 0 ? px[i] : F.c == 1 ? py[i] : pz[i];
             double s, c;
-            if (FAR) {
-                d0a[i] = R(pa); d0b[i] = R(pb); d0c[i] = R(pc);
-                R0[i] = R(0);
-                sincos(-k * (pa * F.plane + pb * cbm + pc * ccm), &s, &c);
-                ph0[i] = mk<C>(R(c), R(s));
-#pragma unroll
-                for (int g = 0; g < H; ++g) {
-                    sincos_small<R>(hkb * d0b[i] * node[g], &fsb[i][g], &fcb[i][g]);
-                    sincos_small<R>(hkc * d0c[i] * node[g], &fsc[i][g], &fcc[i][g]);
-                }
-            } else {
-                const double da = pa - F.plane, db = pb - cbm, dc = pc - ccm;
-                d0a[i] = R(da); d0b[i] = R(db); d0c[i] = R(dc);
-                const double r0 = sqrt(da * da + db * db + dc * dc);
-                R0[i] = R(r0);
-                sincos(k * r0, &s, &c);
-                ph0[i] = mk<C>(R(c), R(s));
-            }
+            const double da = pa - F.plane, db = pb - cbm, dc = pc - ccm;
+            d0a[i] = R(da); d0b[i] = R(db); d0c[i] = R(dc);
+            const double r0 = sqrt(da * da + db * db + dc * dc);
+            R0[i] = R(r0);
+            sincos(k * r0, &s, &c);
+            ph0[i] = mk<C>(R(c), R(s));
         }
         const R kr = R(k);
         const R pref = R(-F.sigma / (4.0 * 3.14159265358979323846));
@@ -198,16 +186,9 @@ __global__ void __launch_bounds__(kTransformThreads) transform_kernel(TransformA
 #pragma unroll
                 for (int i = 0; i < PT; ++i) {
                     C ip = mk<C>(R(0), R(0)), id = mk<C>(R(0), R(0));
-                    C w;               // e^{ikR}/R (near) or e^{-ik rhat . r_c} (far)
+                    C w;               // e^{ikR}/R
                     R ha, cfr;         // bracket = Id + (cfr + i k) ha Ip
-                    if (FAR) {
-                        R s, c;
-                        sincos_mid<R>(-kr * (d0b[i] * dcb + d0c[i] * dcc), &s, &c);
-                        w = cmul(ph0[i], mk<C>(c, s));
-                        node_sum<C, H>(P, fcb[i], fsb[i], fcc[i], fsc[i], ip, id);
-                        ha = d0a[i];
-                        cfr = R(0);
-                    } else {
+                    {
                         const R rb = d0b[i] - dcb, rc = d0c[i] - dcc, ra = d0a[i];
                         const R q = dcb * dcb + dcc * dcc - R(2) * (d0b[i] * dcb + d0c[i] * dcc);
                         const R R2 = ra * ra + rb * rb + rc * rc;
@@ -249,32 +230,185 @@ __global__ void __launch_bounds__(kTransformThreads) transform_kernel(TransformA
         if (valid[i]) a.partial[(long long)blockIdx.y * a.M + pidx[i]] = make_double2(accx[i], accy[i]);
 }
 
-template <typename R, int G> cudaError_t transform_g(const TransformArgs<R>& a, int splits, bool far, cudaStream_t s)
+template <typename R, int G> cudaError_t transform_g(const TransformArgs<R>& a, int splits, cudaStream_t s)
 {
     using C = typename TransformArgs<R>::C;
     constexpr int CH = sizeof(R) == 4 ? 32 : 16;
     const size_t sm = sizeof(C) * CH * 2 * G * G;
-    const int pt = far ? transform_pt<true>() : transform_pt<false>();
-    dim3 grid((unsigned)((a.M + kTransformThreads * pt - 1) / (kTransformThreads * pt)), splits);
-    if (far) {
-        cudaError_t e = cudaFuncSetAttribute(transform_kernel<R, G, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        transform_kernel<R, G, true><<<grid, kTransformThreads, sm, s>>>(a);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(transform_kernel<R, G, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        transform_kernel<R, G, false><<<grid, kTransformThreads, sm, s>>>(a);
-    }
+    dim3 grid((unsigned)((a.M + kTransformThreads * kTransformPT - 1) / (kTransformThreads * kTransformPT)), splits);
+    transform_kernel<R, G><<<grid, kTransformThreads, sm, s>>>(a);
     return cudaGetLastError();
 }
 
-template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, int G, int splits, bool far, cudaStream_t s)
+template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, int G, int splits, cudaStream_t s)
 {
     switch (G) {
-    case 6: return transform_g<R, 6>(a, splits, far, s);
-    case 8: return transform_g<R, 8>(a, splits, far, s);
+    case 6: return transform_g<R, 6>(a, splits, s);
+    case 8: return transform_g<R, 8>(a, splits, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+// ---------------------------------------------------------------------------------
+// far field from the plane spectra
+// ---------------------------------------------------------------------------------
+constexpr int kFarDirs = 32;       // directions per CTA (one per lane)
+constexpr int kFarWarps = 8;       // warps split the j' columns in chunks of 4
+
+// n sinc(n phi / 2) e^{i psi}, phi = 2 pi m'/N - k rhat D, psi = k rhat L / 2 + phi (lo + n/2)
+// (see the header).  psi is split as base + pi ((m' (2 lo + n)) mod 2N) / N with
+// base = k rhat (L/2 - D (lo + n/2)) evaluated in double and reduced to [-pi, pi] once per
+// direction and face, so the single-precision phase stays exact to rounding of O(1) values.
+template <typename R, typename C>
+__device__ __forceinline__ C face_factor(int m, int N, R krd, R base, int lo, int n)
+{
+    const int mp = m < (N + 1) / 2 ? m : m - N;          // index order -N/2..N/2-1
+    const R phi = R(6.283185307179586476925286766559) * R(mp) / R(N) - krd;
+    const R x = R(0.5) * R(n) * phi;
+    R sx, cx;
+    sincos_mid<R>(x, &sx, &cx);
+    const R amp = fabs(x) < R(1e-6) ? R(n) : R(n) * sx / x;
+    const int twoN = 2 * N;
+    const int q = ((mp * (2 * lo + n)) % twoN + twoN) % twoN;
+    R sp, cp;
+    sincos_mid<R>(base + R(3.14159265358979323846) * R(q) / R(N), &sp, &cp);
+    return mk<C>(amp * cp, amp * sp);
+}
+
+__device__ __forceinline__ double reduce_2pi(double x)
+{
+    return x - 6.283185307179586476925286766559 * rint(x * 0.15915494309189533576888376337251);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kFarDirs * kFarWarps) farfield_kernel(const __grid_constant__ FarArgs<R> a)
+{
+    using C = typename FarArgs<R>::C;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sa = reinterpret_cast<C*>(smraw);                       // [kFarDirs][Nb + 1]
+    __shared__ C red[kFarWarps][2][kFarDirs];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long p = (long long)blockIdx.x * kFarDirs + lane;
+    const bool valid = p < a.M;
+    const long long pc = valid ? p : 0;
+    double st, ct, sp, cp;
+    sincos(a.theta[pc], &st, &ct);
+    sincos(a.phi[pc], &sp, &cp);
+    const double rh[3] = {st * cp, st * sp, ct};
+    const double k = a.k;
+    double tx = 0.0, ty = 0.0;
+    const int f_first = a.face_split == 6 ? (int)blockIdx.y : 0;
+    const int f_last = a.face_split == 6 ? (int)blockIdx.y + 1 : 6;
+    for (int fi = f_first; fi < f_last; ++fi) {
+        const FaceGeom F = a.face[fi];
+        const int pitch = F.Nb + 1;
+        const double rb = rh[F.b], rc = rh[F.c], ra = rh[F.axis];
+        // at_{i'} for this lane's direction
+        {
+            const R krd = R(k * rb * F.db);
+            const R base = R(reduce_2pi(k * rb * (0.5 * F.Nb * F.db - F.db * (F.lo_b + 0.5 * F.L))));
+            for (int m = w; m < F.Nb; m += kFarWarps)
+                sa[lane * pitch + m] = face_factor<R, C>(m, F.Nb, krd, base, F.lo_b, F.L);
+        }
+        __syncthreads();
+        const R krd_c = R(k * rc * F.dc);
+        const R base_c = R(reduce_2pi(k * rc * (0.5 * F.Nc * F.dc - F.dc * (F.lo_c + 0.5 * F.M))));
+        const C* ctp = a.ct + a.ct_off[fi];                        // [q][m][j]
+        const C* ctd = ctp + (long long)F.Nb * F.Nc;
+        C sp_tot = mk<C>(R(0), R(0)), sd_tot = mk<C>(R(0), R(0));
+        for (int j0 = 4 * w; j0 < F.Nc; j0 += 4 * kFarWarps) {
+            C ap[4], ad[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) { ap[jj] = mk<C>(R(0), R(0)); ad[jj] = mk<C>(R(0), R(0)); }
+            const C* rp = ctp + j0;
+            const C* rd = ctd + j0;
+            const C* arow = sa + lane * pitch;
+#pragma unroll 4
+            for (int m = 0; m < F.Nb; ++m) {
+                const C av = arow[m];
+                C cpv[4], cdv[4];
+                if constexpr (sizeof(R) == 4) {
+                    const float4 p0 = __ldg(reinterpret_cast<const float4*>(rp + (long long)m * F.Nc));
+                    const float4 p1 = __ldg(reinterpret_cast<const float4*>(rp + (long long)m * F.Nc) + 1);
+                    const float4 d0 = __ldg(reinterpret_cast<const float4*>(rd + (long long)m * F.Nc));
+                    const float4 d1 = __ldg(reinterpret_cast<const float4*>(rd + (long long)m * F.Nc) + 1);
+                    cpv[0] = mk<C>(p0.x, p0.y); cpv[1] = mk<C>(p0.z, p0.w); cpv[2] = mk<C>(p1.x, p1.y); cpv[3] = mk<C>(p1.z, p1.w);
+                    cdv[0] = mk<C>(d0.x, d0.y); cdv[1] = mk<C>(d0.z, d0.w); cdv[2] = mk<C>(d1.x, d1.y); cdv[3] = mk<C>(d1.z, d1.w);
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) { cpv[jj] = __ldg(rp + (long long)m * F.Nc + jj); cdv[jj] = __ldg(rd + (long long)m * F.Nc + jj); }
+                }
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    ap[jj].x += av.x * cpv[jj].x - av.y * cpv[jj].y;
+                    ap[jj].y += av.x * cpv[jj].y + av.y * cpv[jj].x;
+                    ad[jj].x += av.x * cdv[jj].x - av.y * cdv[jj].y;
+                    ad[jj].y += av.x * cdv[jj].y + av.y * cdv[jj].x;
+                }
+            }
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+                const C bt = face_factor<R, C>(j0 + jj, F.Nc, krd_c, base_c, F.lo_c, F.M);
+                sp_tot = cadd(sp_tot, cmul(bt, ap[jj]));
+                sd_tot = cadd(sd_tot, cmul(bt, ad[jj]));
+            }
+        }
+        red[w][0][lane] = sp_tot;
+        red[w][1][lane] = sd_tot;
+        __syncthreads();
+        if (w == 0) {
+            double spx = 0, spy = 0, sdx = 0, sdy = 0;
+            for (int t = 0; t < kFarWarps; ++t) {
+                spx += double(red[t][0][lane].x); spy += double(red[t][0][lane].y);
+                sdx += double(red[t][1][lane].x); sdy += double(red[t][1][lane].y);
+            }
+            // -sigma D_b D_c / (4 pi) e^{-ik rhat_a a_plane} (S_d + i k rhat_a S_psi)
+            double s0, c0;
+            sincos(-k * ra * F.plane, &s0, &c0);
+            const double bx = sdx - k * ra * spy, by = sdy + k * ra * spx;
+            const double pref = -F.sigma * F.db * F.dc / (4.0 * 3.14159265358979323846);
+            tx += pref * (c0 * bx - s0 * by);
+            ty += pref * (c0 * by + s0 * bx);
+        }
+        __syncthreads();
+    }
+    if (w == 0 && valid) a.partial[(long long)(a.face_split == 6 ? blockIdx.y : 0) * a.M + p] = make_double2(tx, ty);
+}
+
+template <typename R> cudaError_t launch_farfield(const FarArgs<R>& a, cudaStream_t s)
+{
+    using C = typename FarArgs<R>::C;
+    int nbmax = 0;
+    for (int f = 0; f < 6; ++f) nbmax = max(nbmax, a.face[f].Nb);
+    const size_t sm = sizeof(C) * kFarDirs * (size_t)(nbmax + 1);
+    cudaError_t e = cudaFuncSetAttribute(farfield_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((unsigned)((a.M + kFarDirs - 1) / kFarDirs), a.face_split);
+    farfield_kernel<R><<<grid, kFarDirs * kFarWarps, sm, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename R, typename C>
+__global__ void spectrum_pack_kernel(const double2* __restrict__ cp, const double2* __restrict__ cd, int Nb, int Nc,
+                                     double scale, C* __restrict__ ct)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)Nb * Nc;
+    if (e >= n) return;
+    const int j = (int)(e % Nc), m = (int)(e / Nc);          // output [m][j]
+    const double2 vp = cp[(long long)j * Nb + m], vd = cd[(long long)j * Nb + m];
+    ct[e] = mk<C>(R(vp.x * scale), R(vp.y * scale));
+    ct[n + e] = mk<C>(R(vd.x * scale), R(vd.y * scale));
+}
+
+template <typename R>
+cudaError_t launch_spectrum_pack(const double2* c_psi, const double2* c_dpsi, int Nb, int Nc, double scale,
+                                 typename std::conditional<sizeof(R) == 4, float2, double2>::type* ct, cudaStream_t s)
+{
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const long long n = (long long)Nb * Nc;
+    spectrum_pack_kernel<R, C><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c_psi, c_dpsi, Nb, Nc, scale, ct);
+    return cudaGetLastError();
 }
 
 template <typename R, typename C>

@@ -44,10 +44,12 @@ template <typename R> struct StepArgs {
     double dt, hbar, mass;
     int mode;                // PSTD_TFSF_EXACT / PSTD_TFSF_PAPER
     int* flag;               // bit 0: non-finite value written
-    double2 tfac[PSTD_MAX_BATCH];   // a(t_n) e^{-i w0 t_n} per member, evaluated on the host in FP64
+    const double2* tfac;     // a(t_n) e^{-i w0 t_n}: [(n - tfac_base) * batch + member], host-built in FP64
+    long long tfac_base;
+    int batch;
 };
 
-// Plane DFT arguments (one launch per axis).
+// Running-DFT arguments for the passes that accumulate on DFT-window steps.
 template <typename R> struct DftArgs {
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
     const C* cur;
@@ -71,10 +73,12 @@ template <typename R> struct DftArgs {
     const long long* window_first;  // per member
 };
 
-template <typename R> cudaError_t launch_xpass(const StepArgs<R>& a, int batch, cudaStream_t s);
-template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, int batch, cudaStream_t s);
-template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, int batch, cudaStream_t s);
-template <typename R> cudaError_t launch_plane_dft(const DftArgs<R>& a, int batch, cudaStream_t s);
+// d == nullptr: plain pass; otherwise the pass also accumulates the running DFT on the two
+// virtual planes normal to its axis (d->axis must match the pass)
+template <typename R> cudaError_t launch_xpass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s);
+template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s);
+template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s);
+template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------
 // surface-equivalence transform
@@ -87,17 +91,38 @@ struct FaceGeom {
     double cb0, cc0;          // centre coordinates of the first surface cell along b, c
     int L, M;                 // surface cells along b, c
     int Nb, Nc;               // plane size
+    int lo_b, lo_c;           // first surface-cell node index along b, c
     long long cell0;          // index of the face's first cell in the global cell order
 };
+
+// Far field from the plane spectra (see farfield_kernel): per face, the 2-D DFT of the
+// scaled psi and d psi/d a planes, transposed to [q][i'][j'] and divided by N_b N_c.
+template <typename R> struct FarArgs {
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const C* ct;              // spectra, faces back to back
+    long long ct_off[6];
+    FaceGeom face[6];
+    const double* theta;
+    const double* phi;
+    long long M;
+    double k;
+    int face_split;           // 1: every block sums all faces; 6: blockIdx.y selects the face
+    double2* partial;         // [face_split][M]
+};
+
+template <typename R> cudaError_t launch_farfield(const FarArgs<R>& a, cudaStream_t s);
+// Ct[q][m][j] = scale * C[q][j][m] in the working precision (C from double2, [Nc][Nb] per quantity)
+template <typename R> cudaError_t launch_spectrum_pack(const double2* c_psi, const double2* c_dpsi, int Nb, int Nc,
+                                                       double scale,
+                                                       typename std::conditional<sizeof(R) == 4, float2, double2>::type* ct,
+                                                       cudaStream_t s);
 
 template <typename R> struct TransformArgs {
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
     const C* rec;             // per cell: G*G psi node values then G*G dpsi node values (weights folded in)
     long long ncells;
     FaceGeom face[6];
-    const double* pts;        // M x 3 points (or directions for the far field)
-    const double* theta;      // far field: angles (when pts == nullptr)
-    const double* phi;
+    const double* pts;        // M x 3 points
     long long M;
     double k;
     double gl_node[16];       // Gauss-Legendre nodes on [-1, 1]
@@ -105,8 +130,7 @@ template <typename R> struct TransformArgs {
     double2* partial;         // [split][M]
 };
 
-template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, int G, int splits, bool far,
-                                                  cudaStream_t s);
+template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, int G, int splits, cudaStream_t s);
 cudaError_t launch_reduce_partials(const double2* partial, int splits, long long M, double2* out,
                                    double* dsdo, cudaStream_t s);
 // complex double GEMM C[MxN] = alpha * A[MxK] B[KxN] (row-major, leading dims given)

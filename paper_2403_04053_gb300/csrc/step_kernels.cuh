@@ -2,19 +2,19 @@
 // three line passes that each apply one axis of the spectral kinetic operator
 // K = sum_a F_a^-1[k_a^2 F_a] (Eq. spatialFFTeigen) to psi^n:
 //
-//   x pass:  prev <- psi^{n-1} - i (dt hbar eta / m) K_x psi^n - (2 i dt / hbar) (V-term + source)
-//   y pass:  prev <- prev       - i (dt hbar eta / m) K_y psi^n
+//   source:  prev <- psi^{n-1} - (2 i dt / hbar) (V-term + source)   (support box only)
+//   x pass:  prev <- prev - i (dt hbar eta / m) K_x psi^n
+//   y pass:  prev <- prev - i (dt hbar eta / m) K_y psi^n
 //   z pass:  prev <- Gamma * [prev - i (dt hbar eta / m) K_z psi^n]
 //
 // so the buffer that held psi^{n-1} ends up holding psi^{n+1}.  The V-term and the
-// source sit in the x pass, whose epilogue walks the tile in memory order: its extra
-// reads of psi^n inside the potential's support are coalesced and independent.  They
-// are evaluated in registers from 1-D tables (no extra HBM traffic outside the
-// potential's support):
+// source run as their own element-wise kernel over the box where they are non-zero
+// (one independent read-modify-write per cell, nothing serialised behind an FFT),
+// evaluated in registers from 1-D tables:
 //   EXACT form : V (psi^n + psi_inc^n)                       (state = scattered field)
 //   PAPER form : V psi~^n + hbar^2/2m psi_inc^n [lap zeta + 2 i k . grad zeta]  (Eq. tildeSchrodinger)
 // with psi_inc^n(r) = a(t_n) e^{-i w0 t_n} prod_a e^{i k_a (x_a - r_O,a)}; the time factor
-// is evaluated in double precision from n on the device.
+// is tabulated in double precision on the host for the steps of each pstd_step call.
 #pragma once
 
 #include <type_traits>
@@ -23,13 +23,6 @@
 #include "pstd_internal.h"
 
 namespace pstd {
-
-__device__ __forceinline__ double envelope_dev(double t, double ramp)
-{
-    if (ramp <= 0.0 || t >= ramp) return 1.0;
-    if (t <= 0.0) return 0.0;
-    return 0.5 * (1.0 - cos(3.14159265358979323846 * t / ramp));
-}
 
 template <typename R, typename C> __device__ __forceinline__ C zero_c() { return mk<C>(R(0), R(0)); }
 
@@ -56,161 +49,13 @@ __device__ __forceinline__ C incident_at(const StepArgs<R>& a, int b, C s, int x
 }
 
 // ---------------------------------------------------------------------------------
-// x pass: 32 consecutive rows per CTA, staged through shared memory (rows are
-// contiguous, so the tile is one contiguous block of 32 * nx values)
-// ---------------------------------------------------------------------------------
-template <typename R, int N>
-__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) xpass_kernel(StepArgs<R> a)
-{
-    using C = typename StepArgs<R>::C;
-    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
-    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
-    const int b = blockIdx.y;
-    const int rows = a.ny * a.nz;
-    const int row0 = blockIdx.x * kLanes;
-    const int nrows = min(kLanes, rows - row0);
-    const long long tile0 = (long long)b * a.ncell + (long long)row0 * N;
-    for (int e = threadIdx.x; e < kLanes * N; e += blockDim.x) {
-        const int r = e / N, x = e - r * N;
-        sm[x * kPitch + r] = r < nrows ? a.cur[tile0 + e] : zero_c<R, C>();
-    }
-    __syncthreads();
-    C v[E];
-    const R eta = R(a.mem[b].eta);
-    kinetic_line<N, true>(v, sm, lane, j, a.tw[0], a.kin[0], eta);
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < E; ++q) sm[slot_pos<N, T, R0>(q, j) * kPitch + lane] = v[q];
-    __syncthreads();
-    const C s = mk<C>(R(a.tfac[b].x), R(a.tfac[b].y));   // a(t_n) e^{-i w0 t_n}
-    const R c2 = R(2.0 * a.dt / a.hbar);
-    const bool paper = a.mode == PSTD_TFSF_PAPER;
-    const int vnx = a.vhi[0] - a.vlo[0], vny = a.vhi[1] - a.vlo[1];
-    for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
-        const int r = e / N, x = e - r * N;
-        const C w = sm[x * kPitch + r];
-        const C p = a.prev[tile0 + e];
-        C acc = mk<C>(p.x + w.y, p.y - w.x);   // p - i w
-        const int row = row0 + r, y = row % a.ny, z = row / a.ny;
-        if (x >= a.vlo[0] && x < a.vhi[0] && y >= a.vlo[1] && y < a.vhi[1] && z >= a.vlo[2] && z < a.vhi[2]) {
-            const R Vv = a.V[((long long)(z - a.vlo[2]) * vny + (y - a.vlo[1])) * vnx + (x - a.vlo[0])];
-            C src = a.cur[tile0 + e];
-            if (!paper) src = cadd(src, incident_at<R, C>(a, b, s, x, y, z));
-            const R cv = c2 * Vv;
-            acc.x += cv * src.y;
-            acc.y -= cv * src.x;
-        }
-        if (paper && x > a.tf_lo[0] && x < a.tf_hi[0] && y > a.tf_lo[1] && y < a.tf_hi[1] && z > a.tf_lo[2] &&
-            z < a.tf_hi[2]) {
-            const R zx = a.zeta[0][x], zx1 = a.zeta1[0][x], zx2 = a.zeta2[0][x];
-            const R zy = a.zeta[1][y], zy1 = a.zeta1[1][y], zy2 = a.zeta2[1][y];
-            const R zz = a.zeta[2][z], zz1 = a.zeta1[2][z], zz2 = a.zeta2[2][z];
-            const R lap = zx2 * zy * zz + zx * zy2 * zz + zx * zy * zz2;
-            const MemberDev& md = a.mem[b];
-            const R kg = R(md.k[0]) * zx1 * zy * zz + R(md.k[1]) * zx * zy1 * zz + R(md.k[2]) * zx * zy * zz1;
-            // hbar^2/2m psi_inc (lap + 2 i kg), times -(2 i dt / hbar)
-            const R h2m = R(a.hbar * a.hbar / (2.0 * a.mass));
-            const C S = cscale(cmul(incident_at<R, C>(a, b, s, x, y, z), mk<C>(lap, R(2) * kg)), h2m);
-            acc.x += c2 * S.y;
-            acc.y -= c2 * S.x;
-        }
-        a.prev[tile0 + e] = acc;
-    }
-}
-
-// ---------------------------------------------------------------------------------
-// y pass: lines along y, 32 consecutive x per CTA (lane = x), coalesced in place
-// ---------------------------------------------------------------------------------
-template <typename R, int N>
-__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) ypass_kernel(StepArgs<R> a)
-{
-    using C = typename StepArgs<R>::C;
-    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
-    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
-    const int x = blockIdx.x * kLanes + lane;
-    const int z = blockIdx.y, b = blockIdx.z;
-    const bool act = x < a.nx;
-    const long long stride = a.nx;
-    const long long base = (long long)b * a.ncell + (long long)z * a.nx * a.ny + x;
-    C v[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) v[q] = act ? a.cur[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
-#if PSTD_PREFETCH_PREV
-    C pv[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) pv[q] = act ? a.prev[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
-#endif
-    const R eta = R(a.mem[b].eta);
-    kinetic_line<N, false>(v, sm, lane, j, a.tw[1], a.kin[1], eta);
-    if (!act) return;
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-        const long long idx = base + slot_pos<N, T, R0>(q, j) * stride;
-#if PSTD_PREFETCH_PREV
-        const C p = pv[q];
-#else
-        const C p = a.prev[idx];
-#endif
-        a.prev[idx] = mk<C>(p.x + v[q].y, p.y - v[q].x);
-    }
-}
-
-// ---------------------------------------------------------------------------------
-// z pass: lines along z, lane = x; completes psi^{n+1} with the mask
-// ---------------------------------------------------------------------------------
-template <typename R, int N>
-__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) zpass_kernel(StepArgs<R> a)
-{
-    using C = typename StepArgs<R>::C;
-    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
-    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
-    const int x = blockIdx.x * kLanes + lane;
-    const int y = blockIdx.y, b = blockIdx.z;
-    const bool act = x < a.nx;
-    const long long stride = (long long)a.nx * a.ny;
-    const long long base = (long long)b * a.ncell + (long long)y * a.nx + x;
-    C v[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) v[q] = act ? a.cur[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
-#if PSTD_PREFETCH_PREV
-    C pv[E];
-#pragma unroll
-    for (int q = 0; q < E; ++q) pv[q] = act ? a.prev[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
-#endif
-    kinetic_line<N, false>(v, sm, lane, j, a.tw[2], a.kin[2], R(a.mem[b].eta));
-    if (!act) return;
-    const R gxy = a.mask[0][x] * a.mask[1][y];
-    bool ok = true;
-#pragma unroll
-    for (int q = 0; q < E; ++q) {
-        const int z = slot_pos<N, T, R0>(q, j);
-        const long long idx = base + z * stride;
-#if PSTD_PREFETCH_PREV
-        const C p = pv[q];
-#else
-        const C p = a.prev[idx];
-#endif
-        const R g = gxy * a.mask[2][z];
-        const C acc = mk<C>(g * (p.x + v[q].y), g * (p.y - v[q].x));
-        ok = ok && finite_c<R>(acc.x, acc.y);
-        a.prev[idx] = acc;
-    }
-    if (!ok) atomicOr(a.flag, 1);
-}
-
-// ---------------------------------------------------------------------------------
-// running DFT on the two virtual planes normal to one axis (Eqs. psiphasor, dpsiphasor).
-// d psi / d a at the plane node h is the spectral derivative sum_q D_h(q) psi(q) with
-// D_h(q) = (1/N) sum_m i k_m e^{2 pi i m (h - q)/N}, formed in the working precision; the
-// products with e^{i omega t_n} are accumulated in double precision.  Lines along y and z:
-// one thread per line, lanes over x (coalesced).  Lines along x: one warp per line, lanes
-// over x, reduced with shuffles.
+// running DFT fused into the passes (Eqs. psiphasor, dpsiphasor): on DFT-window steps each
+// pass also forms, from the raw psi^n of its lines, the spectral normal derivative
+// d psi / d a at the two virtual planes normal to its axis,
+//     D_h(q) = (1/N) sum_m i k_m e^{2 pi i m (h - q)/N},   (d psi/d a)(h) = sum_q D_h(q) psi(q),
+// and psi at the plane nodes; each thread contributes partial sums over the nodes it
+// holds, the T threads of a line are reduced through shared memory, and one thread per
+// line adds e^{i omega t_n} times the results to the double-precision accumulators.
 // ---------------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ void dft_accumulate(const DftArgs<R>& a, int b, long long pix, const double2* __restrict__ ef, int nfreq,
@@ -235,92 +80,225 @@ __device__ __forceinline__ void dft_accumulate(const DftArgs<R>& a, int b, long 
     }
 }
 
-template <typename R>
-__global__ void __launch_bounds__(256) plane_dft_kernel(DftArgs<R> a)
+// partial sums of this thread's raw line values: [0] d/da at h0, [1] d/da at h1, [2] psi(h0), [3] psi(h1)
+template <int N, int T, int R0, typename C, int E>
+__device__ __forceinline__ void dft_partials(const C (&v)[E], int j, const C* __restrict__ dw, int h0, int h1, C (&part)[4])
 {
-    using C = typename DftArgs<R>::C;
-    const int b = blockIdx.y;
-    if (!((a.member_mask >> b) & 1ull)) return;
-    const MemberDev& md = a.mem[b];
-    const int nfreq = md.nfreq;
-    // e^{+i omega_f t_n} for this member and window step, from the host-built table
-    const double2* ef = a.phase + (long long)b * a.phase_member_stride + (a.step - a.window_first[b]);
-    const long long cbase = (long long)b * a.ncell;
-    if (a.axis == 0) {
-        // one warp per x line; lines indexed (y, z); plane [z][y]
-        const int lane = threadIdx.x & 31;
-        const long long line = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-        if (line >= (long long)a.ny * a.nz) return;
-        const C* row = a.cur + cbase + line * a.nx;
-        C d0 = zero_c<R, C>(), d1 = zero_c<R, C>();
-        for (int q = lane; q < a.nx; q += 32) {
-            const C v = row[q], w0 = a.dw[q], w1 = a.dw[a.nx + q];
-            d0 = cadd(d0, cmul(v, w0));
-            d1 = cadd(d1, cmul(v, w1));
-        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            d0.x += __shfl_xor_sync(0xffffffffu, d0.x, o);
-            d0.y += __shfl_xor_sync(0xffffffffu, d0.y, o);
-            d1.x += __shfl_xor_sync(0xffffffffu, d1.x, o);
-            d1.y += __shfl_xor_sync(0xffffffffu, d1.y, o);
-        }
-        if (lane == 0) dft_accumulate<R>(a, b, line, ef, nfreq, row[a.h[0]], row[a.h[1]], d0, d1);
-        return;
+    for (int k = 0; k < 4; ++k) part[k] = mk<C>(decltype(C::x)(0), decltype(C::x)(0));
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const int pos = slot_pos<N, T, R0>(q, j);
+        part[0] = cadd(part[0], cmul(v[q], __ldg(&dw[pos])));
+        part[1] = cadd(part[1], cmul(v[q], __ldg(&dw[N + pos])));
+        if (pos == h0) part[2] = v[q];
+        if (pos == h1) part[3] = v[q];
     }
-    // lines along y or z: 32 lanes over x (coalesced) x 8 segments of the line per CTA,
-    // partial sums reduced through shared memory
-    constexpr int SEG = 8, MAXQ = 48;   // 8 segments of at most 48 nodes cover lines up to 384
-    __shared__ C red[SEG][2][32];
-    const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5;
-    const long long line = (long long)blockIdx.x * 32 + lane;
-    int n, u, w, nu;
-    long long stride, base;
-    const long long nlines = a.axis == 1 ? (long long)a.nx * a.nz : (long long)a.nx * a.ny;
-    const bool act = line < nlines;
-    const long long ln = act ? line : 0;
-    if (a.axis == 1) {            // lines along y; lines (x, z); plane [z][x]
-        n = a.ny; nu = a.nx;
-        u = (int)(ln % a.nx); w = (int)(ln / a.nx);
-        stride = a.nx;
-        base = (long long)w * a.nx * a.ny + u;
-    } else {                      // lines along z; lines (x, y); plane [y][x]
-        n = a.nz; nu = a.nx;
-        u = (int)(ln % a.nx); w = (int)(ln / a.nx);
-        stride = (long long)a.nx * a.ny;
-        base = (long long)w * a.nx + u;
-    }
-    const C* col = a.cur + cbase + base;
-    const int per = (n + SEG - 1) / SEG;
-    const int q0 = seg * per, q1 = min(n, q0 + per);
-    C d0 = zero_c<R, C>(), d1 = zero_c<R, C>();
-    if (act) {
-        C vals[16];
+}
+
+// reduce the partials of the T threads of each line (lane) through `red` (>= 4 T 32 complex)
+// and accumulate.  Every thread of the CTA must call this (it synchronises).
+template <typename R, int T, typename C>
+__device__ __forceinline__ void dft_finish(const C (&part)[4], C* red, int lane, int j, const DftArgs<R>& d, int b,
+                                           long long pix, bool act)
+{
 #pragma unroll
-        for (int c0 = 0; c0 < MAXQ; c0 += 16) {
-            if (q0 + c0 >= q1) break;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) vals[i] = q0 + c0 + i < q1 ? col[(long long)(q0 + c0 + i) * stride] : zero_c<R, C>();
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int q = q0 + c0 + i;
-                if (q < q1) {
-                    d0 = cadd(d0, cmul(vals[i], a.dw[q]));
-                    d1 = cadd(d1, cmul(vals[i], a.dw[n + q]));
-                }
-            }
-        }
-    }
-    red[seg][0][lane] = d0;
-    red[seg][1][lane] = d1;
+    for (int k = 0; k < 4; ++k) red[(k * T + j) * kLanes + lane] = part[k];
     __syncthreads();
-    if (seg != 0 || !act) return;
+    if (j == 0 && act) {
+        C tot[4];
 #pragma unroll
-    for (int s2 = 1; s2 < SEG; ++s2) {
-        d0 = cadd(d0, red[s2][0][lane]);
-        d1 = cadd(d1, red[s2][1][lane]);
+        for (int k = 0; k < 4; ++k) {
+            tot[k] = red[(k * T) * kLanes + lane];
+            for (int t = 1; t < T; ++t) tot[k] = cadd(tot[k], red[(k * T + t) * kLanes + lane]);
+        }
+        const double2* ef = d.phase + (long long)b * d.phase_member_stride + (d.step - d.window_first[b]);
+        dft_accumulate<R>(d, b, pix, ef, d.mem[b].nfreq, tot[2], tot[3], tot[0], tot[1]);
     }
-    dft_accumulate<R>(a, b, (long long)w * nu + u, ef, nfreq, col[a.h[0] * stride], col[a.h[1] * stride], d0, d1);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------
+// x pass: 32 consecutive rows per CTA, staged through shared memory (rows are
+// contiguous, so the tile is one contiguous block of 32 * nx values)
+// ---------------------------------------------------------------------------------
+template <typename R, int N, bool DFT>
+__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) xpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+{
+    using C = typename StepArgs<R>::C;
+    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const int b = blockIdx.y;
+    const int rows = a.ny * a.nz;
+    const int row0 = blockIdx.x * kLanes;
+    const int nrows = min(kLanes, rows - row0);
+    const long long tile0 = (long long)b * a.ncell + (long long)row0 * N;
+    for (int e = threadIdx.x; e < kLanes * N; e += blockDim.x) {
+        const int r = e / N, x = e - r * N;
+        sm[x * kPitch + r] = r < nrows ? a.cur[tile0 + e] : zero_c<R, C>();
+    }
+    __syncthreads();
+    C v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = sm[slot_pos<N, T, R0>(q, j) * kPitch + lane];
+    __syncthreads();
+    const bool dft = DFT && ((d.member_mask >> b) & 1ull);
+    C part[4];
+    if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
+    const R eta = R(a.mem[b].eta);
+    kinetic_line<N, false>(v, sm, lane, j, a.tw[0], a.kin[0], eta);
+    __syncthreads();
+    if (dft) dft_finish<R, T>(part, sm, lane, j, d, b, row0 + lane, lane < nrows);   // plane [z][y]: pixel = row
+#pragma unroll
+    for (int q = 0; q < E; ++q) sm[slot_pos<N, T, R0>(q, j) * kPitch + lane] = v[q];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
+        const int r = e / N, x = e - r * N;
+        const C w = sm[x * kPitch + r];
+        const C p = a.prev[tile0 + e];
+        a.prev[tile0 + e] = mk<C>(p.x + w.y, p.y - w.x);   // p - i w
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// y pass: lines along y, 32 consecutive x per CTA (lane = x), coalesced in place
+// ---------------------------------------------------------------------------------
+template <typename R, int N, bool DFT>
+__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) ypass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+{
+    using C = typename StepArgs<R>::C;
+    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const int x = blockIdx.x * kLanes + lane;
+    const int z = blockIdx.y, b = blockIdx.z;
+    const bool act = x < a.nx;
+    const long long stride = a.nx;
+    const long long base = (long long)b * a.ncell + (long long)z * a.nx * a.ny + x;
+    C v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = act ? a.cur[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
+#if PSTD_PREFETCH_PREV
+    C pv[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) pv[q] = act ? a.prev[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
+#endif
+    const bool dft = DFT && ((d.member_mask >> b) & 1ull);
+    C part[4];
+    if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
+    const R eta = R(a.mem[b].eta);
+    kinetic_line<N, false>(v, sm, lane, j, a.tw[1], a.kin[1], eta);
+    if (dft) {
+        __syncthreads();
+        dft_finish<R, T>(part, sm, lane, j, d, b, (long long)z * a.nx + x, act);   // plane [z][x]
+    }
+    if (!act) return;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const long long idx = base + slot_pos<N, T, R0>(q, j) * stride;
+#if PSTD_PREFETCH_PREV
+        const C p = pv[q];
+#else
+        const C p = a.prev[idx];
+#endif
+        a.prev[idx] = mk<C>(p.x + v[q].y, p.y - v[q].x);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// V-term and TF/SF source over their support box [lo, hi) (x fastest), one cell per thread:
+//   EXACT: prev -= (2 i dt / hbar) V (psi^n + psi_inc^n)
+//   PAPER: prev -= (2 i dt / hbar) [V psi~^n + hbar^2/2m psi_inc^n (lap zeta + 2 i k . grad zeta)]
+// ---------------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ StepArgs<R> a, int lox, int loy, int loz, int bx, int by, int bz)
+{
+    using C = typename StepArgs<R>::C;
+    // block: 32 x 4 cells of one (y, z) slab; grid: (x tiles, y tiles, z * batch)
+    const int x = lox + blockIdx.x * 32 + (threadIdx.x & 31);
+    const int y = loy + blockIdx.y * 4 + (threadIdx.x >> 5);
+    const int b = blockIdx.z / bz, z = loz + blockIdx.z % bz;
+    if (x >= lox + bx || y >= loy + by) return;
+    const long long idx = (long long)b * a.ncell + ((long long)z * a.ny + y) * a.nx + x;
+    const double2 tf = a.tfac[(a.step - a.tfac_base) * a.batch + b];   // a(t_n) e^{-i w0 t_n}
+    const C s = mk<C>(R(tf.x), R(tf.y));
+    const R c2 = R(2.0 * a.dt / a.hbar);
+    const bool paper = a.mode == PSTD_TFSF_PAPER;
+    C acc = mk<C>(R(0), R(0));    // V-term + source, multiplied by -(2 i dt / hbar) at the end
+    if (x >= a.vlo[0] && x < a.vhi[0] && y >= a.vlo[1] && y < a.vhi[1] && z >= a.vlo[2] && z < a.vhi[2]) {
+        const int vnx = a.vhi[0] - a.vlo[0], vny = a.vhi[1] - a.vlo[1];
+        const R Vv = a.V[((long long)(z - a.vlo[2]) * vny + (y - a.vlo[1])) * vnx + (x - a.vlo[0])];
+        C src = a.cur[idx];
+        if (!paper) src = cadd(src, incident_at<R, C>(a, b, s, x, y, z));
+        acc = cscale(src, Vv);
+    }
+    if (paper && x > a.tf_lo[0] && x < a.tf_hi[0] && y > a.tf_lo[1] && y < a.tf_hi[1] && z > a.tf_lo[2] && z < a.tf_hi[2]) {
+        const R zx = a.zeta[0][x], zx1 = a.zeta1[0][x], zx2 = a.zeta2[0][x];
+        const R zy = a.zeta[1][y], zy1 = a.zeta1[1][y], zy2 = a.zeta2[1][y];
+        const R zz = a.zeta[2][z], zz1 = a.zeta1[2][z], zz2 = a.zeta2[2][z];
+        const R lap = zx2 * zy * zz + zx * zy2 * zz + zx * zy * zz2;
+        const MemberDev& md = a.mem[b];
+        const R kg = R(md.k[0]) * zx1 * zy * zz + R(md.k[1]) * zx * zy1 * zz + R(md.k[2]) * zx * zy * zz1;
+        const R h2m = R(a.hbar * a.hbar / (2.0 * a.mass));
+        acc = cadd(acc, cscale(cmul(incident_at<R, C>(a, b, s, x, y, z), mk<C>(lap, R(2) * kg)), h2m));
+    }
+    const C p = a.prev[idx];
+    a.prev[idx] = mk<C>(p.x + c2 * acc.y, p.y - c2 * acc.x);
+}
+
+// ---------------------------------------------------------------------------------
+// z pass: lines along z, lane = x; completes psi^{n+1} with the mask
+// ---------------------------------------------------------------------------------
+template <typename R, int N, bool DFT>
+__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) zpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+{
+    using C = typename StepArgs<R>::C;
+    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const int x = blockIdx.x * kLanes + lane;
+    const int y = blockIdx.y, b = blockIdx.z;
+    const bool act = x < a.nx;
+    const long long stride = (long long)a.nx * a.ny;
+    const long long base = (long long)b * a.ncell + (long long)y * a.nx + x;
+    C v[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = act ? a.cur[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
+#if PSTD_PREFETCH_PREV
+    C pv[E];
+#pragma unroll
+    for (int q = 0; q < E; ++q) pv[q] = act ? a.prev[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
+#endif
+    const bool dft = DFT && ((d.member_mask >> b) & 1ull);
+    C part[4];
+    if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
+    kinetic_line<N, false>(v, sm, lane, j, a.tw[2], a.kin[2], R(a.mem[b].eta));
+    if (dft) {
+        __syncthreads();
+        dft_finish<R, T>(part, sm, lane, j, d, b, (long long)y * a.nx + x, act);   // plane [y][x]
+    }
+    if (!act) return;
+    const R gxy = a.mask[0][x] * a.mask[1][y];
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const int z = slot_pos<N, T, R0>(q, j);
+        const long long idx = base + z * stride;
+#if PSTD_PREFETCH_PREV
+        const C p = pv[q];
+#else
+        const C p = a.prev[idx];
+#endif
+        const R g = gxy * a.mask[2][z];
+        const C acc = mk<C>(g * (p.x + v[q].y), g * (p.y - v[q].x));
+        ok = ok && finite_c<R>(acc.x, acc.y);
+        a.prev[idx] = acc;
+    }
+    if (!ok) atomicOr(a.flag, 1);
 }
 
 // ---------------------------------------------------------------------------------
@@ -328,31 +306,48 @@ __global__ void __launch_bounds__(256) plane_dft_kernel(DftArgs<R> a)
 // ---------------------------------------------------------------------------------
 template <typename R, int N> size_t pass_smem() { return sizeof(typename StepArgs<R>::C) * (size_t)N * kPitch; }
 
-template <typename R, int N> cudaError_t xpass_n(const StepArgs<R>& a, int batch, cudaStream_t s)
+// Raise a kernel's dynamic shared-memory limit once per device instead of on every launch
+// (one flag word per kernel: the template is keyed on the kernel itself).
+template <auto kernel> cudaError_t set_smem_once(size_t bytes)
+{
+    static int done_mask = 0;   // bit d: set on device d (devices 0..30)
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 31 && (__atomic_load_n(&done_mask, __ATOMIC_ACQUIRE) >> dev) & 1) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess && dev < 31) __atomic_fetch_or(&done_mask, 1 << dev, __ATOMIC_RELEASE);
+    return e;
+}
+
+template <typename R, int N> cudaError_t xpass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
     const size_t sm = pass_smem<R, N>();
-    cudaError_t e = cudaFuncSetAttribute(xpass_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = d ? set_smem_once<xpass_kernel<R, N, true>>(sm) : set_smem_once<xpass_kernel<R, N, false>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.ny * a.nz + kLanes - 1) / kLanes, batch);
-    xpass_kernel<R, N><<<grid, kLanes * Plan<N>::T, sm, s>>>(a);
+    if (d) xpass_kernel<R, N, true><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, *d);
+    else xpass_kernel<R, N, false><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, DftArgs<R>{});
     return cudaGetLastError();
 }
-template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, int batch, cudaStream_t s)
+template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
     const size_t sm = pass_smem<R, N>();
-    cudaError_t e = cudaFuncSetAttribute(ypass_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = d ? set_smem_once<ypass_kernel<R, N, true>>(sm) : set_smem_once<ypass_kernel<R, N, false>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + kLanes - 1) / kLanes, a.nz, batch);
-    ypass_kernel<R, N><<<grid, kLanes * Plan<N>::T, sm, s>>>(a);
+    if (d) ypass_kernel<R, N, true><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, *d);
+    else ypass_kernel<R, N, false><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, DftArgs<R>{});
     return cudaGetLastError();
 }
-template <typename R, int N> cudaError_t zpass_n(const StepArgs<R>& a, int batch, cudaStream_t s)
+template <typename R, int N> cudaError_t zpass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
     const size_t sm = pass_smem<R, N>();
-    cudaError_t e = cudaFuncSetAttribute(zpass_kernel<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = d ? set_smem_once<zpass_kernel<R, N, true>>(sm) : set_smem_once<zpass_kernel<R, N, false>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + kLanes - 1) / kLanes, a.ny, batch);
-    zpass_kernel<R, N><<<grid, kLanes * Plan<N>::T, sm, s>>>(a);
+    if (d) zpass_kernel<R, N, true><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, *d);
+    else zpass_kernel<R, N, false><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, DftArgs<R>{});
     return cudaGetLastError();
 }
 
@@ -373,24 +368,30 @@ template <typename R, int N> cudaError_t zpass_n(const StepArgs<R>& a, int batch
     default: return cudaErrorInvalidValue;              \
     }
 
-template <typename R> cudaError_t launch_xpass(const StepArgs<R>& a, int batch, cudaStream_t s)
+template <typename R> cudaError_t launch_xpass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
-    PSTD_SIZE_DISPATCH(xpass_n, a.nx, a, batch, s)
+    PSTD_SIZE_DISPATCH(xpass_n, a.nx, a, d, batch, s)
 }
-template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, int batch, cudaStream_t s)
+template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
-    PSTD_SIZE_DISPATCH(ypass_n, a.ny, a, batch, s)
+    PSTD_SIZE_DISPATCH(ypass_n, a.ny, a, d, batch, s)
 }
-template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, int batch, cudaStream_t s)
+template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
-    PSTD_SIZE_DISPATCH(zpass_n, a.nz, a, batch, s)
+    PSTD_SIZE_DISPATCH(zpass_n, a.nz, a, d, batch, s)
 }
-template <typename R> cudaError_t launch_plane_dft(const DftArgs<R>& a, int batch, cudaStream_t s)
+template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch, cudaStream_t s)
 {
-    const long long lines = a.axis == 0 ? (long long)a.ny * a.nz : a.axis == 1 ? (long long)a.nx * a.nz : (long long)a.nx * a.ny;
-    const long long per_block = a.axis == 0 ? 8 : 32;   // x lines: one warp each; y, z lines: 32 per CTA
-    dim3 grid((unsigned)((lines + per_block - 1) / per_block), batch);
-    plane_dft_kernel<R><<<grid, 256, 0, s>>>(a);
+    // the V box, or for the PAPER form the interior of the TF/SF box (which contains it)
+    int lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        if (a.mode == PSTD_TFSF_PAPER) { lo[d] = a.tf_lo[d] + 1; hi[d] = a.tf_hi[d]; }
+        else { lo[d] = a.vlo[d]; hi[d] = a.vhi[d]; }
+    }
+    const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
+    if (bx <= 0 || by <= 0 || bz <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((bx + 31) / 32), (unsigned)((by + 3) / 4), (unsigned)(bz * batch));
+    source_kernel<R><<<grid, 128, 0, s>>>(a, lo[0], lo[1], lo[2], bx, by, bz);
     return cudaGetLastError();
 }
 
