@@ -101,13 +101,23 @@ def dist_env():
 
 
 def reduce_max(value: float, world: int):
+    """Maximum of a per-rank number over all ranks (NCCL on the GPUs, gloo on the host)."""
     if world <= 1:
         return value
     import torch
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(t_local: float, world: int, units_per_rank: float):
+    """Replicas: every rank processes the same units; the job takes as long as its slowest rank.
+
+    Returns (max-over-ranks seconds per step, whole-job units per second)."""
+    t = reduce_max(t_local, world)
+    return t, world * units_per_rank / t
 
 
 def barrier(world: int):
@@ -183,8 +193,7 @@ def run_gpu(args):
     one_pass(g)
     kstats = {name: g.kernel_stats(name) for name in pstd.KERNELS}
     g.set_timing(False)
-    t_step = reduce_max(sum(times) / len(times), world)
-    value = world * ncell * wl.nsteps / t_step
+    t_step, value = aggregate(sum(times) / len(times), world, ncell * wl.nsteps)
 
     # end to end through host buffers: V, points and angles in, psi and dsigma out
     h2d = wl.V.nbytes + wl.fresnel_points.nbytes + wl.far_theta.nbytes + wl.far_phi.nbytes
@@ -198,7 +207,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
     d2h = 0 if args.skip_e2e else psi_h.nbytes + ds_h.nbytes + fa_h.nbytes
-    t_e2e = reduce_max(sum(e2e_times) / len(e2e_times), world) if e2e_times else float("nan")
+    t_e2e, v_e2e = aggregate(sum(e2e_times) / len(e2e_times), world, ncell * wl.nsteps) if e2e_times else (0.0, None)
 
     # roofline of the dominant kernel: algorithmic bytes = read psi^n, read psi^{n-1},
     # write the updated level = 3 complex64 per cell per pass launch
@@ -227,7 +236,7 @@ def run_gpu(args):
         e1.record(stream)
         torch.cuda.synchronize()
         t64 = e0.elapsed_time(e1) / 1e3
-        step_ms = sum(g64.kernel_stats(n)[1] for n in ("xpass", "ypass", "zpass", "plane_dft"))
+        step_ms = sum(g64.kernel_stats(n)[1] for n in ("xpass", "ypass", "zpass", "source"))
         ds32, ds64c = ds.double().cpu().numpy(), ds64.double().cpu().numpy()
         p32, p64 = psi.cpu().numpy(), psi64.cpu().numpy()
         fp64 = {"value": ncell * wl.nsteps / t64, "unit": "cell-updates/s",
@@ -246,7 +255,7 @@ def run_gpu(args):
                    "dft_window_steps": wl.window_len, "fresnel_points": len(wl.fresnel_points),
                    "far_field_directions": len(wl.far_theta), "parallelism": f"replicas x{world}",
                    "l2": "flushed (256 MB write) between timed steps"},
-        "e2e": {"value": world * ncell * wl.nsteps / t_e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": int(h2d),
+        "e2e": {"value": v_e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": roofline,
         "gpu_launches": int(launches),

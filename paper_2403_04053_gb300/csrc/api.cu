@@ -91,17 +91,19 @@ struct pstd_grid {
     double* gl_w_dev = nullptr;
     FaceGeom faces[6];
     long long ncells = 0;
-    double2* MbT[6] = {};
-    double2* Mc[6] = {};
-    double2* T1 = nullptr;
-    double2* OutP = nullptr;
-    double2* OutD = nullptr;
+    // record / spectrum preparation operands, all in the working precision (float2 or double2)
+    void* MbT[6] = {};
+    void* Mc[6] = {};
+    void* T1 = nullptr;
+    void* OutP = nullptr;
+    void* OutD = nullptr;
+    void* Pw = nullptr;                     // one accumulator plane converted to the working precision (FP32 only)
     void* rec = nullptr;
     int rec_member = -1, rec_freq = -1;
     long long rec_version = -1;
-    double2* Fdft[6][2] = {};               // per face: DFT matrices along b (Nb x Nb) and c (Nc x Nc)
-    double2* specP = nullptr;               // per-face 2-D spectra in double (scratch for the preparation)
-    double2* specD = nullptr;
+    void* Fdft[6][2] = {};                  // per face: DFT matrices along b (Nb x Nb) and c (Nc x Nc)
+    void* specP = nullptr;                  // per-face 2-D spectra (scratch for the preparation)
+    void* specD = nullptr;
     void* ct = nullptr;                     // far-field spectra, working precision, faces back to back
     long long ct_off[6] = {};
     int ct_member = -1, ct_freq = -1;
@@ -583,10 +585,8 @@ pstd_status setup_transform(pstd_grid* g)
         std::vector<cd> mb, mc;
         interp(F.Nb, d.huygens_lo[F.b], F.L, true, mb);    // [Nb][L G]
         interp(F.Nc, d.huygens_lo[F.c], F.M, false, mc);   // [M G][Nc]
-        CK(g, dalloc(&g->MbT[f], mb.size() * 16));
-        CK(g, dalloc(&g->Mc[f], mc.size() * 16));
-        CK(g, cudaMemcpy(g->MbT[f], mb.data(), mb.size() * 16, cudaMemcpyHostToDevice));
-        CK(g, cudaMemcpy(g->Mc[f], mc.data(), mc.size() * 16, cudaMemcpyHostToDevice));
+        if (upload_complex(g, &g->MbT[f], mb) != PSTD_OK || upload_complex(g, &g->Mc[f], mc) != PSTD_OK)
+            return PSTD_ECUDA;
         t1max = std::max(t1max, (size_t)F.Nc * std::max(F.L * G, F.Nb));
         outmax = std::max(outmax, (size_t)F.M * G * F.L * G);
         // DFT matrices e^{-2 pi i u v / N} for the plane spectra of the far field
@@ -595,25 +595,38 @@ pstd_status setup_transform(pstd_grid* g)
             std::vector<cd> fm((size_t)N * N);
             for (int u = 0; u < N; ++u)
                 for (int v = 0; v < N; ++v) fm[(size_t)u * N + v] = std::exp(cd(0.0, -2.0 * kPi * (double)((long long)u * v % N) / N));
-            CK(g, dalloc(&g->Fdft[f][q], fm.size() * 16));
-            CK(g, cudaMemcpy(g->Fdft[f][q], fm.data(), fm.size() * 16, cudaMemcpyHostToDevice));
+            if (upload_complex(g, &g->Fdft[f][q], fm) != PSTD_OK) return PSTD_ECUDA;
         }
         g->ct_off[f] = f == 0 ? 0 : g->ct_off[f - 1] + 2LL * g->faces[f - 1].Nb * g->faces[f - 1].Nc;
         specmax = std::max(specmax, (size_t)F.Nb * F.Nc);
     }
     g->ncells = cell0;
-    CK(g, dalloc(&g->specP, specmax * 16));
-    CK(g, dalloc(&g->specD, specmax * 16));
+    CK(g, dalloc(&g->specP, specmax * g->csize));
+    CK(g, dalloc(&g->specD, specmax * g->csize));
+    if (g->prec != PSTD_F64) CK(g, dalloc(&g->Pw, specmax * g->csize));
     {
         const long long ctn = g->ct_off[5] + 2LL * g->faces[5].Nb * g->faces[5].Nc;
         if (dalloc(&g->ct, (size_t)ctn * g->csize) != cudaSuccess) return fail(g, PSTD_ENOMEM, "far-field spectra");
     }
-    CK(g, dalloc(&g->T1, t1max * 16));
-    CK(g, dalloc(&g->OutP, outmax * 16));
-    CK(g, dalloc(&g->OutD, outmax * 16));
+    CK(g, dalloc(&g->T1, t1max * g->csize));
+    CK(g, dalloc(&g->OutP, outmax * g->csize));
+    CK(g, dalloc(&g->OutD, outmax * g->csize));
     if (dalloc(&g->rec, (size_t)g->ncells * 2 * G * G * g->csize) != cudaSuccess)
         return fail(g, PSTD_ENOMEM, "transform records");
     return PSTD_OK;
+}
+
+// the accumulators stay FP64 (Eqs. psiphasor, dpsiphasor); the preparation GEMMs run in the working
+// precision, so an FP32 grid converts one [Nc][Nb] plane at a time
+template <typename C> const C* plane_in_working_precision(pstd_grid* g, const double2* plane, const FaceGeom& F)
+{
+    if (std::is_same<C, double2>::value) return reinterpret_cast<const C*>(plane);
+    const cudaError_t e = launch_convert<C>(plane, static_cast<C*>(g->Pw), (long long)F.Nb * F.Nc, g->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(g, e, "plane conversion");
+        return nullptr;
+    }
+    return static_cast<const C*>(g->Pw);
 }
 
 pstd_status check_window(pstd_grid* g, int b, int f)
@@ -637,20 +650,23 @@ template <typename R> pstd_status prepare_records(pstd_grid* g, int b, int f)
     const int G = g->G;
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
     const double2* base = g->acc + (long long)b * g->acc_freq_stride * g->acc_freq_cap + (long long)f * g->acc_freq_stride;
+    C* T1 = static_cast<C*>(g->T1);
     for (int fi = 0; fi < 6; ++fi) {
         const FaceGeom& F = g->faces[fi];
         const int LG = F.L * G, MG = F.M * G;
         for (int q = 0; q < 2; ++q) {
-            const double2* P = base + g->face_off[fi] + q * g->face_size[fi];   // [Nc][Nb]
-            double2* out = q == 0 ? g->OutP : g->OutD;
             Timer t(g, 4);
-            CK(g, launch_zgemm(F.Nc, LG, F.Nb, P, F.Nb, g->MbT[fi], LG, g->T1, LG, make_double2(scale.real(), scale.imag()),
-                               g->stream));
-            CK(g, launch_zgemm(MG, LG, F.Nc, g->Mc[fi], F.Nc, g->T1, LG, out, LG, make_double2(1.0, 0.0), g->stream));
+            const C* P = plane_in_working_precision<C>(g, base + g->face_off[fi] + q * g->face_size[fi], F);   // [Nc][Nb]
+            if (!P) return PSTD_ECUDA;
+            C* out = static_cast<C*>(q == 0 ? g->OutP : g->OutD);
+            CK(g, launch_cgemm<C>(F.Nc, LG, F.Nb, P, F.Nb, static_cast<const C*>(g->MbT[fi]), LG, T1, LG,
+                                  make_double2(scale.real(), scale.imag()), g->stream));
+            CK(g, launch_cgemm<C>(MG, LG, F.Nc, static_cast<const C*>(g->Mc[fi]), F.Nc, T1, LG, out, LG,
+                                  make_double2(1.0, 0.0), g->stream));
         }
         Timer t(g, 4);
-        CK(g, launch_pack_records<R>(g->OutP, g->OutD, F.L, F.M, G, g->gl_w_dev, 0.25 * F.db * F.dc, F.cell0,
-                                     static_cast<C*>(g->rec), g->stream));
+        CK(g, launch_pack_records<R>(static_cast<const C*>(g->OutP), static_cast<const C*>(g->OutD), F.L, F.M, G,
+                                     g->gl_w_dev, 0.25 * F.db * F.dc, F.cell0, static_cast<C*>(g->rec), g->stream));
     }
     g->rec_member = b;
     g->rec_freq = f;
@@ -668,19 +684,22 @@ template <typename R> pstd_status prepare_far(pstd_grid* g, int b, int f)
     const cd scale = 1.0 / g->mem[b].inc_phasor[f];   // Eqs. scaledphsiphasor, scaleddpsiphasor
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
     const double2* base = g->acc + (long long)b * g->acc_freq_stride * g->acc_freq_cap + (long long)f * g->acc_freq_stride;
+    C* T1 = static_cast<C*>(g->T1);
     for (int fi = 0; fi < 6; ++fi) {
         const FaceGeom& F = g->faces[fi];
         for (int q = 0; q < 2; ++q) {
-            const double2* P = base + g->face_off[fi] + q * g->face_size[fi];   // [Nc][Nb]
-            double2* spec = q == 0 ? g->specP : g->specD;
             Timer t(g, 4);
-            CK(g, launch_zgemm(F.Nc, F.Nb, F.Nb, P, F.Nb, g->Fdft[fi][0], F.Nb, g->T1, F.Nb,
-                               make_double2(scale.real(), scale.imag()), g->stream));
-            CK(g, launch_zgemm(F.Nc, F.Nb, F.Nc, g->Fdft[fi][1], F.Nc, g->T1, F.Nb, spec, F.Nb, make_double2(1.0, 0.0), g->stream));
+            const C* P = plane_in_working_precision<C>(g, base + g->face_off[fi] + q * g->face_size[fi], F);   // [Nc][Nb]
+            if (!P) return PSTD_ECUDA;
+            C* spec = static_cast<C*>(q == 0 ? g->specP : g->specD);
+            CK(g, launch_cgemm<C>(F.Nc, F.Nb, F.Nb, P, F.Nb, static_cast<const C*>(g->Fdft[fi][0]), F.Nb, T1, F.Nb,
+                                  make_double2(scale.real(), scale.imag()), g->stream));
+            CK(g, launch_cgemm<C>(F.Nc, F.Nb, F.Nc, static_cast<const C*>(g->Fdft[fi][1]), F.Nc, T1, F.Nb, spec, F.Nb,
+                                  make_double2(1.0, 0.0), g->stream));
         }
         Timer t(g, 4);
-        CK(g, launch_spectrum_pack<R>(g->specP, g->specD, F.Nb, F.Nc, 1.0 / ((double)F.Nb * F.Nc),
-                                      static_cast<C*>(g->ct) + g->ct_off[fi], g->stream));
+        CK(g, launch_spectrum_pack<R>(static_cast<const C*>(g->specP), static_cast<const C*>(g->specD), F.Nb, F.Nc,
+                                      1.0 / ((double)F.Nb * F.Nc), static_cast<C*>(g->ct) + g->ct_off[fi], g->stream));
     }
     g->ct_member = b;
     g->ct_freq = f;
@@ -887,7 +906,7 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     cudaStreamSynchronize(g->stream);
     for (void* p : {g->buf[0], g->buf[1], g->V, (void*)g->mem_dev, (void*)g->acc, (void*)g->flag, (void*)g->gl_w_dev,
                     (void*)g->dft_phase, (void*)g->window_first_dev, (void*)g->tfac,
-                    (void*)g->T1, (void*)g->OutP, (void*)g->OutD, g->rec, (void*)g->partial, (void*)g->pts_dev,
+                    g->T1, g->OutP, g->OutD, g->Pw, g->rec, (void*)g->partial, (void*)g->pts_dev,
                     (void*)g->out_dev, (void*)g->dsdo_dev})
         if (p) cudaFree(p);
     for (int a = 0; a < 3; ++a)

@@ -200,7 +200,10 @@ template <> struct Plan<192> { static constexpr int T = 16; static constexpr int
 template <> struct Plan<256> { static constexpr int T = 16; static constexpr int S = 2; static constexpr int R[3] = {16, 16, 0}; };
 template <> struct Plan<384> { static constexpr int T = 16; static constexpr int S = 3; static constexpr int R[3] = {12, 8, 4}; };
 
-constexpr int kLanes = 32;            // lines per CTA
+#ifndef PSTD_LANES
+#define PSTD_LANES 32
+#endif
+constexpr int kLanes = PSTD_LANES;    // lines per CTA (thread index = j * kLanes + line)
 constexpr int kPitch = kLanes + 1;    // shared-memory row pitch (complex elements)
 
 // One Stockham stage.  v holds the thread's E values; on entry they are the stage's

@@ -9,7 +9,7 @@ template cudaError_t launch_zpass<float>(const StepArgs<float>&, const DftArgs<f
 template cudaError_t launch_source<float>(const StepArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_transform<float>(const TransformArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_farfield<float>(const FarArgs<float>&, cudaStream_t);
-template cudaError_t launch_spectrum_pack<float>(const double2*, const double2*, int, int, double, float2*, cudaStream_t);
-template cudaError_t launch_pack_records<float>(const double2*, const double2*, int, int, int, const double*, double,
+template cudaError_t launch_spectrum_pack<float>(const float2*, const float2*, int, int, double, float2*, cudaStream_t);
+template cudaError_t launch_pack_records<float>(const float2*, const float2*, int, int, int, const double*, double,
                                                 long long, float2*, cudaStream_t);
 }  // namespace pstd

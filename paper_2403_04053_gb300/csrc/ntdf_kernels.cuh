@@ -389,30 +389,32 @@ template <typename R> cudaError_t launch_farfield(const FarArgs<R>& a, cudaStrea
 }
 
 template <typename R, typename C>
-__global__ void spectrum_pack_kernel(const double2* __restrict__ cp, const double2* __restrict__ cd, int Nb, int Nc,
-                                     double scale, C* __restrict__ ct)
+__global__ void spectrum_pack_kernel(const C* __restrict__ cp, const C* __restrict__ cd, int Nb, int Nc, R scale,
+                                     C* __restrict__ ct)
 {
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long n = (long long)Nb * Nc;
     if (e >= n) return;
     const int j = (int)(e % Nc), m = (int)(e / Nc);          // output [m][j]
-    const double2 vp = cp[(long long)j * Nb + m], vd = cd[(long long)j * Nb + m];
-    ct[e] = mk<C>(R(vp.x * scale), R(vp.y * scale));
-    ct[n + e] = mk<C>(R(vd.x * scale), R(vd.y * scale));
+    const C vp = cp[(long long)j * Nb + m], vd = cd[(long long)j * Nb + m];
+    ct[e] = mk<C>(vp.x * scale, vp.y * scale);
+    ct[n + e] = mk<C>(vd.x * scale, vd.y * scale);
 }
 
 template <typename R>
-cudaError_t launch_spectrum_pack(const double2* c_psi, const double2* c_dpsi, int Nb, int Nc, double scale,
+cudaError_t launch_spectrum_pack(const typename std::conditional<sizeof(R) == 4, float2, double2>::type* c_psi,
+                                 const typename std::conditional<sizeof(R) == 4, float2, double2>::type* c_dpsi,
+                                 int Nb, int Nc, double scale,
                                  typename std::conditional<sizeof(R) == 4, float2, double2>::type* ct, cudaStream_t s)
 {
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
     const long long n = (long long)Nb * Nc;
-    spectrum_pack_kernel<R, C><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c_psi, c_dpsi, Nb, Nc, scale, ct);
+    spectrum_pack_kernel<R, C><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c_psi, c_dpsi, Nb, Nc, R(scale), ct);
     return cudaGetLastError();
 }
 
 template <typename R, typename C>
-__global__ void pack_records_kernel(const double2* __restrict__ op, const double2* __restrict__ od, int L, int M, int G,
+__global__ void pack_records_kernel(const C* __restrict__ op, const C* __restrict__ od, int L, int M, int G,
                                     const double* __restrict__ glw, double cw, long long cell0, C* __restrict__ rec)
 {
     // one thread per (cell, h', g'); see the record layout above transform_kernel
@@ -426,30 +428,31 @@ __global__ void pack_records_kernel(const double2* __restrict__ op, const double
     const int l = (int)(cell % L), m = (int)(cell / L);
     const long long ld = (long long)L * G;
     const int gp = g, gm = G - 1 - g, hp = h, hm = G - 1 - h;
-    const double w = glw[g] * glw[h] * cw;   // mirrored nodes share their weights
+    const R w = R(glw[g] * glw[h] * cw);   // mirrored nodes share their weights
     const long long r0 = (long long)m * G;
     const long long c0 = (long long)l * G;
     C* out = rec + (cell0 + cell) * (2LL * G * G) + 8 * (h * H + g);
     for (int q = 0; q < 2; ++q) {
-        const double2* src = q == 0 ? op : od;
-        const double2 pp = src[(r0 + hp) * ld + c0 + gp], mp = src[(r0 + hp) * ld + c0 + gm];
-        const double2 pm = src[(r0 + hm) * ld + c0 + gp], mm = src[(r0 + hm) * ld + c0 + gm];
+        const C* src = q == 0 ? op : od;
+        const C pp = src[(r0 + hp) * ld + c0 + gp], mp = src[(r0 + hp) * ld + c0 + gm];
+        const C pm = src[(r0 + hm) * ld + c0 + gp], mm = src[(r0 + hm) * ld + c0 + gm];
         // first sign: node along b (g), second: node along c (h)
-        const double ssx = pp.x + mp.x + pm.x + mm.x, ssy = pp.y + mp.y + pm.y + mm.y;
-        const double aax = pp.x - mp.x - pm.x + mm.x, aay = pp.y - mp.y - pm.y + mm.y;
-        const double asx = pp.x - mp.x + pm.x - mm.x, asy = pp.y - mp.y + pm.y - mm.y;
-        const double sax = pp.x + mp.x - pm.x - mm.x, say = pp.y + mp.y - pm.y - mm.y;
+        const R ssx = pp.x + mp.x + pm.x + mm.x, ssy = pp.y + mp.y + pm.y + mm.y;
+        const R aax = pp.x - mp.x - pm.x + mm.x, aay = pp.y - mp.y - pm.y + mm.y;
+        const R asx = pp.x - mp.x + pm.x - mm.x, asy = pp.y - mp.y + pm.y - mm.y;
+        const R sax = pp.x + mp.x - pm.x - mm.x, say = pp.y + mp.y - pm.y - mm.y;
         C* o = out + 4 * q;
-        o[0] = mk<C>(R(ssx * w), R(ssy * w));
-        o[1] = mk<C>(R(aax * w), R(aay * w));
-        o[2] = mk<C>(R(asx * w), R(asy * w));
-        o[3] = mk<C>(R(sax * w), R(say * w));
+        o[0] = mk<C>(ssx * w, ssy * w);
+        o[1] = mk<C>(aax * w, aay * w);
+        o[2] = mk<C>(asx * w, asy * w);
+        o[3] = mk<C>(sax * w, say * w);
     }
 }
 
 template <typename R>
-cudaError_t launch_pack_records(const double2* out_psi, const double2* out_dpsi, int L, int M, int G, const double* glw,
-                                double cw, long long cell0,
+cudaError_t launch_pack_records(const typename std::conditional<sizeof(R) == 4, float2, double2>::type* out_psi,
+                                const typename std::conditional<sizeof(R) == 4, float2, double2>::type* out_dpsi,
+                                int L, int M, int G, const double* glw, double cw, long long cell0,
                                 typename std::conditional<sizeof(R) == 4, float2, double2>::type* rec, cudaStream_t s)
 {
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;

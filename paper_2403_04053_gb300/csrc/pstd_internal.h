@@ -112,8 +112,9 @@ template <typename R> struct FarArgs {
 
 template <typename R> cudaError_t launch_farfield(const FarArgs<R>& a, cudaStream_t s);
 // Ct[q][m][j] = scale * C[q][j][m] in the working precision (C from double2, [Nc][Nb] per quantity)
-template <typename R> cudaError_t launch_spectrum_pack(const double2* c_psi, const double2* c_dpsi, int Nb, int Nc,
-                                                       double scale,
+template <typename R> cudaError_t launch_spectrum_pack(const typename std::conditional<sizeof(R) == 4, float2, double2>::type* c_psi,
+                                                       const typename std::conditional<sizeof(R) == 4, float2, double2>::type* c_dpsi,
+                                                       int Nb, int Nc, double scale,
                                                        typename std::conditional<sizeof(R) == 4, float2, double2>::type* ct,
                                                        cudaStream_t s);
 
@@ -133,12 +134,14 @@ template <typename R> struct TransformArgs {
 template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, int G, int splits, cudaStream_t s);
 cudaError_t launch_reduce_partials(const double2* partial, int splits, long long M, double2* out,
                                    double* dsdo, cudaStream_t s);
-// complex double GEMM C[MxN] = alpha * A[MxK] B[KxN] (row-major, leading dims given)
-cudaError_t launch_zgemm(int M, int N, int K, const double2* A, int lda, const double2* B, int ldb, double2* C,
-                         int ldc, double2 alpha, cudaStream_t s);
-// gather node values into cell records: rec[(cell0 + m L + l) * 2GG + q GG + h G + g] = Out[(m G + h) * (L G) + l G + g] * w_g w_h * cw
-template <typename R> cudaError_t launch_pack_records(const double2* out_psi, const double2* out_dpsi, int L, int M,
-                                                     int G, const double* glw, double cw, long long cell0,
+// complex GEMM C[MxN] = alpha * A[MxK] B[KxN] (row-major, leading dims given), C = float2 or double2
+template <typename C> cudaError_t launch_cgemm(int M, int N, int K, const C* A, int lda, const C* B, int ldb, C* Cm,
+                                              int ldc, double2 alpha, cudaStream_t s);
+template <typename C> cudaError_t launch_convert(const double2* in, C* out, long long n, cudaStream_t s);
+// gather node values into cell records (mirrored-node combinations, see ntdf_kernels.cuh)
+template <typename R> cudaError_t launch_pack_records(const typename std::conditional<sizeof(R) == 4, float2, double2>::type* out_psi,
+                                                     const typename std::conditional<sizeof(R) == 4, float2, double2>::type* out_dpsi,
+                                                     int L, int M, int G, const double* glw, double cw, long long cell0,
                                                      typename std::conditional<sizeof(R) == 4, float2, double2>::type* rec,
                                                      cudaStream_t s);
 

@@ -36,7 +36,7 @@ template <typename R, typename C> __device__ __forceinline__ C zero_c() { return
 // threads (64 registers each) let the 512 CTAs of a 128^3 pass run in one wave on 152 SMs.
 template <typename R, int N> constexpr int pass_min_blocks()
 {
-    return (sizeof(R) == 4 && Plan<N>::T <= 8) ? (PSTD_PREFETCH_PREV ? 2 : 4) : 1;
+    return (sizeof(R) == 4 && Plan<N>::T <= 8) ? (PSTD_PREFETCH_PREV ? 2 : 4) * (32 / kLanes) : 1;
 }
 
 template <typename R> __device__ __forceinline__ bool finite_c(R a, R b) { return isfinite(a) && isfinite(b); }
@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
-    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
     const int b = blockIdx.y;
     const int rows = a.ny * a.nz;
     const int row0 = blockIdx.x * kLanes;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
-    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
     const int x = blockIdx.x * kLanes + lane;
     const int z = blockIdx.y, b = blockIdx.z;
     const bool act = x < a.nx;
@@ -213,20 +213,27 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 //   EXACT: prev -= (2 i dt / hbar) V (psi^n + psi_inc^n)
 //   PAPER: prev -= (2 i dt / hbar) [V psi~^n + hbar^2/2m psi_inc^n (lap zeta + 2 i k . grad zeta)]
 // ---------------------------------------------------------------------------------
+constexpr int kSourceZ = 4;   // z planes per thread of the source kernel
+
 template <typename R>
 __global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ StepArgs<R> a, int lox, int loy, int loz, int bx, int by, int bz)
 {
     using C = typename StepArgs<R>::C;
-    // block: 32 x 4 cells of one (y, z) slab; grid: (x tiles, y tiles, z * batch)
+    // block: 32 x 4 (x, y) columns, each thread kSourceZ consecutive z; grid: (x tiles, y tiles, z chunks * batch)
     const int x = lox + blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = loy + blockIdx.y * 4 + (threadIdx.x >> 5);
-    const int b = blockIdx.z / bz, z = loz + blockIdx.z % bz;
+    const int zchunks = (bz + kSourceZ - 1) / kSourceZ;
+    const int b = blockIdx.z / zchunks, z0 = loz + (blockIdx.z % zchunks) * kSourceZ;
     if (x >= lox + bx || y >= loy + by) return;
-    const long long idx = (long long)b * a.ncell + ((long long)z * a.ny + y) * a.nx + x;
     const double2 tf = a.tfac[(a.step - a.tfac_base) * a.batch + b];   // a(t_n) e^{-i w0 t_n}
     const C s = mk<C>(R(tf.x), R(tf.y));
     const R c2 = R(2.0 * a.dt / a.hbar);
     const bool paper = a.mode == PSTD_TFSF_PAPER;
+#pragma unroll
+    for (int zz = 0; zz < kSourceZ; ++zz) {
+    const int z = z0 + zz;
+    if (z >= loz + bz) break;
+    const long long idx = (long long)b * a.ncell + ((long long)z * a.ny + y) * a.nx + x;
     C acc = mk<C>(R(0), R(0));    // V-term + source, multiplied by -(2 i dt / hbar) at the end
     if (x >= a.vlo[0] && x < a.vhi[0] && y >= a.vlo[1] && y < a.vhi[1] && z >= a.vlo[2] && z < a.vhi[2]) {
         const int vnx = a.vhi[0] - a.vlo[0], vny = a.vhi[1] - a.vlo[1];
@@ -247,6 +254,7 @@ __global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ Ste
     }
     const C p = a.prev[idx];
     a.prev[idx] = mk<C>(p.x + c2 * acc.y, p.y - c2 * acc.x);
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -259,7 +267,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
-    const int lane = threadIdx.x & 31, j = threadIdx.x >> 5;
+    const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
     const int x = blockIdx.x * kLanes + lane;
     const int y = blockIdx.y, b = blockIdx.z;
     const bool act = x < a.nx;
@@ -390,7 +398,7 @@ template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch,
     }
     const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
     if (bx <= 0 || by <= 0 || bz <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((bx + 31) / 32), (unsigned)((by + 3) / 4), (unsigned)(bz * batch));
+    dim3 grid((unsigned)((bx + 31) / 32), (unsigned)((by + 3) / 4), (unsigned)(((bz + kSourceZ - 1) / kSourceZ) * batch));
     source_kernel<R><<<grid, 128, 0, s>>>(a, lo[0], lo[1], lo[2], bx, by, bz);
     return cudaGetLastError();
 }
