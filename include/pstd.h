@@ -190,9 +190,11 @@ pstd_status pstd_stability_dt_max(const pstd_grid_desc* desc, double vmax, doubl
 
 /* Per-kernel timing with CUDA events on the grid's stream (off by default).  Kernel ids:
  * 0 x-pass, 1 y-pass, 2 z-pass (on DFT-window steps these also accumulate the running DFT),
- * 3 unused, 4 transform/node preparation, 5 point transform, 6 far field, 7 V-term and TF/SF source.  pstd_kernel_stats returns the launches and summed milliseconds since the
- * last pstd_set_timing(g, 1) (synchronises).  pstd_launch_count counts every kernel the
- * grid launched since creation. */
+ * 3 fused x+y pass (FP32 square planes of 64, 96 or 128, on steps without the DFT),
+ * 4 transform/node preparation, 5 point transform, 6 far field, 7 V-term and TF/SF source.
+ * pstd_kernel_stats returns the launches and summed milliseconds since the last
+ * pstd_set_timing(g, 1) (synchronises).  pstd_launch_count counts every kernel the grid
+ * launched since creation. */
 pstd_status pstd_set_timing(pstd_grid* g, int enable);
 pstd_status pstd_kernel_stats(pstd_grid* g, int kernel_id, long* launches, double* total_ms);
 pstd_status pstd_launch_count(pstd_grid* g, long* count);

@@ -78,7 +78,7 @@ struct pstd_grid {
     long long face_off[6] = {}, face_size[6] = {};
     long long acc_freq_stride = 0;
     long long phasor_version = 0;
-    double2* tfac = nullptr;               // [step of the call][member] a(t_n) e^{-i w0 t_n}
+    void* tfac = nullptr;                  // [step of the call][member] a(t_n) e^{-i w0 t_n}, working precision
     size_t tfac_cap = 0;
     double2* dft_phase = nullptr;          // [member][freq][window step] e^{+i omega t_n}
     size_t dft_phase_cap = 0;
@@ -118,6 +118,7 @@ struct pstd_grid {
     size_t dsdo_cap = 0;
     // instrumentation
     bool timing = false;
+    bool use_xy = false;                    // fused x + y pass on steps without plane DFT
     std::vector<TimedLaunch> timed;
     std::vector<cudaEvent_t> event_pool;
     long long launches = 0;
@@ -426,6 +427,8 @@ template <typename R> StepArgs<R> step_args(pstd_grid* g)
     a.mem = g->mem_dev;
     a.step = g->n;
     a.dt = g->desc.dt; a.hbar = g->desc.hbar; a.mass = g->desc.mass;
+    a.c2 = R(2.0 * g->desc.dt / g->desc.hbar);
+    a.h2m = R(g->desc.hbar * g->desc.hbar / (2.0 * g->desc.mass));
     a.mode = g->desc.tfsf_mode;
     a.flag = g->flag;
     return a;
@@ -458,22 +461,29 @@ template <typename R> DftArgs<R> dft_args(pstd_grid* g, unsigned long long mask,
     return a;
 }
 
-// incident time factors a(t_n) e^{-i w0 t_n} for steps [n0, n0 + nsteps) of every member, in
-// double precision, uploaded in stream order (the previous call's kernels finish first)
+// incident time factors a(t_n) e^{-i w0 t_n} for steps [n0, n0 + nsteps) of every member,
+// evaluated in double precision and rounded once to the working precision; uploaded in
+// stream order (the previous call's kernels finish first)
 pstd_status upload_time_factors(pstd_grid* g, long long n0, long nsteps)
 {
-    std::vector<double2> tab((size_t)std::max(1L, nsteps) * g->batch);
+    std::vector<cd> tab((size_t)std::max(1L, nsteps) * g->batch);
     for (long s = 0; s < nsteps; ++s) {
         const double t = (n0 + s) * g->desc.dt;
         for (int b = 0; b < g->batch; ++b) {
             const MemberHost& m = g->mem[b];
             const double env = (m.ramp <= 0 || t >= m.ramp) ? 1.0 : (t <= 0 ? 0.0 : 0.5 * (1.0 - std::cos(kPi * t / m.ramp)));
-            tab[(size_t)s * g->batch + b] = make_double2(env * std::cos(m.w0 * t), -env * std::sin(m.w0 * t));
+            tab[(size_t)s * g->batch + b] = cd(env * std::cos(m.w0 * t), -env * std::sin(m.w0 * t));
         }
     }
-    pstd_status st = ensure(g, &g->tfac, g->tfac_cap, tab.size() * sizeof(double2));
+    pstd_status st = ensure(g, &g->tfac, g->tfac_cap, tab.size() * g->csize);
     if (st != PSTD_OK) return st;
-    CK(g, cudaMemcpyAsync(g->tfac, tab.data(), tab.size() * sizeof(double2), cudaMemcpyHostToDevice, g->stream));
+    if (g->prec == PSTD_F64) {
+        CK(g, cudaMemcpyAsync(g->tfac, tab.data(), tab.size() * 16, cudaMemcpyHostToDevice, g->stream));
+    } else {
+        std::vector<float2> f(tab.size());
+        for (size_t i = 0; i < tab.size(); ++i) f[i] = make_float2((float)tab[i].real(), (float)tab[i].imag());
+        CK(g, cudaMemcpyAsync(g->tfac, f.data(), f.size() * 8, cudaMemcpyHostToDevice, g->stream));
+    }
     return PSTD_OK;
 }
 
@@ -505,20 +515,26 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps)
             ++g->phasor_version;
         }
         StepArgs<R> a = step_args<R>(g);
-        a.tfac = g->tfac;
+        a.tfac = static_cast<const typename StepArgs<R>::C*>(g->tfac);
         a.tfac_base = n0;
         a.batch = g->batch;
         if (g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0]) {
             Timer t(g, 7);
             CK(g, launch_source<R>(a, g->batch, g->stream));
         }
-        {
-            Timer t(g, 0);
-            CK(g, launch_xpass<R>(a, mask ? &dx : nullptr, g->batch, g->stream));
-        }
-        {
-            Timer t(g, 1);
-            CK(g, launch_ypass<R>(a, mask ? &dy : nullptr, g->batch, g->stream));
+        if (!mask && g->use_xy) {
+            // no plane DFT this step: x and y together, one CTA per z plane
+            Timer t(g, 3);
+            CK(g, launch_xypass<R>(a, g->batch, g->stream));
+        } else {
+            {
+                Timer t(g, 0);
+                CK(g, launch_xpass<R>(a, mask ? &dx : nullptr, g->batch, g->stream));
+            }
+            {
+                Timer t(g, 1);
+                CK(g, launch_ypass<R>(a, mask ? &dy : nullptr, g->batch, g->stream));
+            }
         }
         {
             Timer t(g, 2);
@@ -835,6 +851,7 @@ pstd_status pstd_create_grid(const pstd_grid_desc* desc, pstd_grid** out)
     }
     g->stream = static_cast<cudaStream_t>(desc->stream);
     g->prec = desc->precision;
+    g->use_xy = g->prec == PSTD_F32 ? xypass_available<float>(desc->n[0], desc->n[1]) : false;
     g->rsize = g->prec == PSTD_F64 ? 8 : 4;
     g->csize = 2 * g->rsize;
     g->ncell = (long long)desc->n[0] * desc->n[1] * desc->n[2];
@@ -905,7 +922,7 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     DeviceGuard dg(g->dev);
     cudaStreamSynchronize(g->stream);
     for (void* p : {g->buf[0], g->buf[1], g->V, (void*)g->mem_dev, (void*)g->acc, (void*)g->flag, (void*)g->gl_w_dev,
-                    (void*)g->dft_phase, (void*)g->window_first_dev, (void*)g->tfac,
+                    (void*)g->dft_phase, (void*)g->window_first_dev, g->tfac,
                     g->T1, g->OutP, g->OutD, g->Pw, g->rec, (void*)g->partial, (void*)g->pts_dev,
                     (void*)g->out_dev, (void*)g->dsdo_dev})
         if (p) cudaFree(p);

@@ -208,8 +208,10 @@ constexpr int kPitch = kLanes + 1;    // shared-memory row pitch (complex elemen
 
 // One Stockham stage.  v holds the thread's E values; on entry they are the stage's
 // inputs when !FROM_SMEM, otherwise the inputs are read from the tile.  On exit the
-// outputs are in v, and also in the tile when TO_SMEM.
-template <int N, int T, int RAD, int NS, int DIR, bool FROM_SMEM, bool TO_SMEM, typename C, int E>
+// outputs are in v, and also in the tile when TO_SMEM.  Element (pos, lane) of the tile
+// sits at sm[pos * PS + lane * LS] (default: the [pos][lane] tile of kLanes lines).
+template <int N, int T, int RAD, int NS, int DIR, bool FROM_SMEM, bool TO_SMEM, int PS = kPitch, int LS = 1,
+          typename C, int E>
 __device__ __forceinline__ void stockham_stage(C (&v)[E], C* sm, int lane, int j, const C* __restrict__ tw)
 {
     constexpr int NB = E / RAD;
@@ -219,7 +221,7 @@ __device__ __forceinline__ void stockham_stage(C (&v)[E], C* sm, int lane, int j
         for (int t = 0; t < NB; ++t) {
             const int b = j + t * T;
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) v[t * RAD + r] = sm[(b + r * (N / RAD)) * kPitch + lane];
+            for (int r = 0; r < RAD; ++r) v[t * RAD + r] = sm[(b + r * (N / RAD)) * PS + lane * LS];
         }
         if constexpr (TO_SMEM) __syncthreads();
     }
@@ -244,7 +246,7 @@ __device__ __forceinline__ void stockham_stage(C (&v)[E], C* sm, int lane, int j
             const int b = j + t * T;
             const int base = (b / NS) * NS * RAD + (b % NS);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) sm[(base + r * NS) * kPitch + lane] = v[t * RAD + r];
+            for (int r = 0; r < RAD; ++r) sm[(base + r * NS) * PS + lane * LS] = v[t * RAD + r];
         }
         __syncthreads();
     }

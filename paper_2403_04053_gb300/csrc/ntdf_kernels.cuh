@@ -118,6 +118,7 @@ __global__ void __launch_bounds__(kTransformThreads) transform_kernel(const __gr
     constexpr int PT = kTransformPT;
     extern __shared__ __align__(16) unsigned char smraw[];
     C* srec = reinterpret_cast<C*>(smraw);
+    C* scen = srec + CH * REC;   // per-cell centre offsets of the chunk
     const double k = a.k;
 
     long long pidx[PT];
@@ -176,12 +177,17 @@ __global__ void __launch_bounds__(kTransformThreads) transform_kernel(const __gr
             const int nch = (int)min((long long)CH, f_end - cc0);
             __syncthreads();
             for (int e = threadIdx.x; e < nch * REC; e += kTransformThreads) srec[e] = a.rec[cc0 * REC + e];
+            if (threadIdx.x < nch) {
+                // cell centre minus face centre, once per cell of the chunk (double precision
+                // and the index division stay out of the per-point loop)
+                const long long local = cc0 + threadIdx.x - F.cell0;
+                const int m = (int)(local / F.L), l = (int)(local - (long long)m * F.L);
+                scen[threadIdx.x] = mk<C>(R((l - 0.5 * (F.L - 1)) * F.db), R((m - 0.5 * (F.M - 1)) * F.dc));
+            }
             __syncthreads();
             for (int ci = 0; ci < nch; ++ci) {
-                const long long local = cc0 + ci - F.cell0;
-                const int m = (int)(local / F.L), l = (int)(local - (long long)m * F.L);
-                const R dcb = R((l - 0.5 * (F.L - 1)) * F.db);   // cell centre minus face centre
-                const R dcc = R((m - 0.5 * (F.M - 1)) * F.dc);
+                const C cen = scen[ci];
+                const R dcb = cen.x, dcc = cen.y;
                 const C* P = srec + ci * REC;
 #pragma unroll
                 for (int i = 0; i < PT; ++i) {
@@ -234,7 +240,7 @@ template <typename R, int G> cudaError_t transform_g(const TransformArgs<R>& a, 
 {
     using C = typename TransformArgs<R>::C;
     constexpr int CH = sizeof(R) == 4 ? 32 : 16;
-    const size_t sm = sizeof(C) * CH * 2 * G * G;
+    const size_t sm = sizeof(C) * CH * (2 * G * G + 1);
     dim3 grid((unsigned)((a.M + kTransformThreads * kTransformPT - 1) / (kTransformThreads * kTransformPT)), splits);
     transform_kernel<R, G><<<grid, kTransformThreads, sm, s>>>(a);
     return cudaGetLastError();

@@ -42,9 +42,11 @@ template <typename R> struct StepArgs {
     const MemberDev* mem;
     long long step;          // n: index of the current state
     double dt, hbar, mass;
+    R c2;                    // 2 dt / hbar, rounded once on the host
+    R h2m;                   // hbar^2 / 2m
     int mode;                // PSTD_TFSF_EXACT / PSTD_TFSF_PAPER
     int* flag;               // bit 0: non-finite value written
-    const double2* tfac;     // a(t_n) e^{-i w0 t_n}: [(n - tfac_base) * batch + member], host-built in FP64
+    const C* tfac;           // a(t_n) e^{-i w0 t_n}: [(n - tfac_base) * batch + member], evaluated in FP64 on the host
     long long tfac_base;
     int batch;
 };
@@ -79,6 +81,9 @@ template <typename R> cudaError_t launch_xpass(const StepArgs<R>& a, const DftAr
 template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch, cudaStream_t s);
+// fused x + y pass (one CTA per z plane); available for FP32 square planes of 64, 96, 128
+template <typename R> bool xypass_available(int nx, int ny);
+template <typename R> cudaError_t launch_xypass(const StepArgs<R>& a, int batch, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------
 // surface-equivalence transform

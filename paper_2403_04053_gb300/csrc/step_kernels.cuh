@@ -41,6 +41,43 @@ template <typename R, int N> constexpr int pass_min_blocks()
 
 template <typename R> __device__ __forceinline__ bool finite_c(R a, R b) { return isfinite(a) && isfinite(b); }
 
+// Programmatic dependent launch between the kernels of the step: each step kernel is
+// launched so that it may be scheduled while the previous one drains, and waits for the
+// previous grid's completion (and memory) at griddepcontrol.wait before it touches the
+// state; launch_dependents right after lets the next kernel be scheduled as soon as all of
+// this grid's CTAs are resident.  Without the launch attribute both are no-ops.
+#ifndef PSTD_PDL
+#define PSTD_PDL 1
+#endif
+__device__ __forceinline__ void step_kernel_entry()
+{
+#if PSTD_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+template <typename Kern, typename... Args>
+cudaError_t launch_step_kernel(Kern kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t s, const Args&... args)
+{
+#if PSTD_PDL
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+#else
+    kernel<<<grid, block, smem, s>>>(args...);
+    return cudaGetLastError();
+#endif
+}
+
 // psi_inc^n at node (x, y, z) of member b: s e^{i k_x (x - O_x)} e^{i k_y (y - O_y)} e^{i k_z (z - O_z)}
 template <typename R, typename C>
 __device__ __forceinline__ C incident_at(const StepArgs<R>& a, int b, C s, int x, int y, int z)
@@ -125,6 +162,7 @@ __device__ __forceinline__ void dft_finish(const C (&part)[4], C* red, int lane,
 template <typename R, int N, bool DFT>
 __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) xpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
 {
+    step_kernel_entry();
     using C = typename StepArgs<R>::C;
     constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -168,6 +206,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 template <typename R, int N, bool DFT>
 __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) ypass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
 {
+    step_kernel_entry();
     using C = typename StepArgs<R>::C;
     constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -209,6 +248,82 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 }
 
 // ---------------------------------------------------------------------------------
+// xy pass: one CTA per z plane (square N x N planes in FP32), applying K_x + K_y as one
+// 2-D spectral operator, F_y^-1 F_x^-1 [(k_x^2 + k_y^2) F_x F_y psi], with the plane held
+// in shared memory ([y][x], pitch N + 1: conflict-free for rows and for columns):
+//   1. columns (lane = x, read from global, coalesced): forward FFT along y, spectrum
+//      written to the plane;
+//   2. rows (lane = y spectral index): forward FFT along x, multiply by
+//      eta (kin_x[m_x] + kin_y[m_y]) / N (each kin table carries its own axis' 1/N),
+//      inverse FFT along x, written back;
+//   3. columns: inverse FFT along y, then prev -= i * result straight to global.
+// One read of psi^n and one read-modify-write of the partial per cell, instead of two
+// of each for separate x and y passes.
+// ---------------------------------------------------------------------------------
+template <int N> constexpr int xy_threads() { return (N / 32) * Plan<N>::T * 32; }
+template <typename R, int N> constexpr bool xy_supported()
+{
+    return sizeof(R) == 4 && Plan<N>::S == 2 && N % 32 == 0 && xy_threads<N>() <= 1024 &&
+           (size_t)N * (N + 1) * 8 <= 227 * 1024;
+}
+
+template <typename R, int N>
+__global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid_constant__ StepArgs<R> a)
+{
+    step_kernel_entry();
+    using C = typename StepArgs<R>::C;
+    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0], R1 = Plan<N>::R[1], P = N + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int lane = threadIdx.x & 31, j = (threadIdx.x >> 5) % T, grp = threadIdx.x / (32 * T);
+    const int z = blockIdx.x, b = blockIdx.y;
+    const int x = grp * 32 + lane;             // column of this thread in steps 1 and 3
+    const int my = grp * 32 + lane;            // row (spectral y index) in step 2
+    C* smc = sm + grp * 32;                    // columns: (pos, lane) at pos * P + lane
+    C* smr = sm + grp * 32 * P;                // rows:    (pos, lane) at lane * P + pos
+    const long long pbase = (long long)b * a.ncell + (long long)z * N * N;
+    const C* __restrict__ cur = a.cur + pbase + x;
+    C* __restrict__ prev = a.prev + pbase + x;
+    const C* __restrict__ twx = a.tw[0];
+    const C* __restrict__ twy = a.tw[1];
+    C v[E];
+    // 1. forward along y
+#pragma unroll
+    for (int q = 0; q < E; ++q) v[q] = cur[slot_pos<N, T, R0>(q, j) * N];
+    stockham_stage<N, T, R0, 1, -1, false, true, P, 1>(v, smc, lane, j, twy);
+    stockham_stage<N, T, R1, R0, -1, true, false, P, 1>(v, smc, lane, j, twy);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < E; ++q) smc[spec_pos<N, T, R1>(q, j) * P + lane] = v[q];
+    __syncthreads();
+    // 2. along x: forward, spectral multiply, inverse
+    stockham_stage<N, T, R0, 1, -1, true, true, 1, P>(v, smr, lane, j, twx);
+    stockham_stage<N, T, R1, R0, -1, true, false, 1, P>(v, smr, lane, j, twx);
+    {
+        const R eta = R(a.mem[b].eta) * (R(1) / R(N));
+        const R ky = __ldg(&a.kin[1][my]);
+#pragma unroll
+        for (int q = 0; q < E; ++q) v[q] = cscale(v[q], (__ldg(&a.kin[0][spec_pos<N, T, R1>(q, j)]) + ky) * eta);
+    }
+    __syncthreads();
+    stockham_stage<N, T, R1, 1, +1, false, true, 1, P>(v, smr, lane, j, twx);
+    stockham_stage<N, T, R0, R1, +1, true, false, 1, P>(v, smr, lane, j, twx);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < E; ++q) smr[lane * P + slot_pos<N, T, R0>(q, j)] = v[q];
+    __syncthreads();
+    // 3. inverse along y, then the update
+    stockham_stage<N, T, R1, 1, +1, true, true, P, 1>(v, smc, lane, j, twy);
+    stockham_stage<N, T, R0, R1, +1, true, false, P, 1>(v, smc, lane, j, twy);
+#pragma unroll
+    for (int q = 0; q < E; ++q) {
+        const int off = slot_pos<N, T, R0>(q, j) * N;
+        const C p = prev[off];
+        prev[off] = mk<C>(p.x + v[q].y, p.y - v[q].x);
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // V-term and TF/SF source over their support box [lo, hi) (x fastest), one cell per thread:
 //   EXACT: prev -= (2 i dt / hbar) V (psi^n + psi_inc^n)
 //   PAPER: prev -= (2 i dt / hbar) [V psi~^n + hbar^2/2m psi_inc^n (lap zeta + 2 i k . grad zeta)]
@@ -218,6 +333,7 @@ constexpr int kSourceZ = 4;   // z planes per thread of the source kernel
 template <typename R>
 __global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ StepArgs<R> a, int lox, int loy, int loz, int bx, int by, int bz)
 {
+    step_kernel_entry();
     using C = typename StepArgs<R>::C;
     // block: 32 x 4 (x, y) columns, each thread kSourceZ consecutive z; grid: (x tiles, y tiles, z chunks * batch)
     const int x = lox + blockIdx.x * 32 + (threadIdx.x & 31);
@@ -225,9 +341,8 @@ __global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ Ste
     const int zchunks = (bz + kSourceZ - 1) / kSourceZ;
     const int b = blockIdx.z / zchunks, z0 = loz + (blockIdx.z % zchunks) * kSourceZ;
     if (x >= lox + bx || y >= loy + by) return;
-    const double2 tf = a.tfac[(a.step - a.tfac_base) * a.batch + b];   // a(t_n) e^{-i w0 t_n}
-    const C s = mk<C>(R(tf.x), R(tf.y));
-    const R c2 = R(2.0 * a.dt / a.hbar);
+    const C s = a.tfac[(a.step - a.tfac_base) * a.batch + b];   // a(t_n) e^{-i w0 t_n}
+    const R c2 = a.c2;
     const bool paper = a.mode == PSTD_TFSF_PAPER;
 #pragma unroll
     for (int zz = 0; zz < kSourceZ; ++zz) {
@@ -249,8 +364,7 @@ __global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ Ste
         const R lap = zx2 * zy * zz + zx * zy2 * zz + zx * zy * zz2;
         const MemberDev& md = a.mem[b];
         const R kg = R(md.k[0]) * zx1 * zy * zz + R(md.k[1]) * zx * zy1 * zz + R(md.k[2]) * zx * zy * zz1;
-        const R h2m = R(a.hbar * a.hbar / (2.0 * a.mass));
-        acc = cadd(acc, cscale(cmul(incident_at<R, C>(a, b, s, x, y, z), mk<C>(lap, R(2) * kg)), h2m));
+        acc = cadd(acc, cscale(cmul(incident_at<R, C>(a, b, s, x, y, z), mk<C>(lap, R(2) * kg)), a.h2m));
     }
     const C p = a.prev[idx];
     a.prev[idx] = mk<C>(p.x + c2 * acc.y, p.y - c2 * acc.x);
@@ -263,6 +377,7 @@ __global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ Ste
 template <typename R, int N, bool DFT>
 __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) zpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
 {
+    step_kernel_entry();
     using C = typename StepArgs<R>::C;
     constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -334,9 +449,9 @@ template <typename R, int N> cudaError_t xpass_n(const StepArgs<R>& a, const Dft
     cudaError_t e = d ? set_smem_once<xpass_kernel<R, N, true>>(sm) : set_smem_once<xpass_kernel<R, N, false>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.ny * a.nz + kLanes - 1) / kLanes, batch);
-    if (d) xpass_kernel<R, N, true><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, *d);
-    else xpass_kernel<R, N, false><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, DftArgs<R>{});
-    return cudaGetLastError();
+    const DftArgs<R> none{};
+    if (d) return launch_step_kernel(xpass_kernel<R, N, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
+    return launch_step_kernel(xpass_kernel<R, N, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
 }
 template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
@@ -344,9 +459,9 @@ template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const Dft
     cudaError_t e = d ? set_smem_once<ypass_kernel<R, N, true>>(sm) : set_smem_once<ypass_kernel<R, N, false>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + kLanes - 1) / kLanes, a.nz, batch);
-    if (d) ypass_kernel<R, N, true><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, *d);
-    else ypass_kernel<R, N, false><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, DftArgs<R>{});
-    return cudaGetLastError();
+    const DftArgs<R> none{};
+    if (d) return launch_step_kernel(ypass_kernel<R, N, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
+    return launch_step_kernel(ypass_kernel<R, N, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
 }
 template <typename R, int N> cudaError_t zpass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
@@ -354,9 +469,22 @@ template <typename R, int N> cudaError_t zpass_n(const StepArgs<R>& a, const Dft
     cudaError_t e = d ? set_smem_once<zpass_kernel<R, N, true>>(sm) : set_smem_once<zpass_kernel<R, N, false>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + kLanes - 1) / kLanes, a.ny, batch);
-    if (d) zpass_kernel<R, N, true><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, *d);
-    else zpass_kernel<R, N, false><<<grid, kLanes * Plan<N>::T, sm, s>>>(a, DftArgs<R>{});
-    return cudaGetLastError();
+    const DftArgs<R> none{};
+    if (d) return launch_step_kernel(zpass_kernel<R, N, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
+    return launch_step_kernel(zpass_kernel<R, N, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
+}
+
+template <typename R, int N> cudaError_t xypass_n(const StepArgs<R>& a, int batch, cudaStream_t s)
+{
+    if constexpr (xy_supported<R, N>()) {
+        const size_t sm = sizeof(typename StepArgs<R>::C) * (size_t)N * (N + 1);
+        cudaError_t e = set_smem_once<xypass_kernel<R, N>>(sm);
+        if (e != cudaSuccess) return e;
+        const dim3 grid(a.nz, batch);
+        return launch_step_kernel(xypass_kernel<R, N>, grid, dim3(xy_threads<N>()), sm, s, a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
 }
 
 #define PSTD_SIZE_DISPATCH(FN, n, ...)                 \
@@ -388,6 +516,21 @@ template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, const DftAr
 {
     PSTD_SIZE_DISPATCH(zpass_n, a.nz, a, d, batch, s)
 }
+// fused xy pass: FP32, square planes of 64, 96 or 128 (one CTA per plane)
+template <typename R> bool xypass_available(int nx, int ny)
+{
+    return sizeof(R) == 4 && nx == ny && (nx == 64 || nx == 96 || nx == 128);
+}
+template <typename R> cudaError_t launch_xypass(const StepArgs<R>& a, int batch, cudaStream_t s)
+{
+    if (!xypass_available<R>(a.nx, a.ny)) return cudaErrorInvalidValue;
+    switch (a.nx) {
+    case 64: return xypass_n<R, 64>(a, batch, s);
+    case 96: return xypass_n<R, 96>(a, batch, s);
+    case 128: return xypass_n<R, 128>(a, batch, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
 template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch, cudaStream_t s)
 {
     // the V box, or for the PAPER form the interior of the TF/SF box (which contains it)
@@ -399,8 +542,7 @@ template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch,
     const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
     if (bx <= 0 || by <= 0 || bz <= 0) return cudaSuccess;
     dim3 grid((unsigned)((bx + 31) / 32), (unsigned)((by + 3) / 4), (unsigned)(((bz + kSourceZ - 1) / kSourceZ) * batch));
-    source_kernel<R><<<grid, 128, 0, s>>>(a, lo[0], lo[1], lo[2], bx, by, bz);
-    return cudaGetLastError();
+    return launch_step_kernel(source_kernel<R>, grid, dim3(128), 0, s, a, lo[0], lo[1], lo[2], bx, by, bz);
 }
 
 }  // namespace pstd

@@ -25,7 +25,7 @@ FIELD_CURRENT, FIELD_PREVIOUS, FIELD_SCATTERED = 0, 1, 2
 MAX_FREQ = 4
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ESTATE", 6: "ENONFINITE", 7: "ETIMEOUT"}
-KERNELS = {"xpass": 0, "ypass": 1, "zpass": 2, "prepare": 4, "transform": 5, "far_field": 6, "source": 7}
+KERNELS = {"xpass": 0, "ypass": 1, "zpass": 2, "xypass": 3, "prepare": 4, "transform": 5, "far_field": 6, "source": 7}
 
 
 class PstdError(RuntimeError):

@@ -53,6 +53,13 @@ ONE_STEP_SPECS = {
     "mixed-96x16x64": lambda mode: inputs.GridSpec(n=(96, 16, 64), d=(0.2, 0.35, 0.25), dt=0.002, abc_cells=(8, 2, 6),
                                                    tfsf_lo=(30, 5, 20), tfsf_hi=(66, 11, 44), taper_cells=3,
                                                    huygens_lo=(20, 3, 12), huygens_hi=(76, 13, 52), tfsf_mode=mode),
+    # square planes: the fused x+y pass (one CTA per z plane) on steps without the DFT
+    "square-64x64x48": lambda mode: inputs.GridSpec(n=(64, 64, 48), d=(0.25, 0.25, 0.3), dt=0.002, abc_cells=(6, 6, 5),
+                                                    tfsf_lo=(20, 20, 16), tfsf_hi=(44, 44, 32), taper_cells=3,
+                                                    huygens_lo=(14, 14, 10), huygens_hi=(50, 50, 38), tfsf_mode=mode),
+    "square-96x96x24": lambda mode: inputs.GridSpec(n=(96, 96, 24), d=(0.2, 0.2, 0.3), dt=0.001, abc_cells=(8, 8, 3),
+                                                    tfsf_lo=(36, 36, 9), tfsf_hi=(60, 60, 15), taper_cells=2,
+                                                    huygens_lo=(28, 28, 6), huygens_hi=(68, 68, 18), tfsf_mode=mode),
     "radix3-12x192x8": lambda mode: inputs.GridSpec(n=(12, 192, 8), d=(0.3, 0.1, 0.4), dt=0.001, abc_cells=(2, 16, 1),
                                                     tfsf_lo=(4, 60, 3), tfsf_hi=(8, 132, 5), taper_cells=1,
                                                     huygens_lo=(3, 40, 2), huygens_hi=(9, 150, 6), tfsf_mode=mode),
@@ -336,6 +343,29 @@ def test_call_order_errors():
         with pytest.raises(pstd.PstdError) as e:
             g.cross_section(0, 3, [0.1], [0.1])
         assert e.value.code == "EINVAL"
+
+
+def test_fused_xy_pass_outside_the_dft_window():
+    # 64^2 planes in FP32: the fused x+y pass runs on the steps outside the DFT window and
+    # the separate x and y passes (which also accumulate the DFT) inside it
+    spec = ONE_STEP_SPECS["square-64x64x48"]("exact")
+    V = random_core_V(spec, 4)
+    khat, win = (0.3, -0.5, 0.81), (10, 10)
+    sim = po.Simulation(spec, V, khat, K, 0.05, window=win, omegas=[E0])
+    sim.step(30)
+    with pstd.Grid(spec, precision=pstd.F32) as g:
+        g.set_potential(V)
+        g.set_incidence(0, khat, K, 0.05)
+        g.huygens_dft(0, [E0], *win)
+        g.set_timing(True)
+        g.step(30)
+        assert g.kernel_stats("xypass")[0] == 20
+        assert g.kernel_stats("xpass")[0] == 10 and g.kernel_stats("ypass")[0] == 10
+        assert g.kernel_stats("zpass")[0] == 30
+        assert rel(g.get_field(0), sim.cur) < 2e-5
+        ph, ref = g.get_phasors(0, 0), sim.scaled_phasors(0)
+        for a, b in zip(ph, ref):
+            assert rel(a[0], b[0]) < 2e-5 and rel(a[1], b[1]) < 2e-5
 
 
 def test_timing_and_launch_counts():
