@@ -209,11 +209,11 @@ def run_gpu(args):
     d2h = 0 if args.skip_e2e else psi_h.nbytes + ds_h.nbytes + fa_h.nbytes
     t_e2e, v_e2e = aggregate(sum(e2e_times) / len(e2e_times), world, ncell * wl.nsteps) if e2e_times else (0.0, None)
 
-    # roofline of the dominant kernel: algorithmic bytes = read psi^n, read psi^{n-1},
-    # write the updated level = 3 complex64 per cell per pass launch
+    # roofline of the dominant kernel: every pass launch (x, y, z or the fused x+y) reads
+    # psi^n and the partial level and writes it back: 3 complex64 = 24 B per cell
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
-    top = max(("xpass", "ypass", "zpass"), key=lambda n: kstats[n][1])
+    top = max(("xpass", "ypass", "zpass", "xypass"), key=lambda n: kstats[n][1])
     nl, ms = kstats[top]
     achieved = 24.0 * ncell / (ms / nl / 1e3) / 1e9
     roofline = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",

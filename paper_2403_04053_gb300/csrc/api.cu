@@ -518,7 +518,11 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps)
         a.tfac = static_cast<const typename StepArgs<R>::C*>(g->tfac);
         a.tfac_base = n0;
         a.batch = g->batch;
-        if (g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0]) {
+        // the V-term and source: folded into the z pass on steps without the DFT, their own
+        // kernel on DFT steps
+        const bool need_src = g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0];
+        const bool src_in_z = need_src && !mask;
+        if (need_src && !src_in_z) {
             Timer t(g, 7);
             CK(g, launch_source<R>(a, g->batch, g->stream));
         }
@@ -538,7 +542,7 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps)
         }
         {
             Timer t(g, 2);
-            CK(g, launch_zpass<R>(a, mask ? &dz : nullptr, g->batch, g->stream));
+            CK(g, launch_zpass<R>(a, mask ? &dz : nullptr, src_in_z, g->batch, g->stream));
         }
         g->cur ^= 1;
         ++g->n;

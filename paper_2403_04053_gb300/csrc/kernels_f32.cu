@@ -5,7 +5,7 @@
 namespace pstd {
 template cudaError_t launch_xpass<float>(const StepArgs<float>&, const DftArgs<float>*, int, cudaStream_t);
 template cudaError_t launch_ypass<float>(const StepArgs<float>&, const DftArgs<float>*, int, cudaStream_t);
-template cudaError_t launch_zpass<float>(const StepArgs<float>&, const DftArgs<float>*, int, cudaStream_t);
+template cudaError_t launch_zpass<float>(const StepArgs<float>&, const DftArgs<float>*, bool, int, cudaStream_t);
 template cudaError_t launch_source<float>(const StepArgs<float>&, int, cudaStream_t);
 template bool xypass_available<float>(int, int);
 template cudaError_t launch_xypass<float>(const StepArgs<float>&, int, cudaStream_t);

@@ -5,7 +5,7 @@
 namespace pstd {
 template cudaError_t launch_xpass<double>(const StepArgs<double>&, const DftArgs<double>*, int, cudaStream_t);
 template cudaError_t launch_ypass<double>(const StepArgs<double>&, const DftArgs<double>*, int, cudaStream_t);
-template cudaError_t launch_zpass<double>(const StepArgs<double>&, const DftArgs<double>*, int, cudaStream_t);
+template cudaError_t launch_zpass<double>(const StepArgs<double>&, const DftArgs<double>*, bool, int, cudaStream_t);
 template cudaError_t launch_source<double>(const StepArgs<double>&, int, cudaStream_t);
 template bool xypass_available<double>(int, int);
 template cudaError_t launch_xypass<double>(const StepArgs<double>&, int, cudaStream_t);

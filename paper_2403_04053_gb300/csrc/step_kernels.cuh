@@ -330,26 +330,13 @@ __global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid
 // ---------------------------------------------------------------------------------
 constexpr int kSourceZ = 4;   // z planes per thread of the source kernel
 
-template <typename R>
-__global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ StepArgs<R> a, int lox, int loy, int loz, int bx, int by, int bz)
+// V-term + source at node (x, y, z) of member b (before the factor -(2 i dt / hbar));
+// s = a(t_n) e^{-i w0 t_n}, idx the node's state index
+template <typename R, typename C>
+__device__ __forceinline__ C source_acc(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
 {
-    step_kernel_entry();
-    using C = typename StepArgs<R>::C;
-    // block: 32 x 4 (x, y) columns, each thread kSourceZ consecutive z; grid: (x tiles, y tiles, z chunks * batch)
-    const int x = lox + blockIdx.x * 32 + (threadIdx.x & 31);
-    const int y = loy + blockIdx.y * 4 + (threadIdx.x >> 5);
-    const int zchunks = (bz + kSourceZ - 1) / kSourceZ;
-    const int b = blockIdx.z / zchunks, z0 = loz + (blockIdx.z % zchunks) * kSourceZ;
-    if (x >= lox + bx || y >= loy + by) return;
-    const C s = a.tfac[(a.step - a.tfac_base) * a.batch + b];   // a(t_n) e^{-i w0 t_n}
-    const R c2 = a.c2;
     const bool paper = a.mode == PSTD_TFSF_PAPER;
-#pragma unroll
-    for (int zz = 0; zz < kSourceZ; ++zz) {
-    const int z = z0 + zz;
-    if (z >= loz + bz) break;
-    const long long idx = (long long)b * a.ncell + ((long long)z * a.ny + y) * a.nx + x;
-    C acc = mk<C>(R(0), R(0));    // V-term + source, multiplied by -(2 i dt / hbar) at the end
+    C acc = mk<C>(R(0), R(0));
     if (x >= a.vlo[0] && x < a.vhi[0] && y >= a.vlo[1] && y < a.vhi[1] && z >= a.vlo[2] && z < a.vhi[2]) {
         const int vnx = a.vhi[0] - a.vlo[0], vny = a.vhi[1] - a.vlo[1];
         const R Vv = a.V[((long long)(z - a.vlo[2]) * vny + (y - a.vlo[1])) * vnx + (x - a.vlo[0])];
@@ -366,15 +353,47 @@ __global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ Ste
         const R kg = R(md.k[0]) * zx1 * zy * zz + R(md.k[1]) * zx * zy1 * zz + R(md.k[2]) * zx * zy * zz1;
         acc = cadd(acc, cscale(cmul(incident_at<R, C>(a, b, s, x, y, z), mk<C>(lap, R(2) * kg)), a.h2m));
     }
-    const C p = a.prev[idx];
-    a.prev[idx] = mk<C>(p.x + c2 * acc.y, p.y - c2 * acc.x);
+    return acc;
+}
+
+// the box [lo, hi) on which the V-term or the source can be non-zero: the V box, or for the
+// PAPER form the interior of the TF/SF box (which contains it)
+template <typename R> __host__ __device__ inline void source_box(const StepArgs<R>& a, int lo[3], int hi[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        if (a.mode == PSTD_TFSF_PAPER) { lo[d] = a.tf_lo[d] + 1; hi[d] = a.tf_hi[d]; }
+        else { lo[d] = a.vlo[d]; hi[d] = a.vhi[d]; }
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ StepArgs<R> a, int lox, int loy, int loz, int bx, int by, int bz)
+{
+    step_kernel_entry();
+    using C = typename StepArgs<R>::C;
+    // block: 32 x 4 (x, y) columns, each thread kSourceZ consecutive z; grid: (x tiles, y tiles, z chunks * batch)
+    const int x = lox + blockIdx.x * 32 + (threadIdx.x & 31);
+    const int y = loy + blockIdx.y * 4 + (threadIdx.x >> 5);
+    const int zchunks = (bz + kSourceZ - 1) / kSourceZ;
+    const int b = blockIdx.z / zchunks, z0 = loz + (blockIdx.z % zchunks) * kSourceZ;
+    if (x >= lox + bx || y >= loy + by) return;
+    const C s = a.tfac[(a.step - a.tfac_base) * a.batch + b];   // a(t_n) e^{-i w0 t_n}
+    const R c2 = a.c2;
+#pragma unroll
+    for (int zz = 0; zz < kSourceZ; ++zz) {
+        const int z = z0 + zz;
+        if (z >= loz + bz) break;
+        const long long idx = (long long)b * a.ncell + ((long long)z * a.ny + y) * a.nx + x;
+        const C acc = source_acc<R, C>(a, b, s, x, y, z, idx);
+        const C p = a.prev[idx];
+        a.prev[idx] = mk<C>(p.x + c2 * acc.y, p.y - c2 * acc.x);
     }
 }
 
 // ---------------------------------------------------------------------------------
 // z pass: lines along z, lane = x; completes psi^{n+1} with the mask
 // ---------------------------------------------------------------------------------
-template <typename R, int N, bool DFT>
+template <typename R, int N, bool DFT, bool SRC>
 __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) zpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
 {
     step_kernel_entry();
@@ -407,15 +426,26 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     if (!act) return;
     const R gxy = a.mask[0][x] * a.mask[1][y];
     bool ok = true;
+    // with SRC the V-term and source of this column are added here instead of by source_kernel
+    int slo[3] = {0, 0, 0}, shi[3] = {0, 0, 0};
+    if constexpr (SRC) source_box<R>(a, slo, shi);
+    const bool src_col = SRC && x >= slo[0] && x < shi[0] && y >= slo[1] && y < shi[1];
+    const C s = src_col ? a.tfac[(a.step - a.tfac_base) * a.batch + b] : zero_c<R, C>();
 #pragma unroll
     for (int q = 0; q < E; ++q) {
         const int z = slot_pos<N, T, R0>(q, j);
         const long long idx = base + z * stride;
 #if PSTD_PREFETCH_PREV
-        const C p = pv[q];
+        C p = pv[q];
 #else
-        const C p = a.prev[idx];
+        C p = a.prev[idx];
 #endif
+        if constexpr (SRC) {
+            if (src_col && z >= slo[2] && z < shi[2]) {
+                const C sa = source_acc<R, C>(a, b, s, x, y, z, idx);
+                p = mk<C>(p.x + a.c2 * sa.y, p.y - a.c2 * sa.x);
+            }
+        }
         const R g = gxy * a.mask[2][z];
         const C acc = mk<C>(g * (p.x + v[q].y), g * (p.y - v[q].x));
         ok = ok && finite_c<R>(acc.x, acc.y);
@@ -463,15 +493,18 @@ template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const Dft
     if (d) return launch_step_kernel(ypass_kernel<R, N, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
     return launch_step_kernel(ypass_kernel<R, N, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
 }
-template <typename R, int N> cudaError_t zpass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
+template <typename R, int N>
+cudaError_t zpass_n(const StepArgs<R>& a, const DftArgs<R>* d, bool src, int batch, cudaStream_t s)
 {
     const size_t sm = pass_smem<R, N>();
-    cudaError_t e = d ? set_smem_once<zpass_kernel<R, N, true>>(sm) : set_smem_once<zpass_kernel<R, N, false>>(sm);
+    cudaError_t e = d ? set_smem_once<zpass_kernel<R, N, true, false>>(sm)
+                      : src ? set_smem_once<zpass_kernel<R, N, false, true>>(sm) : set_smem_once<zpass_kernel<R, N, false, false>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + kLanes - 1) / kLanes, a.ny, batch);
     const DftArgs<R> none{};
-    if (d) return launch_step_kernel(zpass_kernel<R, N, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
-    return launch_step_kernel(zpass_kernel<R, N, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
+    if (d) return launch_step_kernel(zpass_kernel<R, N, true, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
+    if (src) return launch_step_kernel(zpass_kernel<R, N, false, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
+    return launch_step_kernel(zpass_kernel<R, N, false, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
 }
 
 template <typename R, int N> cudaError_t xypass_n(const StepArgs<R>& a, int batch, cudaStream_t s)
@@ -512,9 +545,11 @@ template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, const DftAr
 {
     PSTD_SIZE_DISPATCH(ypass_n, a.ny, a, d, batch, s)
 }
-template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
+template <typename R>
+cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, bool src, int batch, cudaStream_t s)
 {
-    PSTD_SIZE_DISPATCH(zpass_n, a.nz, a, d, batch, s)
+    if (d && src) return cudaErrorInvalidValue;   // DFT steps run the source kernel instead
+    PSTD_SIZE_DISPATCH(zpass_n, a.nz, a, d, src, batch, s)
 }
 // fused xy pass: FP32, square planes of 64, 96 or 128 (one CTA per plane)
 template <typename R> bool xypass_available(int nx, int ny)
@@ -533,12 +568,8 @@ template <typename R> cudaError_t launch_xypass(const StepArgs<R>& a, int batch,
 }
 template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch, cudaStream_t s)
 {
-    // the V box, or for the PAPER form the interior of the TF/SF box (which contains it)
     int lo[3], hi[3];
-    for (int d = 0; d < 3; ++d) {
-        if (a.mode == PSTD_TFSF_PAPER) { lo[d] = a.tf_lo[d] + 1; hi[d] = a.tf_hi[d]; }
-        else { lo[d] = a.vlo[d]; hi[d] = a.vhi[d]; }
-    }
+    source_box<R>(a, lo, hi);
     const int bx = hi[0] - lo[0], by = hi[1] - lo[1], bz = hi[2] - lo[2];
     if (bx <= 0 || by <= 0 || bz <= 0) return cudaSuccess;
     dim3 grid((unsigned)((bx + 31) / 32), (unsigned)((by + 3) / 4), (unsigned)(((bz + kSourceZ - 1) / kSourceZ) * batch));
