@@ -14,4 +14,8 @@ Modules
                 sum of Eqs. bottomPsi_lm ... Psi, and its far-field limit
   analytic    : textbook closed forms that pin the oracle (partial waves, Born,
                 spherical wave, leapfrog mode evolution)
+  adjoint_oracle : the discrete adjoint (transpose) of the leapfrog run, of the running
+                DFT and of the surface transform, and the gradient of a Fresnel-field
+                magnitude misfit with respect to V (no counterpart in the paper; pinned by
+                central finite differences of the oracle's own forward loss)
 """
