@@ -199,6 +199,38 @@ pstd_status pstd_set_timing(pstd_grid* g, int enable);
 pstd_status pstd_kernel_stats(pstd_grid* g, int kernel_id, long* launches, double* total_ms);
 pstd_status pstd_launch_count(pstd_grid* g, long* count);
 
+/* ---- Discrete adjoint (gradients for inverse scattering) ----------------------------
+ * The paper has no adjoint; these are the exact transposes of the discrete forward path
+ * above, for the gradient of a real loss L with respect to the potential.  Gradient
+ * convention for complex z: g = dL/dRe z + i dL/dIm z (the convention of PyTorch's
+ * complex autograd), complex128 interleaved. */
+
+/* Gradient of L with respect to member b's scaled phasors at frequency index f (the data
+ * pstd_get_phasors returns, same layout), given dl_dpsi[i] = gradient of L with respect to
+ * the field pstd_transform_to_points computes at xyz[3*i..3*i+2] (M complex128).  The
+ * transpose of that transform (Gauss-Legendre quadrature of the trigonometric interpolant,
+ * the same discretisation).  Needs only the member's incidence (its k), not a completed
+ * window.  `mem` applies to xyz, dl_dpsi and out. */
+pstd_status pstd_transform_adjoint(pstd_grid* g, int b, int f, const double* xyz, long M, const void* dl_dpsi, void* out,
+                                   int mem);
+
+/* dL/dV on the box [box_lo, box_hi) of grid nodes (x fastest, doubles) for a loss that is
+ * a function of the scaled phasors of a run of nsteps leapfrog steps from rest, given
+ * dl_dphasors = the gradient of L with respect to them (one block per frequency of the
+ * member's DFT window, each in the layout of pstd_get_phasors).  Batch-1 grids only
+ * (EINVAL otherwise); needs the incidence and the DFT window (ESTATE), and the window must
+ * end within nsteps (EINVAL).  The discrete adjoint of Eq. PSTDupdating with Eq. expmask:
+ * the forward run is repeated with checkpoints of (psi^{n-1}, psi^n) every
+ * checkpoint_interval steps (0: ceil(sqrt(nsteps))), each segment is recomputed, and the
+ * adjoint levels are stepped backward with the forward kernels (the adjoint of the update
+ * is its complex conjugate with no incident wave), accumulating
+ * dL/dV = (2 dt/hbar) sum_n Im[nu^{n+1} (psi^n + psi_inc^n)] (no psi_inc in the PAPER form).
+ * Device memory: 2 ceil(nsteps/K) + K + 2 + nfreq states.  Leaves the grid at rest (state
+ * zero, step 0) with its DFT sums untouched.  `mem` applies to dl_dphasors and dl_dv;
+ * synchronises. */
+pstd_status pstd_adjoint_gradient(pstd_grid* g, long nsteps, const void* dl_dphasors, const int box_lo[3],
+                                  const int box_hi[3], long checkpoint_interval, double* dl_dv, int mem);
+
 /* Message of the last failure on g (or of the last failed pstd_create_grid when g is NULL). */
 const char* pstd_last_error(const pstd_grid* g);
 

@@ -98,6 +98,30 @@ struct pstd_grid {
     void* OutP = nullptr;
     void* OutD = nullptr;
     void* Pw = nullptr;                     // one accumulator plane converted to the working precision (FP32 only)
+    void* MbTH[6] = {};                     // conj(MbT)^T [L G][Nb] and conj(Mc)^T [Nc][M G]: the adjoint transform
+    void* McH[6] = {};
+    // adjoint buffers (allocated on first use)
+    void* adj_table = nullptr;              // [6][M] AdjPoint
+    size_t adj_table_cap = 0;
+    void* adj_partial = nullptr;            // [split][ncells][2 G G]
+    size_t adj_partial_cap = 0;
+    void* adj_rec = nullptr;                // record gradients [ncells][2 G G]
+    void* adj_PA = nullptr;                 // one plane gradient, working precision
+    double2* adj_gpts = nullptr;            // dL/dPsi per point (device copy)
+    size_t adj_gpts_cap = 0;
+    double2* adj_out = nullptr;             // phasor-layout gradient (device copy)
+    size_t adj_out_cap = 0;
+    void* adj_J = nullptr;                  // injection volumes, one per frequency
+    size_t adj_J_cap = 0;
+    void* adj_ckpt = nullptr;               // checkpoints (psi^{n-1}, psi^n)
+    size_t adj_ckpt_cap = 0;
+    void* adj_seg = nullptr;                // forward states of one segment
+    size_t adj_seg_cap = 0;
+    void* adj_nu = nullptr;                 // two adjoint levels
+    size_t adj_nu_cap = 0;
+    void* adj_zero = nullptr;               // one zero complex: the adjoint run's incident time factor
+    double* adj_grad = nullptr;             // gradient accumulators on the box
+    size_t adj_grad_cap = 0;
     void* rec = nullptr;
     int rec_member = -1, rec_freq = -1;
     long long rec_version = -1;
@@ -487,14 +511,52 @@ pstd_status upload_time_factors(pstd_grid* g, long long n0, long nsteps)
     return PSTD_OK;
 }
 
-template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps)
+// Enqueue the kernels of one leapfrog step on the state pair in `a` (all batch members);
+// `mask` selects the members whose running DFT accumulates this step (d* their arguments).
+template <typename R>
+pstd_status enqueue_step(pstd_grid* g, const StepArgs<R>& a, unsigned long long mask, const DftArgs<R>* dx,
+                         const DftArgs<R>* dy, const DftArgs<R>* dz, bool need_src)
+{
+    // the V-term and source: folded into the z pass on steps without the DFT, their own
+    // kernel on DFT steps
+    const bool src_in_z = need_src && !mask;
+    if (need_src && !src_in_z) {
+        Timer t(g, 7);
+        CK(g, launch_source<R>(a, g->batch, g->stream));
+    }
+    if (!mask && g->use_xy) {
+        // no plane DFT this step: x and y together, one CTA per z plane
+        Timer t(g, 3);
+        CK(g, launch_xypass<R>(a, g->batch, g->stream));
+    } else {
+        {
+            Timer t(g, 0);
+            CK(g, launch_xpass<R>(a, mask ? dx : nullptr, g->batch, g->stream));
+        }
+        {
+            Timer t(g, 1);
+            CK(g, launch_ypass<R>(a, mask ? dy : nullptr, g->batch, g->stream));
+        }
+    }
+    {
+        Timer t(g, 2);
+        CK(g, launch_zpass<R>(a, mask ? dz : nullptr, src_in_z, g->batch, g->stream));
+    }
+    return PSTD_OK;
+}
+
+// nsteps leapfrog steps from the grid's current state.  dft = false leaves the running DFT
+// (device sums and host incident phasors) untouched; a non-null `save` receives, in stream
+// order, the state after each step: save + (s + 1) * ncell for step s (batch 1).
+template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft = true, void* save = nullptr)
 {
     const long long n0 = g->n;
     pstd_status st0 = upload_time_factors(g, n0, nsteps);
     if (st0 != PSTD_OK) return st0;
+    const bool need_src = g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0];
     for (long s = 0; s < nsteps; ++s) {
         unsigned long long mask = 0;
-        for (int b = 0; b < g->batch; ++b) {
+        for (int b = 0; b < g->batch && dft; ++b) {
             const MemberHost& m = g->mem[b];
             if (m.nfreq > 0 && g->n >= m.first && g->n < m.first + m.len) mask |= 1ull << b;
         }
@@ -518,34 +580,13 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps)
         a.tfac = static_cast<const typename StepArgs<R>::C*>(g->tfac);
         a.tfac_base = n0;
         a.batch = g->batch;
-        // the V-term and source: folded into the z pass on steps without the DFT, their own
-        // kernel on DFT steps
-        const bool need_src = g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0];
-        const bool src_in_z = need_src && !mask;
-        if (need_src && !src_in_z) {
-            Timer t(g, 7);
-            CK(g, launch_source<R>(a, g->batch, g->stream));
-        }
-        if (!mask && g->use_xy) {
-            // no plane DFT this step: x and y together, one CTA per z plane
-            Timer t(g, 3);
-            CK(g, launch_xypass<R>(a, g->batch, g->stream));
-        } else {
-            {
-                Timer t(g, 0);
-                CK(g, launch_xpass<R>(a, mask ? &dx : nullptr, g->batch, g->stream));
-            }
-            {
-                Timer t(g, 1);
-                CK(g, launch_ypass<R>(a, mask ? &dy : nullptr, g->batch, g->stream));
-            }
-        }
-        {
-            Timer t(g, 2);
-            CK(g, launch_zpass<R>(a, mask ? &dz : nullptr, src_in_z, g->batch, g->stream));
-        }
+        pstd_status st = enqueue_step<R>(g, a, mask, &dx, &dy, &dz, need_src);
+        if (st != PSTD_OK) return st;
         g->cur ^= 1;
         ++g->n;
+        if (save)
+            CK(g, cudaMemcpyAsync(static_cast<char*>(save) + (size_t)(s + 1) * g->ncell * g->csize, g->buf[g->cur],
+                                  (size_t)g->ncell * g->csize, cudaMemcpyDeviceToDevice, g->stream));
     }
     return PSTD_OK;
 }
@@ -607,7 +648,19 @@ pstd_status setup_transform(pstd_grid* g)
         interp(F.Nc, d.huygens_lo[F.c], F.M, false, mc);   // [M G][Nc]
         if (upload_complex(g, &g->MbT[f], mb) != PSTD_OK || upload_complex(g, &g->Mc[f], mc) != PSTD_OK)
             return PSTD_ECUDA;
+        {
+            // conjugate transposes for the adjoint transform
+            const int LG = F.L * G, MG = F.M * G;
+            std::vector<cd> mbh((size_t)LG * F.Nb), mch((size_t)F.Nc * MG);
+            for (int i = 0; i < F.Nb; ++i)
+                for (int r = 0; r < LG; ++r) mbh[(size_t)r * F.Nb + i] = std::conj(mb[(size_t)i * LG + r]);
+            for (int r = 0; r < MG; ++r)
+                for (int j = 0; j < F.Nc; ++j) mch[(size_t)j * MG + r] = std::conj(mc[(size_t)r * F.Nc + j]);
+            if (upload_complex(g, &g->MbTH[f], mbh) != PSTD_OK || upload_complex(g, &g->McH[f], mch) != PSTD_OK)
+                return PSTD_ECUDA;
+        }
         t1max = std::max(t1max, (size_t)F.Nc * std::max(F.L * G, F.Nb));
+        t1max = std::max(t1max, (size_t)F.M * G * F.Nb);   // adjoint: [M G][Nb]
         outmax = std::max(outmax, (size_t)F.M * G * F.L * G);
         // DFT matrices e^{-2 pi i u v / N} for the plane spectra of the far field
         for (int q = 0; q < 2; ++q) {
@@ -624,6 +677,7 @@ pstd_status setup_transform(pstd_grid* g)
     CK(g, dalloc(&g->specP, specmax * g->csize));
     CK(g, dalloc(&g->specD, specmax * g->csize));
     if (g->prec != PSTD_F64) CK(g, dalloc(&g->Pw, specmax * g->csize));
+    CK(g, dalloc(&g->adj_PA, specmax * g->csize));
     {
         const long long ctn = g->ct_off[5] + 2LL * g->faces[5].Nb * g->faces[5].Nc;
         if (dalloc(&g->ct, (size_t)ctn * g->csize) != cudaSuccess) return fail(g, PSTD_ENOMEM, "far-field spectra");
@@ -802,6 +856,227 @@ pstd_status run_transform(pstd_grid* g, int b, int f, const double* pts, long M,
     return PSTD_OK;
 }
 
+// -------------------------------------------------------------------------------------
+// discrete adjoint (the transposes of the forward path; no counterpart in the paper)
+// -------------------------------------------------------------------------------------
+template <typename C, typename R> C make_c(R x, R y)
+{
+    C v;
+    v.x = x;
+    v.y = y;
+    return v;
+}
+
+double envelope_at(const MemberHost& m, double t)
+{
+    return (m.ramp <= 0 || t >= m.ramp) ? 1.0 : (t <= 0 ? 0.0 : 0.5 * (1.0 - std::cos(kPi * t / m.ramp)));
+}
+
+// gradient with respect to member b's scaled phasors (phasor layout, one frequency) of a
+// real loss of the transformed field at M points, given dL/dPsi there (device arrays)
+template <typename R>
+pstd_status run_transform_adjoint(pstd_grid* g, int b, const double* pts, const double2* gpts, long M, double2* out)
+{
+    pstd_status st = setup_transform(g);
+    if (st != PSTD_OK) return st;
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const int G = g->G, H = G / 2, REC = 2 * G * G;
+    AdjointTransformArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    for (int fi = 0; fi < 6; ++fi) a.face[fi] = g->faces[fi];
+    a.pts = pts;
+    a.gpts = gpts;
+    a.M = M;
+    a.k = g->mem[b].k;
+    for (int q = 0; q < G; ++q) a.gl_node[q] = g->gl_x[q];
+    a.ncells = g->ncells;
+    st = ensure(g, &g->adj_table, g->adj_table_cap, (size_t)6 * M * sizeof(AdjPoint<R>));
+    if (st != PSTD_OK) return st;
+    a.table = static_cast<AdjPoint<R>*>(g->adj_table);
+    // split the points so that about four waves of CTAs (five resident per SM) run
+    long long maxitems = 0;
+    for (int f = 0; f < 6; ++f) maxitems = std::max(maxitems, (long long)g->faces[f].L * g->faces[f].M * H);
+    const long long ctas = 6 * ((maxitems + 127) / 128);
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev);
+    long long splits = std::max(1LL, std::min((4LL * 5 * nsm + ctas - 1) / ctas, ((long long)M + 127) / 128));
+    a.points_per_split = ((M + splits - 1) / splits + 127) / 128 * 128;
+    splits = (M + a.points_per_split - 1) / a.points_per_split;
+    const size_t nrec = (size_t)g->ncells * REC;
+    if (!g->adj_rec && dalloc(&g->adj_rec, nrec * g->csize) != cudaSuccess) return fail(g, PSTD_ENOMEM, "adjoint records");
+    if (splits > 1) {
+        st = ensure(g, &g->adj_partial, g->adj_partial_cap, (size_t)splits * nrec * g->csize);
+        if (st != PSTD_OK) return st;
+        a.partial = static_cast<C*>(g->adj_partial);
+    } else {
+        a.partial = static_cast<C*>(g->adj_rec);
+    }
+    {
+        Timer t(g, 5);
+        CK(g, launch_adj_points<R>(a, g->stream));
+        CK(g, launch_transform_adjoint<R>(a, G, (int)splits, g->stream));
+        if (splits > 1) CK(g, launch_sum_splits<R>(a.partial, (int)splits, (long long)nrec, static_cast<C*>(g->adj_rec), g->stream));
+    }
+    // records -> node values -> plane gradients: P_adj = Mc^H out_adj MbT^H
+    C* T1 = static_cast<C*>(g->T1);
+    for (int fi = 0; fi < 6; ++fi) {
+        const FaceGeom& F = g->faces[fi];
+        const int LG = F.L * G, MG = F.M * G;
+        Timer t(g, 4);
+        CK(g, launch_unpack_records<R>(static_cast<const C*>(g->adj_rec), F.L, F.M, G, g->gl_w_dev, 0.25 * F.db * F.dc,
+                                       F.cell0, static_cast<C*>(g->OutP), static_cast<C*>(g->OutD), g->stream));
+        for (int q = 0; q < 2; ++q) {
+            const C* oa = static_cast<const C*>(q == 0 ? g->OutP : g->OutD);
+            CK(g, launch_cgemm<C>(MG, F.Nb, LG, oa, LG, static_cast<const C*>(g->MbTH[fi]), F.Nb, T1, F.Nb,
+                                  make_double2(1.0, 0.0), g->stream));
+            CK(g, launch_cgemm<C>(F.Nc, F.Nb, MG, static_cast<const C*>(g->McH[fi]), MG, T1, F.Nb,
+                                  static_cast<C*>(g->adj_PA), F.Nb, make_double2(1.0, 0.0), g->stream));
+            CK(g, launch_widen<R>(static_cast<const C*>(g->adj_PA), out + g->face_off[fi] + q * g->face_size[fi],
+                                  (long long)F.Nb * F.Nc, g->stream));
+        }
+    }
+    return PSTD_OK;
+}
+
+// dL/dV on the box [lo, hi) by the discrete adjoint of an nsteps run from rest (batch 1),
+// given gph (device, nfreq blocks in the phasor layout) = dL/d(scaled phasors).  The forward
+// run is repeated with checkpoints of (psi^{n-1}, psi^n) every K steps; each segment is then
+// recomputed, and the adjoint levels nu are stepped backward with the forward kernels.
+template <typename R>
+pstd_status run_adjoint(pstd_grid* g, long nsteps, const double2* gph, const int lo[3], const int hi[3], long K, double* grad_out)
+{
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const MemberHost& m = g->mem[0];
+    const size_t sbytes = (size_t)g->ncell * g->csize;
+    const int nf = m.nfreq;
+    // incident phasors at r_O over the window (Eq. incpsiphasor): S_f
+    std::vector<cd> S(nf, cd(0, 0));
+    for (long long n = m.first; n < m.first + m.len; ++n) {
+        const double t = n * g->desc.dt;
+        const cd inc = envelope_at(m, t) * std::exp(cd(0.0, -m.w0 * t));
+        for (int f = 0; f < nf; ++f) S[f] += inc * std::exp(cd(0.0, m.omega[f] * t));
+    }
+    for (int f = 0; f < nf; ++f)
+        if (std::abs(S[f]) == 0.0) return fail(g, PSTD_ESTATE, "incident phasor at r_O is zero");
+    // injection volumes J_f = (1 / S_f) E^T conj(g_f)
+    pstd_status st = ensure(g, &g->adj_J, g->adj_J_cap, (size_t)nf * sbytes);
+    if (st != PSTD_OK) return st;
+    for (int f = 0; f < nf; ++f) {
+        InjectionArgs<R> ia;
+        std::memset(&ia, 0, sizeof(ia));
+        ia.g = gph + (size_t)f * g->acc_freq_stride;
+        for (int i = 0; i < 6; ++i) { ia.face_off[i] = g->face_off[i]; ia.face_size[i] = g->face_size[i]; }
+        for (int ax = 0; ax < 3; ++ax) {
+            ia.dw[ax] = static_cast<const C*>(g->dw[ax]);
+            ia.h[ax][0] = g->desc.huygens_lo[ax];
+            ia.h[ax][1] = g->desc.huygens_hi[ax];
+            ia.n[ax] = g->desc.n[ax];
+        }
+        ia.ncell = g->ncell;
+        const cd sc = 1.0 / S[f];
+        ia.scale = make_double2(sc.real(), sc.imag());
+        ia.J = reinterpret_cast<C*>(static_cast<char*>(g->adj_J) + (size_t)f * sbytes);
+        CK(g, launch_injection<R>(ia, g->stream));
+    }
+    // buffers
+    if (K <= 0) K = std::max(1L, (long)std::ceil(std::sqrt((double)nsteps)));
+    const long nseg = (nsteps + K - 1) / K;
+    st = ensure(g, &g->adj_ckpt, g->adj_ckpt_cap, (size_t)nseg * 2 * sbytes);
+    if (st != PSTD_OK) return st;
+    st = ensure(g, &g->adj_seg, g->adj_seg_cap, (size_t)K * sbytes);
+    if (st != PSTD_OK) return st;
+    st = ensure(g, &g->adj_nu, g->adj_nu_cap, 2 * sbytes);
+    if (st != PSTD_OK) return st;
+    const long long box = (long long)(hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]);
+    st = ensure(g, &g->adj_grad, g->adj_grad_cap, (size_t)box * sizeof(double));
+    if (st != PSTD_OK) return st;
+    if (!g->adj_zero) {
+        CK(g, dalloc(&g->adj_zero, 16));
+        CK(g, cudaMemsetAsync(g->adj_zero, 0, 16, g->stream));
+    }
+    char* ckpt = static_cast<char*>(g->adj_ckpt);
+    char* seg = static_cast<char*>(g->adj_seg);
+    // forward with checkpoints (the running DFT is left as it is)
+    CK(g, cudaMemsetAsync(g->buf[0], 0, sbytes, g->stream));
+    CK(g, cudaMemsetAsync(g->buf[1], 0, sbytes, g->stream));
+    g->n = 0;
+    g->cur = 0;
+    for (long s = 0; s < nseg; ++s) {
+        CK(g, cudaMemcpyAsync(ckpt + (size_t)(2 * s) * sbytes, g->buf[g->cur ^ 1], sbytes, cudaMemcpyDeviceToDevice, g->stream));
+        CK(g, cudaMemcpyAsync(ckpt + (size_t)(2 * s + 1) * sbytes, g->buf[g->cur], sbytes, cudaMemcpyDeviceToDevice, g->stream));
+        st = run_steps<R>(g, std::min(K, nsteps - s * K), false);
+        if (st != PSTD_OK) return st;
+    }
+    // backward
+    C* nu[2] = {static_cast<C*>(g->adj_nu), reinterpret_cast<C*>(static_cast<char*>(g->adj_nu) + sbytes)};
+    int nc = 0;   // nu[nc] = nu^{n+1} (current), nu[nc ^ 1] = nu^{n+2} (previous)
+    CK(g, cudaMemsetAsync(g->adj_nu, 0, 2 * sbytes, g->stream));
+    CK(g, cudaMemsetAsync(g->adj_grad, 0, (size_t)box * sizeof(double), g->stream));
+    const bool need_src = g->vhi[0] > g->vlo[0];
+    const bool exact = g->desc.tfsf_mode == PSTD_TFSF_EXACT;
+    for (long s = nseg - 1; s >= 0; --s) {
+        const long n0 = s * K, n1 = std::min(nsteps, n0 + K);
+        // recompute u^{n0} .. u^{n1-1} into the segment buffer
+        g->cur = 0;
+        CK(g, cudaMemcpyAsync(g->buf[1], ckpt + (size_t)(2 * s) * sbytes, sbytes, cudaMemcpyDeviceToDevice, g->stream));
+        CK(g, cudaMemcpyAsync(g->buf[0], ckpt + (size_t)(2 * s + 1) * sbytes, sbytes, cudaMemcpyDeviceToDevice, g->stream));
+        CK(g, cudaMemcpyAsync(seg, g->buf[0], sbytes, cudaMemcpyDeviceToDevice, g->stream));
+        g->n = n0;
+        if (n1 - n0 > 1) {
+            st = run_steps<R>(g, n1 - n0 - 1, false, seg);
+            if (st != PSTD_OK) return st;
+        }
+        for (long n = n1 - 1; n >= n0; --n) {
+            const double t = n * g->desc.dt;
+            // dL/dV += (2 dt / hbar) Im[nu^{n+1} (u^n + psi_inc^n)]
+            GradArgs<R> ga;
+            std::memset(&ga, 0, sizeof(ga));
+            ga.nu = nu[nc];
+            ga.u = reinterpret_cast<const C*>(seg + (size_t)(n - n0) * sbytes);
+            for (int ax = 0; ax < 3; ++ax) {
+                ga.phase[ax] = static_cast<const C*>(g->phase[ax]);
+                ga.lo[ax] = lo[ax];
+                ga.hi[ax] = hi[ax];
+            }
+            const cd sf = envelope_at(m, t) * std::exp(cd(0.0, -m.w0 * t));
+            ga.s = make_c<C>(R(sf.real()), R(sf.imag()));
+            ga.with_inc = exact ? 1 : 0;
+            ga.nx = g->desc.n[0];
+            ga.ny = g->desc.n[1];
+            ga.c2 = 2.0 * g->desc.dt / g->desc.hbar;
+            ga.grad = g->adj_grad;
+            CK(g, launch_grad<R>(ga, g->stream));
+            // observation term on the DFT-window steps: nu^{n+2} += sum_f e^{i w_f t_n} J_f
+            if (nf > 0 && n >= m.first && n < m.first + m.len)
+                for (int f = 0; f < nf; ++f) {
+                    const cd e = std::exp(cd(0.0, m.omega[f] * t));
+                    CK(g, launch_inject<R>(nu[nc ^ 1], reinterpret_cast<const C*>(static_cast<char*>(g->adj_J) + (size_t)f * sbytes),
+                                           make_c<C>(R(e.real()), R(e.imag())), g->ncell, g->stream));
+                }
+            // nu^n = Gamma [nu^{n+2} - (2 i dt / hbar)(eta hbar^2/2m K + V) nu^{n+1}]: the forward
+            // step with the EXACT V-term and no incident wave
+            StepArgs<R> a = step_args<R>(g);
+            a.cur = nu[nc];
+            a.prev = nu[nc ^ 1];
+            a.mode = PSTD_TFSF_EXACT;
+            a.tfac = static_cast<const C*>(g->adj_zero);
+            a.tfac_base = 0;
+            a.step = 0;
+            a.batch = 1;
+            st = enqueue_step<R>(g, a, 0, nullptr, nullptr, nullptr, need_src);
+            if (st != PSTD_OK) return st;
+            nc ^= 1;
+        }
+    }
+    CK(g, cudaMemcpyAsync(grad_out, g->adj_grad, (size_t)box * sizeof(double), cudaMemcpyDeviceToDevice, g->stream));
+    // leave the grid at rest: state zero, step 0 (the running DFT is untouched)
+    CK(g, cudaMemsetAsync(g->buf[0], 0, sbytes, g->stream));
+    CK(g, cudaMemsetAsync(g->buf[1], 0, sbytes, g->stream));
+    g->n = 0;
+    g->cur = 0;
+    return PSTD_OK;
+}
+
 }  // namespace
 
 namespace pstd {
@@ -933,9 +1208,14 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     for (int a = 0; a < 3; ++a)
         for (void* p : {g->tw[a], g->kin[a], g->mask[a], g->zeta[a], g->zeta1[a], g->zeta2[a], g->phase[a], g->dw[a]})
             if (p) cudaFree(p);
+    for (void* p : {g->adj_table, g->adj_partial, g->adj_rec, g->adj_PA, (void*)g->adj_gpts, (void*)g->adj_out, g->adj_J,
+                    g->adj_ckpt, g->adj_seg, g->adj_nu, g->adj_zero, (void*)g->adj_grad})
+        if (p) cudaFree(p);
     for (int f = 0; f < 6; ++f) {
         if (g->MbT[f]) cudaFree(g->MbT[f]);
         if (g->Mc[f]) cudaFree(g->Mc[f]);
+        if (g->MbTH[f]) cudaFree(g->MbTH[f]);
+        if (g->McH[f]) cudaFree(g->McH[f]);
         for (int q = 0; q < 2; ++q)
             if (g->Fdft[f][q]) cudaFree(g->Fdft[f][q]);
     }
@@ -1386,3 +1666,72 @@ const char* pstd_last_error(const pstd_grid* g)
 }
 
 }  // extern "C"
+
+pstd_status pstd_transform_adjoint(pstd_grid* g, int b, int f, const double* xyz, long M, const void* dl_dpsi, void* out,
+                                   int mem)
+{
+    if (!g || !out || (M > 0 && (!xyz || !dl_dpsi))) return fail(g, PSTD_EINVAL, "null argument");
+    if (M < 0) return fail(g, PSTD_EINVAL, "M");
+    if (mem != PSTD_MEM_HOST && mem != PSTD_MEM_DEVICE) return fail(g, PSTD_EINVAL, "mem");
+    DeviceGuard dg(g->dev);
+    pstd_status st = check_member(g, b);
+    if (st != PSTD_OK) return st;
+    if (!g->mem[b].has_inc) return fail(g, PSTD_ESTATE, "pstd_set_incidence first (the transform needs k)");
+    if (f < 0 || f >= std::max(1, g->mem[b].nfreq)) return fail(g, PSTD_EINVAL, "frequency index out of range");
+    const size_t count = (size_t)g->acc_freq_stride;
+    st = ensure(g, &g->adj_out, g->adj_out_cap, count * sizeof(double2));
+    if (st != PSTD_OK) return st;
+    CK(g, cudaMemsetAsync(g->adj_out, 0, count * sizeof(double2), g->stream));
+    if (M > 0) {
+        const double* pts = xyz;
+        const double2* gp = static_cast<const double2*>(dl_dpsi);
+        if (mem == PSTD_MEM_HOST) {
+            st = ensure(g, &g->pts_dev, g->pts_cap, sizeof(double) * 3 * M);
+            if (st != PSTD_OK) return st;
+            st = ensure(g, &g->adj_gpts, g->adj_gpts_cap, sizeof(double2) * M);
+            if (st != PSTD_OK) return st;
+            CK(g, cudaMemcpyAsync(g->pts_dev, xyz, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, g->stream));
+            CK(g, cudaMemcpyAsync(g->adj_gpts, dl_dpsi, sizeof(double2) * M, cudaMemcpyHostToDevice, g->stream));
+            pts = g->pts_dev;
+            gp = g->adj_gpts;
+        }
+        st = g->prec == PSTD_F64 ? run_transform_adjoint<double>(g, b, pts, gp, M, g->adj_out)
+                                 : run_transform_adjoint<float>(g, b, pts, gp, M, g->adj_out);
+        if (st != PSTD_OK) return st;
+    }
+    return copy_out(g, out, g->adj_out, count * sizeof(double2), mem);
+}
+
+pstd_status pstd_adjoint_gradient(pstd_grid* g, long nsteps, const void* dl_dphasors, const int box_lo[3],
+                                  const int box_hi[3], long checkpoint_interval, double* dl_dv, int mem)
+{
+    if (!g || !dl_dphasors || !box_lo || !box_hi || !dl_dv) return fail(g, PSTD_EINVAL, "null argument");
+    if (mem != PSTD_MEM_HOST && mem != PSTD_MEM_DEVICE) return fail(g, PSTD_EINVAL, "mem");
+    if (g->batch != 1) return fail(g, PSTD_EINVAL, "the adjoint runs on grids with batch 1");
+    if (nsteps <= 0 || checkpoint_interval < 0) return fail(g, PSTD_EINVAL, "nsteps / checkpoint_interval");
+    DeviceGuard dg(g->dev);
+    const MemberHost& m = g->mem[0];
+    if (!m.has_inc) return fail(g, PSTD_ESTATE, "pstd_set_incidence first");
+    if (m.nfreq < 1 || m.len < 1) return fail(g, PSTD_ESTATE, "pstd_huygens_dft first (the loss is a function of the phasors)");
+    if (m.first + m.len > nsteps) return fail(g, PSTD_EINVAL, "the DFT window must end within nsteps");
+    for (int a = 0; a < 3; ++a)
+        if (box_lo[a] < 0 || box_hi[a] > g->desc.n[a] || box_lo[a] >= box_hi[a]) return fail(g, PSTD_EINVAL, "box");
+    const size_t count = (size_t)g->acc_freq_stride * m.nfreq;
+    pstd_status st = ensure(g, &g->adj_out, g->adj_out_cap, count * sizeof(double2));
+    if (st != PSTD_OK) return st;
+    CK(g, cudaMemcpyAsync(g->adj_out, dl_dphasors, count * sizeof(double2),
+                          mem == PSTD_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, g->stream));
+    const long long box = (long long)(box_hi[0] - box_lo[0]) * (box_hi[1] - box_lo[1]) * (box_hi[2] - box_lo[2]);
+    double* dst = dl_dv;
+    if (mem == PSTD_MEM_HOST) {
+        st = ensure(g, &g->pts_dev, g->pts_cap, sizeof(double) * box);   // staging
+        if (st != PSTD_OK) return st;
+        dst = g->pts_dev;
+    }
+    st = g->prec == PSTD_F64 ? run_adjoint<double>(g, nsteps, g->adj_out, box_lo, box_hi, checkpoint_interval, dst)
+                             : run_adjoint<float>(g, nsteps, g->adj_out, box_lo, box_hi, checkpoint_interval, dst);
+    if (st != PSTD_OK) return st;
+    if (mem == PSTD_MEM_HOST) return copy_out(g, dl_dv, dst, sizeof(double) * box, PSTD_MEM_HOST);
+    CK(g, cudaStreamSynchronize(g->stream));
+    return PSTD_OK;
+}

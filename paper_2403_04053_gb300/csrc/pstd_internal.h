@@ -138,6 +138,77 @@ template <typename R> struct TransformArgs {
 };
 
 template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, int G, int splits, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------
+// discrete adjoint (see adjoint_kernels.cuh)
+// ---------------------------------------------------------------------------------
+// J = scale * E^T conj(g): g = gradient with respect to one frequency's scaled phasors
+// (six faces, psi plane then dpsi plane each, [c][b], faces at face_off)
+template <typename R> struct InjectionArgs {
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const double2* g;
+    long long face_off[6], face_size[6];
+    const C* dw[3];           // [2][N_axis] spectral-derivative weights of the two planes per axis
+    int h[3][2];              // plane node indices per axis (low, high)
+    int n[3];
+    long long ncell;
+    double2 scale;            // 1 / S_f
+    C* J;
+};
+
+// grad[box] += c2 Im[nu (u + s phase)] over the box [lo, hi), x fastest
+template <typename R> struct GradArgs {
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const C* nu;              // nu^{n+1}
+    const C* u;               // u^n
+    const C* phase[3];        // member 0's incident phase tables
+    C s;                      // a(t_n) e^{-i w0 t_n}
+    int with_inc;             // EXACT form: add psi_inc^n
+    int nx, ny;
+    int lo[3], hi[3];
+    double c2;                // 2 dt / hbar
+    double* grad;
+};
+
+template <typename R> struct AdjPoint {
+    R d0a, d0b, d0c, R0;      // point minus face centre (normal, b, c) and its length
+    R ax, ay;                 // pref conj(e^{ik R0}) dL/dPsi_p
+};
+
+template <typename R> struct AdjointTransformArgs {
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    FaceGeom face[6];
+    const double* pts;        // M x 3
+    const double2* gpts;      // dL/dPsi per point
+    long long M;
+    double k;
+    double gl_node[16];
+    AdjPoint<R>* table;       // [6][M]
+    long long ncells;
+    long long points_per_split;
+    C* partial;               // [split][ncells][2 G G]
+};
+
+template <typename R> cudaError_t launch_injection(const InjectionArgs<R>& a, cudaStream_t s);
+template <typename R>
+cudaError_t launch_inject(typename std::conditional<sizeof(R) == 4, float2, double2>::type* prev,
+                          const typename std::conditional<sizeof(R) == 4, float2, double2>::type* J,
+                          typename std::conditional<sizeof(R) == 4, float2, double2>::type coef, long long n, cudaStream_t s);
+template <typename R> cudaError_t launch_grad(const GradArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_adj_points(const AdjointTransformArgs<R>& a, cudaStream_t s);
+template <typename R> cudaError_t launch_transform_adjoint(const AdjointTransformArgs<R>& a, int G, int splits, cudaStream_t s);
+template <typename R>
+cudaError_t launch_sum_splits(const typename std::conditional<sizeof(R) == 4, float2, double2>::type* partial, int splits,
+                              long long n, typename std::conditional<sizeof(R) == 4, float2, double2>::type* rec,
+                              cudaStream_t s);
+template <typename R>
+cudaError_t launch_unpack_records(const typename std::conditional<sizeof(R) == 4, float2, double2>::type* rec, int L, int M,
+                                  int G, const double* glw, double cw, long long cell0,
+                                  typename std::conditional<sizeof(R) == 4, float2, double2>::type* op,
+                                  typename std::conditional<sizeof(R) == 4, float2, double2>::type* od, cudaStream_t s);
+template <typename R>
+cudaError_t launch_widen(const typename std::conditional<sizeof(R) == 4, float2, double2>::type* in, double2* out,
+                         long long n, cudaStream_t s);
 cudaError_t launch_reduce_partials(const double2* partial, int splits, long long M, double2* out,
                                    double* dsdo, cudaStream_t s);
 // complex GEMM C[MxN] = alpha * A[MxK] B[KxN] (row-major, leading dims given), C = float2 or double2

@@ -65,6 +65,8 @@ _SIGS = {
     "pstd_kernel_stats": (c_int, [c_void_p, c_int, POINTER(c_long), POINTER(c_double)]),
     "pstd_launch_count": (c_int, [c_void_p, POINTER(c_long)]),
     "pstd_last_error": (ctypes.c_char_p, [c_void_p]),
+    "pstd_transform_adjoint": (c_int, [c_void_p, c_int, c_int, c_void_p, c_long, c_void_p, c_void_p, c_int]),
+    "pstd_adjoint_gradient": (c_int, [c_void_p, c_long, c_void_p, POINTER(c_int), POINTER(c_int), c_long, c_void_p, c_int]),
 }
 
 _lib = None
@@ -229,18 +231,73 @@ class Grid:
             raise ValueError("prev and cur must both be host arrays or both device tensors")
         self._c(self.lib.pstd_set_field(self.h, b, pp, pc, int(n), mp), "pstd_set_field")
 
-    def get_phasors(self, b: int = 0, f: int = 0):
-        """Six (psi, d psi / d axis) plane pairs (complex128), face order 2*axis + side."""
+    def _plane_shapes(self):
         nx, ny, nz = self.spec.n
-        shapes = [(nz, ny), (nz, ny), (nz, nx), (nz, nx), (ny, nx), (ny, nx)]
-        total = sum(2 * s[0] * s[1] for s in shapes)
-        buf = np.empty(total, dtype=np.complex128)
-        self._c(self.lib.pstd_get_phasors(self.h, b, f, buf.ctypes.data_as(c_void_p), MEM_HOST), "pstd_get_phasors")
+        return [(nz, ny), (nz, ny), (nz, nx), (nz, nx), (ny, nx), (ny, nx)]
+
+    def phasor_count(self) -> int:
+        """complex128 entries of one frequency's phasors (six faces, psi then d psi plane)."""
+        return sum(2 * s[0] * s[1] for s in self._plane_shapes())
+
+    def split_phasors(self, buf):
+        """Flat phasor-layout array -> six (psi, d psi) plane pairs (views)."""
         out, off = [], 0
-        for s in shapes:
+        for s in self._plane_shapes():
             m = s[0] * s[1]
             out.append((buf[off:off + m].reshape(s), buf[off + m:off + 2 * m].reshape(s)))
             off += 2 * m
+        return out
+
+    def join_phasors(self, pairs) -> np.ndarray:
+        """Six (psi, d psi) plane pairs -> flat phasor-layout complex128 array."""
+        return np.concatenate([np.asarray(a, dtype=np.complex128).ravel() for pair in pairs for a in pair])
+
+    def get_phasors(self, b: int = 0, f: int = 0):
+        """Six (psi, d psi / d axis) plane pairs (complex128), face order 2*axis + side."""
+        buf = np.empty(self.phasor_count(), dtype=np.complex128)
+        self._c(self.lib.pstd_get_phasors(self.h, b, f, buf.ctypes.data_as(c_void_p), MEM_HOST), "pstd_get_phasors")
+        return self.split_phasors(buf)
+
+    # -- discrete adjoint -----------------------------------------------------------
+    def transform_adjoint(self, b: int, f: int, xyz, dl_dpsi):
+        """Gradient with respect to the scaled phasors (pstd_transform_adjoint).  Host inputs
+        give six (psi, d psi) plane pairs; CUDA tensors give a flat complex128 tensor."""
+        if _is_cuda_tensor(xyz):
+            import torch
+            g = dl_dpsi.to(torch.complex128).contiguous()
+            out = torch.empty(self.phasor_count(), dtype=torch.complex128, device=xyz.device)
+            self._c(self.lib.pstd_transform_adjoint(self.h, b, f, c_void_p(xyz.data_ptr()), int(xyz.shape[0]),
+                                                    c_void_p(g.data_ptr()), c_void_p(out.data_ptr()), MEM_DEVICE),
+                    "pstd_transform_adjoint")
+            return out
+        pts = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        g = np.ascontiguousarray(dl_dpsi, dtype=np.complex128)
+        out = np.empty(self.phasor_count(), dtype=np.complex128)
+        self._c(self.lib.pstd_transform_adjoint(self.h, b, f, pts.ctypes.data_as(c_void_p), len(pts),
+                                                g.ctypes.data_as(c_void_p), out.ctypes.data_as(c_void_p), MEM_HOST),
+                "pstd_transform_adjoint")
+        return self.split_phasors(out)
+
+    def adjoint_gradient(self, nsteps: int, dl_dphasors, box_lo, box_hi, checkpoint_interval: int = 0):
+        """dL/dV on the node box [box_lo, box_hi) (x, y, z) as a [z, y, x] array
+        (pstd_adjoint_gradient).  dl_dphasors: per frequency, six plane pairs or a flat
+        array; or one flat CUDA tensor holding every frequency (then the result is a CUDA tensor)."""
+        lo = (c_int * 3)(*[int(v) for v in box_lo])
+        hi = (c_int * 3)(*[int(v) for v in box_hi])
+        shape = (int(box_hi[2]) - int(box_lo[2]), int(box_hi[1]) - int(box_lo[1]), int(box_hi[0]) - int(box_lo[0]))
+        if _is_cuda_tensor(dl_dphasors):
+            import torch
+            g = dl_dphasors.to(torch.complex128).contiguous()
+            out = torch.empty(shape, dtype=torch.float64, device=g.device)
+            self._c(self.lib.pstd_adjoint_gradient(self.h, int(nsteps), c_void_p(g.data_ptr()), lo, hi, int(checkpoint_interval),
+                                                   c_void_p(out.data_ptr()), MEM_DEVICE), "pstd_adjoint_gradient")
+            return out
+        blocks = [self.join_phasors(x) if isinstance(x, (list, tuple)) else np.asarray(x, dtype=np.complex128).ravel()
+                  for x in dl_dphasors]
+        g = np.ascontiguousarray(np.concatenate(blocks))
+        out = np.empty(shape, dtype=np.float64)
+        self._c(self.lib.pstd_adjoint_gradient(self.h, int(nsteps), g.ctypes.data_as(c_void_p), lo, hi, int(checkpoint_interval),
+                                               out.ctypes.data_as(c_void_p), MEM_HOST), "pstd_adjoint_gradient")
         return out
 
     # -- transforms -----------------------------------------------------------------
@@ -307,3 +364,54 @@ def setup_workload(grid: Grid, wl, b: int = 0, inc_index: int = 0, nfreq_omegas=
     grid.set_incidence(b, inc.khat, inc.k, inc.ramp_time)
     w0 = wl.spec.hbar * inc.k ** 2 / (2 * wl.spec.mass)
     grid.huygens_dft(b, nfreq_omegas or [w0], wl.window_first, wl.window_len)
+
+
+def fresnel_field(V, grid: Grid, points, nsteps: int, box_lo, box_hi, checkpoint_interval: int = 0):
+    """Psi at `points` after an nsteps run from rest, differentiable with respect to V.
+
+    V: real CUDA tensor [z, y, x] on the grid (the whole potential); points: CUDA tensor
+    M x 3 (float64).  The grid must hold member 0's incidence and DFT window (batch 1).
+    Backward is the discrete adjoint (pstd_transform_adjoint, pstd_adjoint_gradient); the
+    gradient is computed on the node box [box_lo, box_hi) and is zero outside it."""
+    return _FresnelField.apply(V, grid, points, int(nsteps), tuple(box_lo), tuple(box_hi), int(checkpoint_interval))
+
+
+def _make_fresnel_function():
+    import torch
+
+    class FresnelField(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, V, grid, points, nsteps, box_lo, box_hi, checkpoint_interval):
+            grid.set_potential(V.detach().contiguous())
+            grid.reset()
+            grid.step(nsteps)
+            psi = grid.transform_to_points(0, 0, points)
+            ctx.grid, ctx.points, ctx.nsteps = grid, points, nsteps
+            ctx.box = (box_lo, box_hi, checkpoint_interval)
+            ctx.vshape, ctx.vdtype = V.shape, V.dtype
+            return psi
+
+        @staticmethod
+        def backward(ctx, grad_psi):
+            grid = ctx.grid
+            lo, hi, K = ctx.box
+            g_ph = grid.transform_adjoint(0, 0, ctx.points, grad_psi)
+            gbox = grid.adjoint_gradient(ctx.nsteps, g_ph, lo, hi, K)
+            gV = torch.zeros(ctx.vshape, dtype=ctx.vdtype, device=gbox.device)
+            gV[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = gbox.to(ctx.vdtype)
+            return gV, None, None, None, None, None, None
+
+    return FresnelField
+
+
+class _LazyFunction:
+    """Defers `import torch` until the autograd function is first used."""
+    _fn = None
+
+    def apply(self, *args):
+        if _LazyFunction._fn is None:
+            _LazyFunction._fn = _make_fresnel_function()
+        return _LazyFunction._fn.apply(*args)
+
+
+_FresnelField = _LazyFunction()

@@ -1,0 +1,218 @@
+"""GPU discrete adjoint against the FP64 oracle's adjoint and against finite differences.
+
+Tolerances (relative, from the arithmetic): FP64 path 1e-9 (the G = 8 cell quadrature
+reproduces the oracle's sinc sum to ~1e-13; the backward sweep adds round-off of the
+same order as the forward run); FP32 path 2e-4 on the transform adjoint and 2e-3 on
+dL/dV (single-precision round-off accumulated over the forward and the backward sweep,
+ten times the FP32 state tolerance); finite differences 1e-6 (central differences with
+h = 1e-4 in FP64).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import adjoint_oracle as ao
+from paper_2403_04053_gb300 import inputs, pstd
+
+pytestmark = pytest.mark.gpu
+
+K = 2 * math.pi
+E0 = 0.5 * K * K
+KHAT = (0.3, -0.5, 0.81)
+PTS = np.array([[3.0, -2.0, 5.5], [-4.0, 6.0, 1.0], [0.5, 0.2, -9.0], [1.0, 2.0, 3.0]])
+TARGET = np.full(len(PTS), 0.01)
+NSTEPS, WIN = 80, (50, 30)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def small_spec(mode):
+    return inputs.GridSpec(n=(24, 24, 24), d=(0.25, 0.25, 0.25), dt=0.004, abc_cells=(3, 3, 3), tfsf_lo=(6, 6, 6),
+                           tfsf_hi=(17, 17, 17), taper_cells=2, huygens_lo=(4, 4, 4), huygens_hi=(19, 19, 19),
+                           tfsf_mode=mode)
+
+
+def core_V(spec, seed):
+    rng = np.random.default_rng(seed)
+    V = np.zeros(spec.shape)
+    c = spec.core_box()
+    sl = (slice(c[2][0], c[2][1] + 1), slice(c[1][0], c[1][1] + 1), slice(c[0][0], c[0][1] + 1))
+    V[sl] = rng.uniform(-3, 3, V[sl].shape)
+    return V
+
+
+def gpu_forward(spec, V, prec, nsteps=NSTEPS, win=WIN):
+    g = pstd.Grid(spec, precision=prec)
+    g.set_potential(V)
+    g.set_incidence(0, KHAT, K, 0.05)
+    g.huygens_dft(0, [E0], *win)
+    g.step(nsteps)
+    psi = g.transform_to_points(0, 0, PTS)
+    L, gpts = ao.magnitude_misfit(psi, TARGET)
+    return g, psi, L, gpts
+
+
+def box_of(spec, mode):
+    if mode == "exact":
+        return (2, 2, 2), (22, 22, 22)          # beyond the core too, where V itself must vanish
+    c = spec.core_box()
+    return tuple(c[a][0] for a in range(3)), tuple(c[a][1] + 1 for a in range(3))
+
+
+def sub(arr, lo, hi):
+    return arr[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]
+
+
+@pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-9), (pstd.F32, 2e-4)])
+def test_transform_adjoint_matches_oracle(prec, tol):
+    spec = small_spec("exact")
+    rng = np.random.default_rng(2)
+    y = rng.standard_normal(len(PTS)) + 1j * rng.standard_normal(len(PTS))
+    with pstd.Grid(spec, precision=prec) as g:
+        g.set_incidence(0, KHAT, K, 0.05)
+        got = g.transform_adjoint(0, 0, PTS, y)
+    ref = ao.transform_adjoint(spec, K, PTS, y)
+    assert rel(g.join_phasors(got), g.join_phasors(ref)) < tol
+
+
+@pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-9), (pstd.F32, 2e-3)])
+@pytest.mark.parametrize("mode", ["exact", "paper"])
+def test_adjoint_gradient_matches_oracle(mode, prec, tol):
+    spec = small_spec(mode)
+    V = core_V(spec, 7)
+    L_ref, grad_ref, psi_ref = ao.fresnel_loss_and_gradient(spec, V, KHAT, K, 0.05, WIN, NSTEPS, PTS, TARGET)
+    lo, hi = box_of(spec, mode)
+    g, psi, L, gpts = gpu_forward(spec, V, prec)
+    with g:
+        assert rel(psi, psi_ref) < (1e-10 if prec == pstd.F64 else 2e-4)
+        g_ph = g.transform_adjoint(0, 0, PTS, gpts)
+        grad = g.adjoint_gradient(NSTEPS, [g_ph], lo, hi)
+        assert g.get_step() == 0                   # left at rest
+    assert rel(grad, sub(grad_ref, lo, hi)) < tol
+
+
+def test_adjoint_gradient_matches_gpu_finite_differences():
+    spec = small_spec("exact")
+    V = core_V(spec, 9)
+    lo, hi = (2, 2, 2), (22, 22, 22)
+    g, psi, L, gpts = gpu_forward(spec, V, pstd.F64)
+    with g:
+        grad = g.adjoint_gradient(NSTEPS, [g.transform_adjoint(0, 0, PTS, gpts)], lo, hi)
+    h = 1e-4
+    errs = []
+    for (z, y, x) in [(12, 11, 10), (9, 14, 12), (10, 10, 14), (15, 8, 13)]:   # inside the core
+        Lpm = []
+        for sgn in (1, -1):
+            Vp = V.copy()
+            Vp[z, y, x] += sgn * h
+            gp, _, Lp, _ = gpu_forward(spec, Vp, pstd.F64)
+            gp.close()
+            Lpm.append(Lp)
+        fd = (Lpm[0] - Lpm[1]) / (2 * h)
+        errs.append(abs(fd - grad[z - lo[2], y - lo[1], x - lo[0]]))
+    assert max(errs) / np.abs(grad).max() < 1e-6
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    spec = small_spec("exact")
+    V = core_V(spec, 7)
+    g, psi, L, gpts = gpu_forward(spec, V, pstd.F64)
+    with g:
+        g_ph = g.transform_adjoint(0, 0, PTS, gpts)
+        lo, hi = box_of(spec, "exact")
+        grads = [g.adjoint_gradient(NSTEPS, [g_ph], lo, hi, k) for k in (0, 1, 7, NSTEPS)]
+    for other in grads[1:]:
+        assert rel(other, grads[0]) < 1e-13
+
+
+def test_autograd_function_matches_the_adjoint():
+    torch = pytest.importorskip("torch")
+    spec = small_spec("exact")
+    V = core_V(spec, 7)
+    lo, hi = box_of(spec, "exact")
+    with pstd.Grid(spec, precision=pstd.F64) as g:
+        g.set_incidence(0, KHAT, K, 0.05)
+        g.huygens_dft(0, [E0], *WIN)
+        Vt = torch.tensor(V, device="cuda", requires_grad=True)
+        pts = torch.tensor(PTS, device="cuda")
+        psi = pstd.fresnel_field(Vt, g, pts, NSTEPS, lo, hi)
+        loss = ((psi.abs() - torch.tensor(TARGET, device="cuda")) ** 2).sum()
+        loss.backward()
+        gV = Vt.grad.cpu().numpy()
+    L_ref, grad_ref, _ = ao.fresnel_loss_and_gradient(spec, V, KHAT, K, 0.05, WIN, NSTEPS, PTS, TARGET)
+    assert abs(float(loss.detach()) - L_ref) < 1e-9 * L_ref
+    assert rel(sub(gV, lo, hi), sub(grad_ref, lo, hi)) < 1e-9
+    outside = gV.copy()
+    outside[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = 0
+    assert not outside.any()
+
+
+def test_adjoint_call_errors():
+    spec = small_spec("exact")
+    gph = [np.zeros(1)]
+    with pstd.Grid(spec, precision=pstd.F32, batch=2) as g:
+        with pytest.raises(pstd.PstdError) as e:
+            g.adjoint_gradient(10, gph, (0, 0, 0), (4, 4, 4))
+        assert e.value.code == "EINVAL"
+    with pstd.Grid(spec, precision=pstd.F32) as g:
+        g.set_incidence(0, KHAT, K, 0.05)
+        with pytest.raises(pstd.PstdError) as e:
+            g.adjoint_gradient(10, gph, (0, 0, 0), (4, 4, 4))
+        assert e.value.code == "ESTATE"       # no DFT window
+        g.huygens_dft(0, [E0], 5, 10)
+        z = np.zeros(g.phasor_count(), dtype=np.complex128)
+        for lo, hi in [((0, 0, 0), (25, 4, 4)), ((3, 0, 0), (3, 4, 4)), ((-1, 0, 0), (4, 4, 4))]:
+            with pytest.raises(pstd.PstdError) as e:
+                g.adjoint_gradient(20, [z], lo, hi)
+            assert e.value.code == "EINVAL"
+        with pytest.raises(pstd.PstdError) as e:
+            g.adjoint_gradient(12, [z], (0, 0, 0), (4, 4, 4))   # window ends after step 12
+        assert e.value.code == "EINVAL"
+        # a zero loss gradient gives a zero dL/dV
+        assert not g.adjoint_gradient(20, [z], (0, 0, 0), (4, 4, 4)).any()
+
+
+def test_full_size_adjoint_against_finite_differences():
+    # 128^3 Gaussian-sum grid, FP64, a 400-step run (window the last 120 steps), 64 points of
+    # a Fresnel plane; central differences at four voxels of the central 48^3 block, and
+    # the FP32 adjoint against the FP64 one on the whole block
+    wl = inputs.gaussian_sum_workload(nsteps=400, with_outputs=False)
+    spec = wl.spec
+    inc = wl.incidences[0]
+    rng = np.random.default_rng(4)
+    pts = inputs.plane_points(inc.khat, 20.0, 18.0, 8)
+    target = np.abs(rng.standard_normal(len(pts))) * 1e-3
+    lo, hi = (40, 40, 40), (88, 88, 88)
+
+    def run(V, prec):
+        g = pstd.Grid(spec, precision=prec)
+        g.set_potential(V)
+        g.set_incidence(0, inc.khat, inc.k, inc.ramp_time)
+        g.huygens_dft(0, [E0], 280, 120)
+        g.step(400)
+        psi = g.transform_to_points(0, 0, pts)
+        L, gpts = ao.magnitude_misfit(psi, target)
+        return g, L, gpts
+
+    g, L, gpts = run(wl.V, pstd.F64)
+    with g:
+        grad64 = g.adjoint_gradient(400, [g.transform_adjoint(0, 0, pts, gpts)], lo, hi)
+    g, L32, gpts32 = run(wl.V, pstd.F32)
+    with g:
+        grad32 = g.adjoint_gradient(400, [g.transform_adjoint(0, 0, pts, gpts32)], lo, hi)
+    assert rel(grad32, grad64) < 2e-3
+    h = 1e-4
+    errs = []
+    for (z, y, x) in [(64, 64, 64), (60, 70, 55), (50, 45, 80), (75, 66, 61)]:
+        Lpm = []
+        for sgn in (1, -1):
+            V = wl.V.copy()
+            V[z, y, x] += sgn * h
+            gp, Lp, _ = run(V, pstd.F64)
+            gp.close()
+            Lpm.append(Lp)
+        errs.append(abs((Lpm[0] - Lpm[1]) / (2 * h) - grad64[z - lo[2], y - lo[1], x - lo[0]]))
+    assert max(errs) / np.abs(grad64).max() < 1e-6
