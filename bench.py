@@ -28,6 +28,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "PSTD cell-updates/s, FP32 vs FP64 at stated error (1 GB300); adjoint/forward time"
+
+# DRAM bytes (read + write) of one cold launch at 128^3, from an ncu --set full capture of
+# that kernel (dram__bytes_read.sum + dram__bytes_write.sum); drop an entry when its kernel changes
+DRAM_TRAFFIC = {"xypass": 34.05e6, "zpass": 34.74e6}
 WORKLOAD = "gaussian-sum-128^3"
 
 
@@ -217,7 +221,7 @@ def run_gpu(args):
     nl, ms = kstats[top]
     achieved = 24.0 * ncell / (ms / nl / 1e3) / 1e9
     roofline = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None,
+                "frac": round(achieved / hbm, 4), "traffic": DRAM_TRAFFIC.get(top),
                 "avg_launch_us": round(ms / nl * 1e3, 2), "algorithmic_bytes_per_launch": 24 * ncell,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback"}
     kernel_ms = {n: {"launches": c, "total_ms": round(t, 3)} for n, (c, t) in kstats.items()}
@@ -247,6 +251,10 @@ def run_gpu(args):
         g64.close()
     g.close()
 
+    # adjoint leg: gradient of the Fresnel-plane |Psi| misfit with respect to V on the central
+    # 48^3 block (128^3, FP32, 2000 steps, 128^2 points), timed against its forward run
+    adjoint = None if args.skip_adjoint else adjoint_leg(pstd, inputs, stream, dev)
+
     out = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -261,6 +269,7 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "kernels": kernel_ms,
         "fp64": fp64,
+        "adjoint": adjoint,
     }
     if rank == 0:
         out["clocks"] = clk.summary()
@@ -270,6 +279,52 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def adjoint_leg(pstd, inputs, stream, dev):
+    """Forward run + loss, then the discrete adjoint (transform adjoint + backward sweep with
+    sqrt(N) checkpoints), each timed with CUDA events on the library's stream."""
+    import torch
+    wl, V_target = inputs.adjoint_workload()
+    inc = wl.incidences[0]
+    w0 = wl.spec.hbar * inc.k ** 2 / (2 * wl.spec.mass)
+    lo, hi = (40, 40, 40), (88, 88, 88)
+    g = pstd.Grid(wl.spec, precision=pstd.F32, stream=stream.cuda_stream)
+    g.set_incidence(0, inc.khat, inc.k, inc.ramp_time)
+    g.huygens_dft(0, [w0], wl.window_first, wl.window_len)
+    pts = torch.from_numpy(wl.fresnel_points).to(dev)
+    g.set_potential(torch.from_numpy(V_target).to(dev))
+    g.reset()
+    g.step(wl.nsteps)
+    target = g.transform_to_points(0, 0, pts).abs()
+    V = torch.from_numpy(wl.V).to(dev)
+    g.set_potential(V)
+    times = []
+    for _ in range(3):   # the first repetition is a warm-up
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        g.reset()
+        g.step(wl.nsteps)
+        psi = g.transform_to_points(0, 0, pts)
+        ev[1].record(stream)
+        mag = psi.abs()
+        loss = ((mag - target) ** 2).sum()
+        gpts = 2 * (mag - target) * psi / mag
+        gph = g.transform_adjoint(0, 0, pts, gpts)
+        grad = g.adjoint_gradient(wl.nsteps, gph, lo, hi)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        times.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])))
+    g.close()
+    fwd = statistics.median(t[0] for t in times[1:])
+    adj = statistics.median(t[1] for t in times[1:])
+    K = math.ceil(math.sqrt(wl.nsteps))
+    return {"workload": "adjoint-128^3: V on the central 48^3 block (seeded smoothed noise), 2000 steps, "
+                        "|Psi| misfit on a 128^2 Fresnel plane", "dtype": "c64",
+            "forward_ms": round(fwd, 3), "adjoint_ms": round(adj, 3), "adjoint_over_forward": round(adj / fwd, 3),
+            "checkpoint_interval": K, "grad_box": [48, 48, 48], "loss": float(loss),
+            "grad_max_abs": float(grad.abs().max())}
 
 
 # ----------------------------------------------------------------------------------
@@ -339,6 +394,7 @@ def main():
     p.add_argument("--skip-cpu", action="store_true")
     p.add_argument("--skip-fp64", action="store_true")
     p.add_argument("--skip-e2e", action="store_true")
+    p.add_argument("--skip-adjoint", action="store_true")
     args = p.parse_args()
     if args.impl == "reference":
         run_reference(args)

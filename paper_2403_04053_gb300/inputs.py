@@ -322,3 +322,46 @@ def gaussian_sum_workload(n: int = 128, dx: float = 0.25, nsteps: int = 3000, se
         wl.fresnel_points = plane_points(khat, D * D / (4 * lam), 1.5 * D, fresnel_count)
         wl.far_theta, wl.far_phi = far_field_grid()
     return wl
+
+
+def smoothed_noise_potential(spec: GridSpec, seed: int, block: int = 48, sigma_cells: float = 2.0,
+                             amplitude: float = 1.0) -> np.ndarray:
+    """Seeded Gaussian noise on the central block^3 nodes, smoothed by a Gaussian of
+    sigma_cells (separable, truncated at 4 sigma), scaled so that max |V| = amplitude."""
+    rng = np.random.default_rng(seed)
+    V = np.zeros(spec.shape)
+    lo = [spec.n[a] // 2 - block // 2 for a in range(3)]
+    noise = rng.standard_normal((block, block, block))
+    r = int(math.ceil(4 * sigma_cells))
+    x = np.arange(-r, r + 1)
+    ker = np.exp(-0.5 * (x / sigma_cells) ** 2)
+    ker /= ker.sum()
+    for ax in range(3):
+        noise = np.apply_along_axis(lambda v: np.convolve(v, ker, mode="same"), ax, noise)
+    noise *= amplitude / np.max(np.abs(noise))
+    V[lo[2]:lo[2] + block, lo[1]:lo[1] + block, lo[0]:lo[0] + block] = noise
+    return V
+
+
+def adjoint_workload(n: int = 128, dx: float = 0.25, nsteps: int = 2000, seed: int = 2407, block: int = 48,
+                     fresnel_count: int = 128, abc: int = 16, tf=(24, 104), taper: int = 4, hb=(20, 108)):
+    """Inverse-scattering gradient case: V on the central block^3 from seeded smoothed noise
+    (sigma 2 cells, amplitude 0.2 E), k = 2 pi along a seeded direction, dt = 0.9 x the
+    stability bound; the loss is the L2 misfit of |Psi| on a fresnel_count^2 plane (normal to
+    khat at D^2/(4 lambda), side 1.5 D) against the field of a second seeded potential.
+    Returns (Workload, V_target); the workload's window is the last three carrier periods."""
+    k = 2 * math.pi
+    E0 = 0.5 * k * k
+    spec = GridSpec(n=(n, n, n), d=(dx, dx, dx), dt=1.0, abc_cells=(abc,) * 3,
+                    tfsf_lo=(tf[0],) * 3, tfsf_hi=(tf[1],) * 3, taper_cells=taper,
+                    huygens_lo=(hb[0],) * 3, huygens_hi=(hb[1],) * 3)
+    V = smoothed_noise_potential(spec, seed, block, 2.0, 0.2 * E0)
+    V_target = smoothed_noise_potential(spec, seed + 100, block, 2.0, 0.2 * E0)
+    spec.dt = stable_dt(spec.n, spec.d, 0.2 * E0)
+    khat = seeded_direction(seed + 1)
+    n0, M = dft_window(E0, spec.dt, nsteps)
+    wl = Workload(name=f"adjoint-{n}^3", spec=spec, V=V, incidences=[Incidence(tuple(khat), k, 0.5)],
+                  nsteps=nsteps, window_first=n0, window_len=M)
+    D = (tf[1] - taper - (tf[0] + taper)) * dx
+    wl.fresnel_points = plane_points(khat, D * D / (4 * (2 * math.pi / k)), 1.5 * D, fresnel_count)
+    return wl, V_target
