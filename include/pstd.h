@@ -231,6 +231,14 @@ pstd_status pstd_transform_adjoint(pstd_grid* g, int b, int f, const double* xyz
 pstd_status pstd_adjoint_gradient(pstd_grid* g, long nsteps, const void* dl_dphasors, const int box_lo[3],
                                   const int box_hi[3], long checkpoint_interval, double* dl_dv, int mem);
 
+/* Record adjoint checkpoints during pstd_step: from the next step taken from rest (after
+ * pstd_reset), the state pair (psi^{n-1}, psi^n) is copied aside every `interval` steps, for
+ * up to max_steps steps (allocated now: 2 ceil(max_steps/interval) states).  A later
+ * pstd_adjoint_gradient over nsteps <= the recorded run with the same checkpoint interval then
+ * uses them instead of repeating the forward run.  pstd_set_potential and pstd_set_incidence
+ * discard the record; pstd_set_field stops it.  interval 0 stops recording.  Batch-1 grids. */
+pstd_status pstd_set_checkpointing(pstd_grid* g, long interval, long max_steps);
+
 /* Message of the last failure on g (or of the last failed pstd_create_grid when g is NULL). */
 const char* pstd_last_error(const pstd_grid* g);
 

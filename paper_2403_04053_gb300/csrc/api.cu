@@ -122,6 +122,13 @@ struct pstd_grid {
     void* adj_zero = nullptr;               // one zero complex: the adjoint run's incident time factor
     double* adj_grad = nullptr;             // gradient accumulators on the box
     size_t adj_grad_cap = 0;
+    // checkpoints in adj_ckpt: segment s holds (psi^{sK-1}, psi^{sK}) of the run from rest;
+    // valid for s K < ckpt_upto and s < ckpt_slots (ckpt_upto = -1: none valid)
+    bool ckpt_record = false;               // pstd_step records them (pstd_set_checkpointing)
+    bool ckpt_contig = true;                // the state is the run from rest at step n (V, incidence unchanged)
+    long ckpt_K = 0;
+    long ckpt_slots = 0;
+    long long ckpt_upto = -1;
     void* rec = nullptr;
     int rec_member = -1, rec_freq = -1;
     long long rec_version = -1;
@@ -576,6 +583,18 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft 
             }
             ++g->phasor_version;
         }
+        // checkpoint recording for the adjoint: steps of the run from rest, recorded from step 0 on
+        if (dft && !save && g->ckpt_record && g->ckpt_contig && g->n == 0) g->ckpt_upto = 0;
+        const bool record = dft && !save && g->ckpt_record && g->ckpt_contig && g->ckpt_upto == g->n;
+        if (record && g->n % g->ckpt_K == 0) {
+            const long slot = (long)(g->n / g->ckpt_K);
+            if (slot < g->ckpt_slots) {
+                const size_t sb = (size_t)g->ncell * g->csize;
+                char* ck = static_cast<char*>(g->adj_ckpt);
+                CK(g, cudaMemcpyAsync(ck + (size_t)(2 * slot) * sb, g->buf[g->cur ^ 1], sb, cudaMemcpyDeviceToDevice, g->stream));
+                CK(g, cudaMemcpyAsync(ck + (size_t)(2 * slot + 1) * sb, g->buf[g->cur], sb, cudaMemcpyDeviceToDevice, g->stream));
+            }
+        }
         StepArgs<R> a = step_args<R>(g);
         a.tfac = static_cast<const typename StepArgs<R>::C*>(g->tfac);
         a.tfac_base = n0;
@@ -584,6 +603,7 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft 
         if (st != PSTD_OK) return st;
         g->cur ^= 1;
         ++g->n;
+        if (record) g->ckpt_upto = g->n;
         if (save)
             CK(g, cudaMemcpyAsync(static_cast<char*>(save) + (size_t)(s + 1) * g->ncell * g->csize, g->buf[g->cur],
                                   (size_t)g->ncell * g->csize, cudaMemcpyDeviceToDevice, g->stream));
@@ -981,8 +1001,6 @@ pstd_status run_adjoint(pstd_grid* g, long nsteps, const double2* gph, const int
     // buffers
     if (K <= 0) K = std::max(1L, (long)std::ceil(std::sqrt((double)nsteps)));
     const long nseg = (nsteps + K - 1) / K;
-    st = ensure(g, &g->adj_ckpt, g->adj_ckpt_cap, (size_t)nseg * 2 * sbytes);
-    if (st != PSTD_OK) return st;
     st = ensure(g, &g->adj_seg, g->adj_seg_cap, (size_t)K * sbytes);
     if (st != PSTD_OK) return st;
     st = ensure(g, &g->adj_nu, g->adj_nu_cap, 2 * sbytes);
@@ -994,19 +1012,29 @@ pstd_status run_adjoint(pstd_grid* g, long nsteps, const double2* gph, const int
         CK(g, dalloc(&g->adj_zero, 16));
         CK(g, cudaMemsetAsync(g->adj_zero, 0, 16, g->stream));
     }
-    char* ckpt = static_cast<char*>(g->adj_ckpt);
     char* seg = static_cast<char*>(g->adj_seg);
-    // forward with checkpoints (the running DFT is left as it is)
-    CK(g, cudaMemsetAsync(g->buf[0], 0, sbytes, g->stream));
-    CK(g, cudaMemsetAsync(g->buf[1], 0, sbytes, g->stream));
-    g->n = 0;
-    g->cur = 0;
-    for (long s = 0; s < nseg; ++s) {
-        CK(g, cudaMemcpyAsync(ckpt + (size_t)(2 * s) * sbytes, g->buf[g->cur ^ 1], sbytes, cudaMemcpyDeviceToDevice, g->stream));
-        CK(g, cudaMemcpyAsync(ckpt + (size_t)(2 * s + 1) * sbytes, g->buf[g->cur], sbytes, cudaMemcpyDeviceToDevice, g->stream));
-        st = run_steps<R>(g, std::min(K, nsteps - s * K), false);
+    // checkpoints: those pstd_step recorded for this run if they cover it, else a forward run
+    // that takes them (the running DFT is left as it is)
+    const bool recorded = g->ckpt_upto >= nsteps && g->ckpt_K == K && nseg <= g->ckpt_slots;
+    if (!recorded) {
+        st = ensure(g, &g->adj_ckpt, g->adj_ckpt_cap, (size_t)nseg * 2 * sbytes);
         if (st != PSTD_OK) return st;
+        char* ck = static_cast<char*>(g->adj_ckpt);
+        CK(g, cudaMemsetAsync(g->buf[0], 0, sbytes, g->stream));
+        CK(g, cudaMemsetAsync(g->buf[1], 0, sbytes, g->stream));
+        g->n = 0;
+        g->cur = 0;
+        for (long s = 0; s < nseg; ++s) {
+            CK(g, cudaMemcpyAsync(ck + (size_t)(2 * s) * sbytes, g->buf[g->cur ^ 1], sbytes, cudaMemcpyDeviceToDevice, g->stream));
+            CK(g, cudaMemcpyAsync(ck + (size_t)(2 * s + 1) * sbytes, g->buf[g->cur], sbytes, cudaMemcpyDeviceToDevice, g->stream));
+            st = run_steps<R>(g, std::min(K, nsteps - s * K), false);
+            if (st != PSTD_OK) return st;
+        }
+        g->ckpt_K = K;
+        g->ckpt_slots = (long)(g->adj_ckpt_cap / (2 * sbytes));
+        g->ckpt_upto = nsteps;
     }
+    char* ckpt = static_cast<char*>(g->adj_ckpt);
     // backward
     C* nu[2] = {static_cast<C*>(g->adj_nu), reinterpret_cast<C*>(static_cast<char*>(g->adj_nu) + sbytes)};
     int nc = 0;   // nu[nc] = nu^{n+1} (current), nu[nc ^ 1] = nu^{n+2} (previous)
@@ -1074,6 +1102,7 @@ pstd_status run_adjoint(pstd_grid* g, long nsteps, const double2* gph, const int
     CK(g, cudaMemsetAsync(g->buf[1], 0, sbytes, g->stream));
     g->n = 0;
     g->cur = 0;
+    g->ckpt_contig = true;
     return PSTD_OK;
 }
 
@@ -1242,6 +1271,7 @@ pstd_status pstd_reset(pstd_grid* g)
     }
     g->n = 0;
     g->cur = 0;
+    g->ckpt_contig = true;
     ++g->phasor_version;
     return PSTD_OK;
 }
@@ -1250,6 +1280,8 @@ pstd_status pstd_set_potential(pstd_grid* g, const void* V, int mem, int dtype)
 {
     if (!g || !V) return fail(g, PSTD_EINVAL, "null argument");
     DeviceGuard dg(g->dev);
+    g->ckpt_upto = -1;        // recorded checkpoints belong to the previous potential
+    g->ckpt_contig = false;
     if (dtype != PSTD_DTYPE_F32 && dtype != PSTD_DTYPE_F64) return fail(g, PSTD_EINVAL, "dtype");
     const pstd_grid_desc& d = g->desc;
     const size_t n = (size_t)g->ncell;
@@ -1314,6 +1346,8 @@ pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double
 {
     if (!g || !khat) return fail(g, PSTD_EINVAL, "null argument");
     DeviceGuard dg(g->dev);
+    g->ckpt_upto = -1;        // recorded checkpoints belong to the previous incidence
+    g->ckpt_contig = false;
     pstd_status st = check_member(g, b);
     if (st != PSTD_OK) return st;
     if (envelope != PSTD_ENV_CW_RAMP) return fail(g, PSTD_EINVAL, "envelope");
@@ -1560,6 +1594,7 @@ pstd_status pstd_set_field(pstd_grid* g, int b, const void* prev, const void* cu
     st = copy_in(g, static_cast<char*>(g->buf[g->cur ^ 1]) + (size_t)b * bytes, prev, bytes, mem);
     if (st != PSTD_OK) return st;
     g->n = n;
+    g->ckpt_contig = false;   // no longer the run from rest
     ++g->phasor_version;
     if (mem == PSTD_MEM_HOST) CK(g, cudaStreamSynchronize(g->stream));
     return PSTD_OK;
@@ -1733,5 +1768,26 @@ pstd_status pstd_adjoint_gradient(pstd_grid* g, long nsteps, const void* dl_dpha
     if (st != PSTD_OK) return st;
     if (mem == PSTD_MEM_HOST) return copy_out(g, dl_dv, dst, sizeof(double) * box, PSTD_MEM_HOST);
     CK(g, cudaStreamSynchronize(g->stream));
+    return PSTD_OK;
+}
+
+pstd_status pstd_set_checkpointing(pstd_grid* g, long interval, long max_steps)
+{
+    if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
+    if (interval < 0 || max_steps < 0) return fail(g, PSTD_EINVAL, "interval / max_steps");
+    if (interval > 0 && g->batch != 1) return fail(g, PSTD_EINVAL, "checkpoints are recorded on grids with batch 1");
+    DeviceGuard dg(g->dev);
+    g->ckpt_upto = -1;
+    if (interval == 0) {
+        g->ckpt_record = false;
+        return PSTD_OK;
+    }
+    const size_t sbytes = (size_t)g->ncell * g->csize;
+    const long slots = std::max(1L, (max_steps + interval - 1) / interval);
+    pstd_status st = ensure(g, &g->adj_ckpt, g->adj_ckpt_cap, (size_t)slots * 2 * sbytes);
+    if (st != PSTD_OK) return st;
+    g->ckpt_record = true;
+    g->ckpt_K = interval;
+    g->ckpt_slots = (long)(g->adj_ckpt_cap / (2 * sbytes));
     return PSTD_OK;
 }

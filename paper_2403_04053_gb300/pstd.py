@@ -8,6 +8,7 @@ no CPU fallback: if the library is missing or fails to load, the import raises.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 from ctypes import POINTER, byref, c_double, c_int, c_long, c_void_p
 
@@ -67,6 +68,7 @@ _SIGS = {
     "pstd_last_error": (ctypes.c_char_p, [c_void_p]),
     "pstd_transform_adjoint": (c_int, [c_void_p, c_int, c_int, c_void_p, c_long, c_void_p, c_void_p, c_int]),
     "pstd_adjoint_gradient": (c_int, [c_void_p, c_long, c_void_p, POINTER(c_int), POINTER(c_int), c_long, c_void_p, c_int]),
+    "pstd_set_checkpointing": (c_int, [c_void_p, c_long, c_long]),
 }
 
 _lib = None
@@ -278,6 +280,10 @@ class Grid:
                 "pstd_transform_adjoint")
         return self.split_phasors(out)
 
+    def set_checkpointing(self, interval: int, max_steps: int):
+        """Record adjoint checkpoints during step() (pstd_set_checkpointing); interval 0 stops."""
+        self._c(self.lib.pstd_set_checkpointing(self.h, int(interval), int(max_steps)), "pstd_set_checkpointing")
+
     def adjoint_gradient(self, nsteps: int, dl_dphasors, box_lo, box_hi, checkpoint_interval: int = 0):
         """dL/dV on the node box [box_lo, box_hi) (x, y, z) as a [z, y, x] array
         (pstd_adjoint_gradient).  dl_dphasors: per frequency, six plane pairs or a flat
@@ -383,6 +389,9 @@ def _make_fresnel_function():
         @staticmethod
         def forward(ctx, V, grid, points, nsteps, box_lo, box_hi, checkpoint_interval):
             grid.set_potential(V.detach().contiguous())
+            # record the checkpoints the backward sweep needs during this run
+            K = checkpoint_interval if checkpoint_interval > 0 else int(math.ceil(math.sqrt(nsteps)))
+            grid.set_checkpointing(K, nsteps)
             grid.reset()
             grid.step(nsteps)
             psi = grid.transform_to_points(0, 0, points)

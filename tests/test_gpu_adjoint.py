@@ -128,6 +128,32 @@ def test_checkpoint_interval_does_not_change_the_gradient():
         assert rel(other, grads[0]) < 1e-13
 
 
+def test_recorded_checkpoints_give_the_same_gradient():
+    # checkpoints recorded by pstd_step replace the adjoint's own forward run; a new
+    # potential discards them
+    spec = small_spec("exact")
+    V1, V2 = core_V(spec, 7), core_V(spec, 8)
+    lo, hi = box_of(spec, "exact")
+    ref = {}
+    for name, V in (("V1", V1), ("V2", V2)):
+        g, psi, L, gpts = gpu_forward(spec, V, pstd.F64)
+        with g:
+            gph = g.transform_adjoint(0, 0, PTS, gpts)
+            ref[name] = (gph, g.adjoint_gradient(NSTEPS, [gph], lo, hi, 9))
+    with pstd.Grid(spec, precision=pstd.F64) as g:
+        g.set_potential(V1)
+        g.set_incidence(0, KHAT, K, 0.05)
+        g.huygens_dft(0, [E0], *WIN)
+        g.set_checkpointing(9, NSTEPS)
+        g.reset()
+        g.step(NSTEPS)
+        assert rel(g.adjoint_gradient(NSTEPS, [ref["V1"][0]], lo, hi, 9), ref["V1"][1]) < 1e-12
+        # the same record serves a second call; then a new potential must not reuse it
+        assert rel(g.adjoint_gradient(NSTEPS, [ref["V1"][0]], lo, hi, 9), ref["V1"][1]) < 1e-12
+        g.set_potential(V2)
+        assert rel(g.adjoint_gradient(NSTEPS, [ref["V2"][0]], lo, hi, 9), ref["V2"][1]) < 1e-12
+
+
 def test_autograd_function_matches_the_adjoint():
     torch = pytest.importorskip("torch")
     spec = small_spec("exact")
