@@ -254,6 +254,8 @@ def run_gpu(args):
     # adjoint leg: gradient of the Fresnel-plane |Psi| misfit with respect to V on the central
     # 48^3 block (128^3, FP32, 2000 steps, 128^2 points), timed against its forward run
     adjoint = None if args.skip_adjoint else adjoint_leg(pstd, inputs, stream, dev)
+    # batched leg: 16 incidences against one potential on a 256^3 grid (HBM-bound regime)
+    batched = None if args.skip_batched else batched_leg(pstd, inputs, stream, dev, flush)
 
     out = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
@@ -270,6 +272,7 @@ def run_gpu(args):
         "kernels": kernel_ms,
         "fp64": fp64,
         "adjoint": adjoint,
+        "batched": batched,
     }
     if rank == 0:
         out["clocks"] = clk.summary()
@@ -279,6 +282,52 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def batched_leg(pstd, inputs, stream, dev, flush):
+    """Cell-updates/s of the batched 256^3 x 16 configuration over 80 steps (the last 40 in
+    every member's DFT window), plus the HBM roofline of its dominant pass."""
+    import torch
+    wl = inputs.batched_workload()
+    spec = wl.spec
+    B = len(wl.incidences)
+    nsteps = 80
+    g = pstd.Grid(spec, precision=pstd.F32, batch=B, stream=stream.cuda_stream)
+    g.set_potential(torch.from_numpy(wl.V).to(dev))
+    for b, inc in enumerate(wl.incidences):
+        g.set_incidence(b, inc.khat, inc.k, inc.ramp_time)
+        g.huygens_dft(b, [spec.hbar * inc.k ** 2 / (2 * spec.mass)], 40, 40)
+    ncell = int(np.prod(spec.n))
+    times = []
+    for rep in range(3):   # the first repetition is a warm-up
+        g.reset()
+        flush.fill_(1.0)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        g.step(nsteps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        times.append(ev[0].elapsed_time(ev[1]) / 1e3)
+    t = statistics.median(times[1:])
+    g.reset()
+    g.set_timing(True)
+    g.step(nsteps)
+    ks = {name: g.kernel_stats(name) for name in ("xpass", "ypass", "zpass", "source")}
+    g.set_timing(False)
+    g.close()
+    top = max(("xpass", "ypass", "zpass"), key=lambda n: ks[n][1])
+    nl, ms = ks[top]
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    achieved = 24.0 * ncell * B / (ms / nl / 1e3) / 1e9
+    return {"workload": f"batched-256^3: {B} incidences (8 Fibonacci directions x k in {{2pi, pi}}) on one "
+                        "Gaussian-sum potential, FP32, 80 steps (40 in the DFT window)",
+            "value": B * ncell * nsteps / t, "unit": "cell-updates/s", "ms_per_step": t / nsteps * 1e3,
+            "state_bytes": 2 * B * ncell * 8,
+            "kernels_us": {n: round(v[1] / max(1, v[0]) * 1e3, 1) for n, v in ks.items()},
+            "roofline": {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "algorithmic_bytes_per_launch": 24 * ncell * B}}
 
 
 def adjoint_leg(pstd, inputs, stream, dev):
@@ -397,6 +446,7 @@ def main():
     p.add_argument("--skip-fp64", action="store_true")
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-adjoint", action="store_true")
+    p.add_argument("--skip-batched", action="store_true")
     args = p.parse_args()
     if args.impl == "reference":
         run_reference(args)

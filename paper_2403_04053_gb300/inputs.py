@@ -365,3 +365,37 @@ def adjoint_workload(n: int = 128, dx: float = 0.25, nsteps: int = 2000, seed: i
     D = (tf[1] - taper - (tf[0] + taper)) * dx
     wl.fresnel_points = plane_points(khat, D * D / (4 * (2 * math.pi / k)), 1.5 * D, fresnel_count)
     return wl, V_target
+
+
+def batched_workload(n: int = 256, dx: float = 0.25, nsteps: int = 3000, seed: int = 2408, abc: int = 24,
+                     tf=(40, 216), taper: int = 4, hb=(32, 224), directions: int = 8):
+    """Many incidences against one potential: one seeded Gaussian-sum potential (as in
+    gaussian_sum_workload, amplitudes relative to E at k = 2 pi) on an n^3 grid, and
+    `directions` Fibonacci-sphere directions x k in {2 pi, pi} (2 * directions members,
+    k = 2 pi first).  Each member's DFT window is the last three periods of its own carrier;
+    they are returned as wl.windows = [(first, len), ...] (wl.window_* hold member 0's).
+
+    The potential is evaluated on a 96^3 sub-box around the centre, which holds every
+    Gaussian down to the 1e-8 cut, and embedded: the same values as a whole-grid evaluation."""
+    k0 = 2 * math.pi
+    E = 0.5 * k0 * k0
+    spec = GridSpec(n=(n, n, n), d=(dx, dx, dx), dt=1.0, abc_cells=(abc,) * 3,
+                    tfsf_lo=(tf[0],) * 3, tfsf_hi=(tf[1],) * 3, taper_cells=taper,
+                    huygens_lo=(hb[0],) * 3, huygens_hi=(hb[1],) * 3)
+    m = 96
+    small = GridSpec(n=(m, m, m), d=(dx, dx, dx), dt=1.0, abc_cells=(1, 1, 1), tfsf_lo=(1, 1, 1),
+                     tfsf_hi=(m - 1, m - 1, m - 1), taper_cells=1, huygens_lo=(1, 1, 1), huygens_hi=(m - 1, m - 1, m - 1))
+    Vs = gaussian_sum_potential(small, E, seed)
+    V = np.zeros(spec.shape)
+    o = n // 2 - m // 2
+    V[o:o + m, o:o + m, o:o + m] = Vs
+    spec.dt = stable_dt(spec.n, spec.d, float(np.max(np.abs(V))))
+    incs, windows = [], []
+    for k in (k0, 0.5 * k0):
+        for d in fibonacci_directions(directions):
+            incs.append(Incidence(tuple(d), k, 0.5))
+            windows.append(dft_window(0.5 * k * k, spec.dt, nsteps))
+    wl = Workload(name=f"batched-{n}^3-x{len(incs)}", spec=spec, V=V, incidences=incs, nsteps=nsteps,
+                  window_first=windows[0][0], window_len=windows[0][1])
+    wl.windows = windows
+    return wl

@@ -378,3 +378,32 @@ def test_timing_and_launch_counts():
             n, ms = g.kernel_stats(name)
             assert n == 5 and ms > 0
         assert g.launch_count() == 15
+
+
+def test_batched_256_cube_matches_separate_runs():
+    # the batched configuration at full size: 16 incidences on one potential (256^3, FP32),
+    # 12 steps with every member's DFT window over steps 4..11; members 3 and 12 (k = 2 pi and
+    # k = pi) stepped in a batch of two with member 0 (whose energy sets the absorber) give the
+    # same state and phasors
+    wl = inputs.batched_workload()
+    spec = wl.spec
+    B = len(wl.incidences)
+
+    def setup(g, members):
+        g.set_potential(wl.V)
+        for b, i in enumerate(members):
+            inc = wl.incidences[i]
+            g.set_incidence(b, inc.khat, inc.k, inc.ramp_time)
+            g.huygens_dft(b, [0.5 * inc.k ** 2], 4, 8)
+
+    with pstd.Grid(spec, precision=pstd.F32, batch=B) as g:
+        setup(g, range(B))
+        g.step(12)
+        got = {i: (g.get_field(i), g.get_phasors(i, 0)) for i in (3, 12)}
+    for i in (3, 12):
+        with pstd.Grid(spec, precision=pstd.F32, batch=2) as g1:
+            setup(g1, [0, i])
+            g1.step(12)
+            assert rel(got[i][0], g1.get_field(1)) < 1e-6
+            for a, b in zip(got[i][1], g1.get_phasors(1, 0)):
+                assert rel(a[0], b[0]) < 1e-6 and rel(a[1], b[1]) < 1e-6
