@@ -284,19 +284,21 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def batched_leg(pstd, inputs, stream, dev, flush):
-    """Cell-updates/s of the batched 256^3 x 16 configuration over 80 steps (the last 40 in
-    every member's DFT window), plus the HBM roofline of its dominant pass."""
+def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80):
+    """Cell-updates/s of the batched 256^3 x 16 configuration over 80 steps (the last half in
+    every member's DFT window), plus the HBM roofline of its dominant pass.  `members` < 16
+    keeps only the first members (a smaller case of the same kernels, for profiling)."""
     import torch
     wl = inputs.batched_workload()
+    if members:
+        wl.incidences = wl.incidences[:members]
     spec = wl.spec
     B = len(wl.incidences)
-    nsteps = 80
     g = pstd.Grid(spec, precision=pstd.F32, batch=B, stream=stream.cuda_stream)
     g.set_potential(torch.from_numpy(wl.V).to(dev))
     for b, inc in enumerate(wl.incidences):
         g.set_incidence(b, inc.khat, inc.k, inc.ramp_time)
-        g.huygens_dft(b, [spec.hbar * inc.k ** 2 / (2 * spec.mass)], 40, 40)
+        g.huygens_dft(b, [spec.hbar * inc.k ** 2 / (2 * spec.mass)], nsteps // 2, nsteps - nsteps // 2)
     ncell = int(np.prod(spec.n))
     times = []
     for rep in range(3):   # the first repetition is a warm-up
@@ -322,7 +324,7 @@ def batched_leg(pstd, inputs, stream, dev, flush):
     hbm = pk.get("hbm_gbs", 6800.0)
     achieved = 24.0 * ncell * B / (ms / nl / 1e3) / 1e9
     return {"workload": f"batched-256^3: {B} incidences (8 Fibonacci directions x k in {{2pi, pi}}) on one "
-                        "Gaussian-sum potential, FP32, 80 steps (40 in the DFT window)",
+                        f"Gaussian-sum potential, FP32, {nsteps} steps ({nsteps - nsteps // 2} in the DFT window)",
             "value": B * ncell * nsteps / t, "unit": "cell-updates/s", "ms_per_step": t / nsteps * 1e3,
             "state_bytes": 2 * B * ncell * 8,
             "kernels_us": {n: round(v[1] / max(1, v[0]) * 1e3, 1) for n, v in ks.items()},
@@ -447,9 +449,20 @@ def main():
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-adjoint", action="store_true")
     p.add_argument("--skip-batched", action="store_true")
+    p.add_argument("--batched-only", action="store_true",
+                   help="run only the batched leg (with --batched-members / --batched-steps) and print it")
+    p.add_argument("--batched-members", type=int, default=0)
+    p.add_argument("--batched-steps", type=int, default=80)
     args = p.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.batched_only:
+        import torch
+        from paper_2403_04053_gb300 import inputs, pstd
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        print(json.dumps(batched_leg(pstd, inputs, torch.cuda.current_stream(), dev, flush,
+                                     args.batched_members or None, args.batched_steps)), flush=True)
     else:
         run_gpu(args)
 

@@ -849,7 +849,7 @@ pstd_status run_transform(pstd_grid* g, int b, int f, const double* pts, long M,
     a.M = M;
     a.k = g->mem[b].k;
     for (int q = 0; q < g->G; ++q) a.gl_node[q] = g->gl_x[q];
-    const long long per_block = 128;
+    const long long per_block = 128 * PSTD_TRANSFORM_PT;
     const long long blocks = (M + per_block - 1) / per_block;
     const int CH = sizeof(R) == 4 ? 32 : 16;
     const long long chunks = (g->ncells + CH - 1) / CH;

@@ -61,7 +61,7 @@ template <typename R> __device__ __forceinline__ void sincos_mid(R x, R* s, R* c
 }
 
 constexpr int kTransformThreads = 128;
-constexpr int kTransformPT = 1;   // one point per thread keeps registers low enough for 7 resident CTAs
+constexpr int kTransformPT = PSTD_TRANSFORM_PT;
 
 // Cell records hold, for psi and for d psi/d a, the node values (quadrature weights and
 // cell Jacobian folded in) regrouped over the mirrored Gauss-Legendre nodes

@@ -137,6 +137,11 @@ template <typename R> struct TransformArgs {
     double2* partial;         // [split][M]
 };
 
+// points per thread of the surface transform (CTAs of 128 threads): two points share each
+// cell record read from shared memory
+#ifndef PSTD_TRANSFORM_PT
+#define PSTD_TRANSFORM_PT 2
+#endif
 template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, int G, int splits, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------

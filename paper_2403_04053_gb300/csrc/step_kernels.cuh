@@ -32,11 +32,16 @@ template <typename R, typename C> __device__ __forceinline__ C zero_c() { return
 #define PSTD_PREFETCH_PREV 0
 #endif
 
-// Minimum resident CTAs per SM requested from the register allocator: 4 CTAs of 256
-// threads (64 registers each) let the 512 CTAs of a 128^3 pass run in one wave on 152 SMs.
+// Minimum resident CTAs per SM requested from the register allocator (64 registers a
+// thread, 2048 threads an SM): 4 CTAs of 256 threads let the 512 CTAs of a 128^3 pass run
+// in one wave on 152 SMs; for the 512-thread CTAs of N = 192 and 256 (at most 16 values a
+// thread) 2 CTAs, so that HBM-bound passes keep enough loads in flight.
 template <typename R, int N> constexpr int pass_min_blocks()
 {
-    return (sizeof(R) == 4 && Plan<N>::T <= 8) ? (PSTD_PREFETCH_PREV ? 2 : 4) * (32 / kLanes) : 1;
+    return !(sizeof(R) == 4) ? 1
+           : Plan<N>::T <= 8 ? (PSTD_PREFETCH_PREV ? 2 : 4) * (32 / kLanes)
+           : (Plan<N>::T == 16 && N / Plan<N>::T <= 16) ? 2 * (32 / kLanes)
+           : 1;
 }
 
 template <typename R> __device__ __forceinline__ bool finite_c(R a, R b) { return isfinite(a) && isfinite(b); }
