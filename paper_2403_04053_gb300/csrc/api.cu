@@ -524,17 +524,17 @@ template <typename R>
 pstd_status enqueue_step(pstd_grid* g, const StepArgs<R>& a, unsigned long long mask, const DftArgs<R>* dx,
                          const DftArgs<R>* dy, const DftArgs<R>* dz, bool need_src)
 {
-    // the V-term and source: folded into the z pass on steps without the DFT, their own
-    // kernel on DFT steps
-    const bool src_in_z = need_src && !mask;
+    // the V-term and source: folded into the z pass when x and y run fused; their own kernel
+    // ahead of the separate x and y passes otherwise (where the DFT variants are heavier)
+    const bool src_in_z = need_src && (g->use_xy || !mask);
     if (need_src && !src_in_z) {
         Timer t(g, 7);
         CK(g, launch_source<R>(a, g->batch, g->stream));
     }
-    if (!mask && g->use_xy) {
-        // no plane DFT this step: x and y together, one CTA per z plane
+    if (g->use_xy) {
+        // x and y together, one CTA per z plane (with the x and y plane DFT on window steps)
         Timer t(g, 3);
-        CK(g, launch_xypass<R>(a, g->batch, g->stream));
+        CK(g, launch_xypass<R>(a, mask ? dx : nullptr, mask ? dy : nullptr, g->batch, g->stream));
     } else {
         {
             Timer t(g, 0);

@@ -8,7 +8,7 @@ template cudaError_t launch_ypass<float>(const StepArgs<float>&, const DftArgs<f
 template cudaError_t launch_zpass<float>(const StepArgs<float>&, const DftArgs<float>*, bool, int, cudaStream_t);
 template cudaError_t launch_source<float>(const StepArgs<float>&, int, cudaStream_t);
 template bool xypass_available<float>(int, int);
-template cudaError_t launch_xypass<float>(const StepArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_xypass<float>(const StepArgs<float>&, const DftArgs<float>*, const DftArgs<float>*, int, cudaStream_t);
 template cudaError_t launch_transform<float>(const TransformArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_farfield<float>(const FarArgs<float>&, cudaStream_t);
 template cudaError_t launch_spectrum_pack<float>(const float2*, const float2*, int, int, double, float2*, cudaStream_t);

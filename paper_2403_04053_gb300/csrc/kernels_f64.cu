@@ -8,7 +8,7 @@ template cudaError_t launch_ypass<double>(const StepArgs<double>&, const DftArgs
 template cudaError_t launch_zpass<double>(const StepArgs<double>&, const DftArgs<double>*, bool, int, cudaStream_t);
 template cudaError_t launch_source<double>(const StepArgs<double>&, int, cudaStream_t);
 template bool xypass_available<double>(int, int);
-template cudaError_t launch_xypass<double>(const StepArgs<double>&, int, cudaStream_t);
+template cudaError_t launch_xypass<double>(const StepArgs<double>&, const DftArgs<double>*, const DftArgs<double>*, int, cudaStream_t);
 template cudaError_t launch_transform<double>(const TransformArgs<double>&, int, int, cudaStream_t);
 template cudaError_t launch_farfield<double>(const FarArgs<double>&, cudaStream_t);
 template cudaError_t launch_spectrum_pack<double>(const double2*, const double2*, int, int, double, double2*, cudaStream_t);

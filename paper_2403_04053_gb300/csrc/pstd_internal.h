@@ -79,12 +79,13 @@ template <typename R> struct DftArgs {
 // virtual planes normal to its axis (d->axis must match the pass)
 template <typename R> cudaError_t launch_xpass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s);
-// src: also add the V-term and source in the z-pass epilogue (steps without the DFT only)
+// src: also add the V-term and source in the z-pass epilogue
 template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, bool src, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch, cudaStream_t s);
 // fused x + y pass (one CTA per z plane); available for FP32 square planes of 64, 96, 128
 template <typename R> bool xypass_available(int nx, int ny);
-template <typename R> cudaError_t launch_xypass(const StepArgs<R>& a, int batch, cudaStream_t s);
+template <typename R>
+cudaError_t launch_xypass(const StepArgs<R>& a, const DftArgs<R>* dx, const DftArgs<R>* dy, int batch, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------
 // surface-equivalence transform

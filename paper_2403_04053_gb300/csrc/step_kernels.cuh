@@ -272,8 +272,27 @@ template <typename R, int N> constexpr bool xy_supported()
            (size_t)N * (N + 1) * 8 <= 227 * 1024;
 }
 
-template <typename R, int N>
-__global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid_constant__ StepArgs<R> a)
+// On DFT-window steps (DFT = true) the pass also forms the running DFT of the planes normal
+// to x and to y: for the x planes each warp reads whole rows of the z plane (coalesced) and
+// reduces D_h(x) psi(x, y) over x with shuffles; for the y planes the raw column values of
+// step 1 give the partial sums, reduced over the T threads of a column in shared memory
+// placed after the plane.
+template <int N> constexpr size_t xy_dft_red_elems() { return (size_t)4 * Plan<N>::T * N; }
+
+template <typename R, typename C> __device__ __forceinline__ C warp_sum(C v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
+
+template <typename R, int N, bool DFT>
+__global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid_constant__ StepArgs<R> a,
+                                                                      const __grid_constant__ DftArgs<R> dx,
+                                                                      const __grid_constant__ DftArgs<R> dy)
 {
     step_kernel_entry();
     using C = typename StepArgs<R>::C;
@@ -292,9 +311,40 @@ __global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid
     const C* __restrict__ twx = a.tw[0];
     const C* __restrict__ twy = a.tw[1];
     C v[E];
+    const bool dft = DFT && ((dx.member_mask >> b) & 1ull);
+    if (dft) {
+        // x planes: row y of this z plane, lanes over x
+        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        const double2* efx = dx.phase + (long long)b * dx.phase_member_stride + (dx.step - dx.window_first[b]);
+        for (int y = warp; y < N; y += nwarps) {
+            const C* row = a.cur + pbase + (long long)y * N;
+            C d0 = zero_c<R, C>(), d1 = zero_c<R, C>(), p0 = zero_c<R, C>(), p1 = zero_c<R, C>();
+#pragma unroll
+            for (int k = 0; k < N / 32; ++k) {
+                const int xx = lane + 32 * k;
+                const C u = row[xx];
+                d0 = cadd(d0, cmul(u, dx.dw[xx]));
+                d1 = cadd(d1, cmul(u, dx.dw[N + xx]));
+                if (xx == dx.h[0]) p0 = u;
+                if (xx == dx.h[1]) p1 = u;
+            }
+            d0 = warp_sum<R, C>(d0);
+            d1 = warp_sum<R, C>(d1);
+            p0 = warp_sum<R, C>(p0);
+            p1 = warp_sum<R, C>(p1);
+            if (lane == 0) dft_accumulate<R>(dx, b, (long long)z * N + y, efx, dx.mem[b].nfreq, p0, p1, d0, d1);   // plane [z][y]
+        }
+    }
     // 1. forward along y
 #pragma unroll
     for (int q = 0; q < E; ++q) v[q] = cur[slot_pos<N, T, R0>(q, j) * N];
+    if (dft) {
+        // y planes from the raw column values
+        C part[4];
+        dft_partials<N, T, R0>(v, j, dy.dw, dy.h[0], dy.h[1], part);
+        C* red = sm + (size_t)N * P + (size_t)grp * 4 * T * 32;
+        dft_finish<R, T>(part, red, lane, j, dy, b, (long long)z * N + x, true);   // plane [z][x]
+    }
     stockham_stage<N, T, R0, 1, -1, false, true, P, 1>(v, smc, lane, j, twy);
     stockham_stage<N, T, R1, R0, -1, true, false, P, 1>(v, smc, lane, j, twy);
     __syncthreads();
@@ -502,24 +552,34 @@ template <typename R, int N>
 cudaError_t zpass_n(const StepArgs<R>& a, const DftArgs<R>* d, bool src, int batch, cudaStream_t s)
 {
     const size_t sm = pass_smem<R, N>();
-    cudaError_t e = d ? set_smem_once<zpass_kernel<R, N, true, false>>(sm)
+    cudaError_t e = d ? (src ? set_smem_once<zpass_kernel<R, N, true, true>>(sm) : set_smem_once<zpass_kernel<R, N, true, false>>(sm))
                       : src ? set_smem_once<zpass_kernel<R, N, false, true>>(sm) : set_smem_once<zpass_kernel<R, N, false, false>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + kLanes - 1) / kLanes, a.ny, batch);
     const DftArgs<R> none{};
+    if (d && src) return launch_step_kernel(zpass_kernel<R, N, true, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
     if (d) return launch_step_kernel(zpass_kernel<R, N, true, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
     if (src) return launch_step_kernel(zpass_kernel<R, N, false, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
     return launch_step_kernel(zpass_kernel<R, N, false, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
 }
 
-template <typename R, int N> cudaError_t xypass_n(const StepArgs<R>& a, int batch, cudaStream_t s)
+template <typename R, int N>
+cudaError_t xypass_n(const StepArgs<R>& a, const DftArgs<R>* dx, const DftArgs<R>* dy, int batch, cudaStream_t s)
 {
     if constexpr (xy_supported<R, N>()) {
-        const size_t sm = sizeof(typename StepArgs<R>::C) * (size_t)N * (N + 1);
-        cudaError_t e = set_smem_once<xypass_kernel<R, N>>(sm);
-        if (e != cudaSuccess) return e;
+        using C = typename StepArgs<R>::C;
         const dim3 grid(a.nz, batch);
-        return launch_step_kernel(xypass_kernel<R, N>, grid, dim3(xy_threads<N>()), sm, s, a);
+        if (dx && dy) {
+            const size_t sm = sizeof(C) * ((size_t)N * (N + 1) + xy_dft_red_elems<N>());
+            cudaError_t e = set_smem_once<xypass_kernel<R, N, true>>(sm);
+            if (e != cudaSuccess) return e;
+            return launch_step_kernel(xypass_kernel<R, N, true>, grid, dim3(xy_threads<N>()), sm, s, a, *dx, *dy);
+        }
+        const size_t sm = sizeof(C) * (size_t)N * (N + 1);
+        cudaError_t e = set_smem_once<xypass_kernel<R, N, false>>(sm);
+        if (e != cudaSuccess) return e;
+        const DftArgs<R> none{};
+        return launch_step_kernel(xypass_kernel<R, N, false>, grid, dim3(xy_threads<N>()), sm, s, a, none, none);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -553,7 +613,6 @@ template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, const DftAr
 template <typename R>
 cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, bool src, int batch, cudaStream_t s)
 {
-    if (d && src) return cudaErrorInvalidValue;   // DFT steps run the source kernel instead
     PSTD_SIZE_DISPATCH(zpass_n, a.nz, a, d, src, batch, s)
 }
 // fused xy pass: FP32, square planes of 64, 96 or 128 (one CTA per plane)
@@ -561,13 +620,14 @@ template <typename R> bool xypass_available(int nx, int ny)
 {
     return sizeof(R) == 4 && nx == ny && (nx == 64 || nx == 96 || nx == 128);
 }
-template <typename R> cudaError_t launch_xypass(const StepArgs<R>& a, int batch, cudaStream_t s)
+template <typename R>
+cudaError_t launch_xypass(const StepArgs<R>& a, const DftArgs<R>* dx, const DftArgs<R>* dy, int batch, cudaStream_t s)
 {
     if (!xypass_available<R>(a.nx, a.ny)) return cudaErrorInvalidValue;
     switch (a.nx) {
-    case 64: return xypass_n<R, 64>(a, batch, s);
-    case 96: return xypass_n<R, 96>(a, batch, s);
-    case 128: return xypass_n<R, 128>(a, batch, s);
+    case 64: return xypass_n<R, 64>(a, dx, dy, batch, s);
+    case 96: return xypass_n<R, 96>(a, dx, dy, batch, s);
+    case 128: return xypass_n<R, 128>(a, dx, dy, batch, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -212,6 +212,31 @@ def test_128_cubed_one_step_elementwise(big, prec, tol):
     assert np.max(np.abs(got - sim.cur)) < 20 * tol * np.max(np.abs(sim.cur))
 
 
+@pytest.fixture(scope="module")
+def big_short_run(big):
+    wl = big
+    inc = wl.incidences[0]
+    sim = po.Simulation(wl.spec, wl.V, inc.khat, inc.k, 0.05, window=(20, 30), omegas=[K * K / 2])
+    sim.step(50)
+    return sim
+
+
+@pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-11), (pstd.F32, 2e-5)])
+def test_128_cubed_short_run_state_and_phasors(big, big_short_run, prec, tol):
+    # 50 steps, the last 30 in the DFT window: the state and the six plane phasors (FP32: the
+    # fused x+y pass with its plane DFT, and the z pass with DFT and source)
+    wl, sim = big, big_short_run
+    inc = wl.incidences[0]
+    with pstd.Grid(wl.spec, precision=prec) as g:
+        g.set_potential(wl.V)
+        g.set_incidence(0, inc.khat, inc.k, 0.05)
+        g.huygens_dft(0, [K * K / 2], 20, 30)
+        g.step(50)
+        assert rel(g.get_field(0), sim.cur) < tol
+        for a, b in zip(g.get_phasors(0, 0), sim.scaled_phasors(0)):
+            assert rel(a[0], b[0]) < tol and rel(a[1], b[1]) < tol
+
+
 @pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-10), (pstd.F32, 1e-4)])
 def test_128_cubed_sampled_transform(big, prec, tol):
     """Phasors from a short 128^3 run; the surface transform at sampled Fresnel-plane points and
@@ -345,27 +370,28 @@ def test_call_order_errors():
         assert e.value.code == "EINVAL"
 
 
-def test_fused_xy_pass_outside_the_dft_window():
-    # 64^2 planes in FP32: the fused x+y pass runs on the steps outside the DFT window and
-    # the separate x and y passes (which also accumulate the DFT) inside it
+def test_fused_xy_pass_with_and_without_the_dft():
+    # 64^2 planes in FP32: the fused x+y pass runs on every step, with the x- and y-plane DFT
+    # on the window steps, and the z pass carries the V-term and source throughout
     spec = ONE_STEP_SPECS["square-64x64x48"]("exact")
     V = random_core_V(spec, 4)
     khat, win = (0.3, -0.5, 0.81), (10, 10)
-    sim = po.Simulation(spec, V, khat, K, 0.05, window=win, omegas=[E0])
+    sim = po.Simulation(spec, V, khat, K, 0.05, window=win, omegas=[E0, 0.9 * E0])
     sim.step(30)
     with pstd.Grid(spec, precision=pstd.F32) as g:
         g.set_potential(V)
         g.set_incidence(0, khat, K, 0.05)
-        g.huygens_dft(0, [E0], *win)
+        g.huygens_dft(0, [E0, 0.9 * E0], *win)
         g.set_timing(True)
         g.step(30)
-        assert g.kernel_stats("xypass")[0] == 20
-        assert g.kernel_stats("xpass")[0] == 10 and g.kernel_stats("ypass")[0] == 10
-        assert g.kernel_stats("zpass")[0] == 30
+        assert g.kernel_stats("xypass")[0] == 30
+        assert g.kernel_stats("xpass")[0] == 0 and g.kernel_stats("ypass")[0] == 0
+        assert g.kernel_stats("zpass")[0] == 30 and g.kernel_stats("source")[0] == 0
         assert rel(g.get_field(0), sim.cur) < 2e-5
-        ph, ref = g.get_phasors(0, 0), sim.scaled_phasors(0)
-        for a, b in zip(ph, ref):
-            assert rel(a[0], b[0]) < 2e-5 and rel(a[1], b[1]) < 2e-5
+        for f in range(2):
+            ph, ref = g.get_phasors(0, f), sim.scaled_phasors(f)
+            for a, b in zip(ph, ref):
+                assert rel(a[0], b[0]) < 2e-5 and rel(a[1], b[1]) < 2e-5
 
 
 def test_timing_and_launch_counts():
