@@ -233,8 +233,13 @@ def test_128_cubed_short_run_state_and_phasors(big, big_short_run, prec, tol):
         g.huygens_dft(0, [K * K / 2], 20, 30)
         g.step(50)
         assert rel(g.get_field(0), sim.cur) < tol
-        for a, b in zip(g.get_phasors(0, 0), sim.scaled_phasors(0)):
-            assert rel(a[0], b[0]) < tol and rel(a[1], b[1]) < tol
+        got, ref = g.get_phasors(0, 0), sim.scaled_phasors(0)
+    # jointly over the six planes: after 50 steps some planes have barely been reached and
+    # hold values near the round-off floor of the state
+    for q in range(2):
+        a = np.concatenate([p[q].ravel() for p in got])
+        b = np.concatenate([p[q].ravel() for p in ref])
+        assert rel(a, b) < tol
 
 
 @pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-10), (pstd.F32, 1e-4)])
