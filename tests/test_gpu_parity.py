@@ -234,12 +234,11 @@ def test_128_cubed_short_run_state_and_phasors(big, big_short_run, prec, tol):
         g.step(50)
         assert rel(g.get_field(0), sim.cur) < tol
         got, ref = g.get_phasors(0, 0), sim.scaled_phasors(0)
-    # jointly over the six planes: after 50 steps some planes have barely been reached and
-    # hold values near the round-off floor of the state
-    for q in range(2):
-        a = np.concatenate([p[q].ravel() for p in got])
-        b = np.concatenate([p[q].ravel() for p in ref])
-        assert rel(a, b) < tol
+    # after 50 steps the scattered wave has not reached the Huygens planes (their values sit at
+    # the round-off floor), so the phasors are compared on the scale of the state itself
+    scale = np.max(np.abs(sim.cur))
+    for a, b in zip(got, ref):
+        assert np.max(np.abs(a[0] - b[0])) < tol * scale and np.max(np.abs(a[1] - b[1])) < tol * scale * K
 
 
 @pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-10), (pstd.F32, 1e-4)])
