@@ -138,25 +138,38 @@ __device__ __forceinline__ void dft_partials(const C (&v)[E], int j, const C* __
     }
 }
 
-// reduce the partials of the T threads of each line (lane) through `red` (>= 4 T 32 complex)
-// and accumulate.  Every thread of the CTA must call this (it synchronises).
+// Reduce the partials of the T threads of each line (lane) through `red` (>= 4 T 32 complex)
+// and accumulate.  dft_stage stores this thread's partials; after a barrier, dft_commit sums
+// a line's T partials and adds them to the double-precision accumulators.  A pass whose `red`
+// is not reused commits at its very end, so that no thread waits on the accumulators'
+// read-modify-write; dft_finish does both with barriers, for passes that reuse `red`.
+template <int T, typename C>
+__device__ __forceinline__ void dft_stage(const C (&part)[4], C* red, int lane, int j)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) red[(k * T + j) * kLanes + lane] = part[k];
+}
+
+template <typename R, int T, typename C>
+__device__ __forceinline__ void dft_commit(const C* red, int lane, const DftArgs<R>& d, int b, long long pix)
+{
+    C tot[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        tot[k] = red[(k * T) * kLanes + lane];
+        for (int t = 1; t < T; ++t) tot[k] = cadd(tot[k], red[(k * T + t) * kLanes + lane]);
+    }
+    const double2* ef = d.phase + (long long)b * d.phase_member_stride + (d.step - d.window_first[b]);
+    dft_accumulate<R>(d, b, pix, ef, d.mem[b].nfreq, tot[2], tot[3], tot[0], tot[1]);
+}
+
 template <typename R, int T, typename C>
 __device__ __forceinline__ void dft_finish(const C (&part)[4], C* red, int lane, int j, const DftArgs<R>& d, int b,
                                            long long pix, bool act)
 {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) red[(k * T + j) * kLanes + lane] = part[k];
+    dft_stage<T>(part, red, lane, j);
     __syncthreads();
-    if (j == 0 && act) {
-        C tot[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            tot[k] = red[(k * T) * kLanes + lane];
-            for (int t = 1; t < T; ++t) tot[k] = cadd(tot[k], red[(k * T + t) * kLanes + lane]);
-        }
-        const double2* ef = d.phase + (long long)b * d.phase_member_stride + (d.step - d.window_first[b]);
-        dft_accumulate<R>(d, b, pix, ef, d.mem[b].nfreq, tot[2], tot[3], tot[0], tot[1]);
-    }
+    if (j == 0 && act) dft_commit<R, T>(red, lane, d, b, pix);
     __syncthreads();
 }
 
@@ -236,8 +249,9 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     const R eta = R(a.mem[b].eta);
     kinetic_line<N, false>(v, sm, lane, j, a.tw[1], a.kin[1], eta);
     if (dft) {
+        __syncthreads();   // the exchange tile is free again
+        dft_stage<T>(part, sm, lane, j);
         __syncthreads();
-        dft_finish<R, T>(part, sm, lane, j, d, b, (long long)z * a.nx + x, act);   // plane [z][x]
     }
     if (!act) return;
 #pragma unroll
@@ -250,6 +264,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 #endif
         a.prev[idx] = mk<C>(p.x + v[q].y, p.y - v[q].x);
     }
+    if (dft && j == 0) dft_commit<R, T>(sm, lane, d, b, (long long)z * a.nx + x);   // plane [z][x]
 }
 
 // ---------------------------------------------------------------------------------
@@ -277,7 +292,7 @@ template <typename R, int N> constexpr bool xy_supported()
 // reduces D_h(x) psi(x, y) over x with shuffles; for the y planes the raw column values of
 // step 1 give the partial sums, reduced over the T threads of a column in shared memory
 // placed after the plane.
-template <int N> constexpr size_t xy_dft_red_elems() { return (size_t)4 * Plan<N>::T * N; }
+template <int N> constexpr size_t xy_dft_red_elems() { return (size_t)4 * Plan<N>::T * N + (size_t)4 * N; }
 
 template <typename R, typename C> __device__ __forceinline__ C warp_sum(C v)
 {
@@ -312,10 +327,12 @@ __global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid
     const C* __restrict__ twy = a.tw[1];
     C v[E];
     const bool dft = DFT && ((dx.member_mask >> b) & 1ull);
+    // DFT scratch after the plane: y-plane partials [group][4][T][32], then x-plane sums [N][4]
+    C* red_y = sm + (size_t)N * P;
+    C* sum_x = red_y + (size_t)4 * T * N;
     if (dft) {
         // x planes: row y of this z plane, lanes over x
         const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-        const double2* efx = dx.phase + (long long)b * dx.phase_member_stride + (dx.step - dx.window_first[b]);
         for (int y = warp; y < N; y += nwarps) {
             const C* row = a.cur + pbase + (long long)y * N;
             C d0 = zero_c<R, C>(), d1 = zero_c<R, C>(), p0 = zero_c<R, C>(), p1 = zero_c<R, C>();
@@ -332,18 +349,23 @@ __global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid
             d1 = warp_sum<R, C>(d1);
             p0 = warp_sum<R, C>(p0);
             p1 = warp_sum<R, C>(p1);
-            if (lane == 0) dft_accumulate<R>(dx, b, (long long)z * N + y, efx, dx.mem[b].nfreq, p0, p1, d0, d1);   // plane [z][y]
+            if (lane == 0) {
+                sum_x[4 * y + 0] = d0;
+                sum_x[4 * y + 1] = d1;
+                sum_x[4 * y + 2] = p0;
+                sum_x[4 * y + 3] = p1;
+            }
         }
     }
     // 1. forward along y
 #pragma unroll
     for (int q = 0; q < E; ++q) v[q] = cur[slot_pos<N, T, R0>(q, j) * N];
     if (dft) {
-        // y planes from the raw column values
+        // y planes from the raw column values (the barriers of the FFT stages below order
+        // these stores before the commit at the end)
         C part[4];
         dft_partials<N, T, R0>(v, j, dy.dw, dy.h[0], dy.h[1], part);
-        C* red = sm + (size_t)N * P + (size_t)grp * 4 * T * 32;
-        dft_finish<R, T>(part, red, lane, j, dy, b, (long long)z * N + x, true);   // plane [z][x]
+        dft_stage<T>(part, red_y + (size_t)grp * 4 * T * 32, lane, j);
     }
     stockham_stage<N, T, R0, 1, -1, false, true, P, 1>(v, smc, lane, j, twy);
     stockham_stage<N, T, R1, R0, -1, true, false, P, 1>(v, smc, lane, j, twy);
@@ -375,6 +397,14 @@ __global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid
         const int off = slot_pos<N, T, R0>(q, j) * N;
         const C p = prev[off];
         prev[off] = mk<C>(p.x + v[q].y, p.y - v[q].x);
+    }
+    if (dft && threadIdx.x < N) {
+        // commit: thread t adds row t's x-plane sums and column t's y-plane sums
+        const int t = threadIdx.x;
+        const double2* efx = dx.phase + (long long)b * dx.phase_member_stride + (dx.step - dx.window_first[b]);
+        dft_accumulate<R>(dx, b, (long long)z * N + t, efx, dx.mem[b].nfreq, sum_x[4 * t + 2], sum_x[4 * t + 3],
+                          sum_x[4 * t + 0], sum_x[4 * t + 1]);                       // plane [z][y]
+        dft_commit<R, T>(red_y + (size_t)(t / 32) * 4 * T * 32, t % 32, dy, b, (long long)z * N + t);   // plane [z][x]
     }
 }
 
@@ -475,8 +505,9 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
     kinetic_line<N, false>(v, sm, lane, j, a.tw[2], a.kin[2], R(a.mem[b].eta));
     if (dft) {
+        __syncthreads();   // the exchange tile is free again
+        dft_stage<T>(part, sm, lane, j);
         __syncthreads();
-        dft_finish<R, T>(part, sm, lane, j, d, b, (long long)y * a.nx + x, act);   // plane [y][x]
     }
     if (!act) return;
     const R gxy = a.mask[0][x] * a.mask[1][y];
@@ -507,6 +538,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
         a.prev[idx] = acc;
     }
     if (!ok) atomicOr(a.flag, 1);
+    if (dft && j == 0) dft_commit<R, T>(sm, lane, d, b, (long long)y * a.nx + x);   // plane [y][x]
 }
 
 // ---------------------------------------------------------------------------------
