@@ -17,6 +17,7 @@
 // is tabulated in double precision on the host for the steps of each pstd_step call.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
 
 #include "fft_line.cuh"
@@ -542,6 +543,135 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 }
 
 // ---------------------------------------------------------------------------------
+// pipelined y and z passes for large planes (FP32, N = 192 or 256, steps without the
+// DFT): a persistent CTA per SM walks its tiles of kLanes lines; while it transforms one
+// tile, cp.async stages the next tile's psi^n values, and during the transform of the next
+// the partial level it will update, into shared memory (each thread stages and later reads
+// back only its own values, so cp.async.wait_group orders them and no barrier is needed).
+// Stores of the updated level are fire-and-forget.  HBM sees the loads of one tile while
+// the SM computes another, instead of each CTA alternating between the two.
+// ---------------------------------------------------------------------------------
+template <typename R, int N> constexpr bool pipe_supported()
+{
+    return sizeof(R) == 4 && Plan<N>::T == 16 && N / Plan<N>::T <= 16 &&
+           sizeof(float2) * ((size_t)N * kPitch + 2 * (size_t)N * kLanes) <= 227 * 1024;
+}
+template <typename R, int N> constexpr size_t pipe_smem()
+{
+    return sizeof(typename StepArgs<R>::C) * ((size_t)N * kPitch + 2 * (size_t)N * kLanes);
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING> __device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+// AXIS 1: lines along y (tile = x block, z plane); AXIS 2: lines along z (tile = x block, y row)
+template <typename R, int N, int AXIS, bool SRC>
+__global__ void __launch_bounds__(kLanes * Plan<N>::T, 1) colpass_pipe_kernel(const __grid_constant__ StepArgs<R> a)
+{
+    step_kernel_entry();
+    using C = typename StepArgs<R>::C;
+    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C* sm = reinterpret_cast<C*>(smraw);            // FFT exchange tile [N][kPitch]
+    C* cst = sm + (size_t)N * kPitch;               // staged psi^n      [N][kLanes]
+    C* pst = cst + (size_t)N * kLanes;              // staged partial    [N][kLanes]
+    const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
+    const int xtiles = (a.nx + kLanes - 1) / kLanes;
+    const int other = AXIS == 1 ? a.nz : a.ny;
+    const long long ntiles = (long long)xtiles * other * a.batch;
+    const long long stride = AXIS == 1 ? (long long)a.nx : (long long)a.nx * a.ny;
+    const C* __restrict__ tw = a.tw[AXIS];
+    const R* __restrict__ kin = a.kin[AXIS];
+    // tile t -> member b, in-plane index o, column x of this thread, base index
+    auto decode = [&](long long t, int& b, int& o, int& x) -> long long {
+        const int xt = (int)(t % xtiles);
+        const long long r = t / xtiles;
+        o = (int)(r % other);
+        b = (int)(r / other);
+        x = xt * kLanes + lane;
+        return (long long)b * a.ncell + (AXIS == 1 ? (long long)o * a.nx * a.ny : (long long)o * a.nx) + x;
+    };
+    auto stage = [&](C* buf, const C* src, long long t) {
+        int b, o, x;
+        const long long base = decode(t, b, o, x);
+        if (x < a.nx) {
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                const int pos = slot_pos<N, T, R0>(q, j);
+                cp_async8(&buf[pos * kLanes + lane], src + base + pos * stride);
+            }
+        }
+        cp_async_commit();
+    };
+    long long t = blockIdx.x;
+    if (t < ntiles) {
+        stage(cst, a.cur, t);
+        stage(pst, a.prev, t);
+    }
+    for (; t < ntiles; t += gridDim.x) {
+        const long long tn = t + gridDim.x;
+        int b, o, x;
+        const long long base = decode(t, b, o, x);
+        const bool act = x < a.nx;
+        cp_async_wait<1>();                          // this tile's psi^n
+        C v[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) v[q] = act ? cst[slot_pos<N, T, R0>(q, j) * kLanes + lane] : zero_c<R, C>();
+        if (tn < ntiles) stage(cst, a.cur, tn);
+        else cp_async_commit();
+        kinetic_line<N, false>(v, sm, lane, j, tw, kin, R(a.mem[b].eta));
+        cp_async_wait<1>();                          // this tile's partial level
+        if (act) {
+            if constexpr (AXIS == 1) {
+#pragma unroll
+                for (int q = 0; q < E; ++q) {
+                    const int pos = slot_pos<N, T, R0>(q, j);
+                    const C p = pst[pos * kLanes + lane];
+                    a.prev[base + pos * stride] = mk<C>(p.x + v[q].y, p.y - v[q].x);
+                }
+            } else {
+                const int y = o;
+                const R gxy = a.mask[0][x] * a.mask[1][y];
+                bool ok = true;
+                int slo[3] = {0, 0, 0}, shi[3] = {0, 0, 0};
+                if constexpr (SRC) source_box<R>(a, slo, shi);
+                const bool src_col = SRC && x >= slo[0] && x < shi[0] && y >= slo[1] && y < shi[1];
+                const C s = src_col ? a.tfac[(a.step - a.tfac_base) * a.batch + b] : zero_c<R, C>();
+#pragma unroll
+                for (int q = 0; q < E; ++q) {
+                    const int z = slot_pos<N, T, R0>(q, j);
+                    const long long idx = base + z * stride;
+                    C p = pst[z * kLanes + lane];
+                    if constexpr (SRC) {
+                        if (src_col && z >= slo[2] && z < shi[2]) {
+                            const C sa = source_acc<R, C>(a, b, s, x, y, z, idx);
+                            p = mk<C>(p.x + a.c2 * sa.y, p.y - a.c2 * sa.x);
+                        }
+                    }
+                    const R g = gxy * a.mask[2][z];
+                    const C acc = mk<C>(g * (p.x + v[q].y), g * (p.y - v[q].x));
+                    ok = ok && finite_c<R>(acc.x, acc.y);
+                    a.prev[idx] = acc;
+                }
+                if (!ok) atomicOr(a.flag, 1);
+            }
+        }
+        if (tn < ntiles) stage(pst, a.prev, tn);
+        else cp_async_commit();
+        __syncthreads();                             // the exchange tile is reused by the next tile
+    }
+    cp_async_wait<0>();
+}
+
+// ---------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------
 template <typename R, int N> size_t pass_smem() { return sizeof(typename StepArgs<R>::C) * (size_t)N * kPitch; }
@@ -570,8 +700,37 @@ template <typename R, int N> cudaError_t xpass_n(const StepArgs<R>& a, const Dft
     if (d) return launch_step_kernel(xpass_kernel<R, N, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
     return launch_step_kernel(xpass_kernel<R, N, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
 }
+inline int sm_count()
+{
+    static int count[32] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 32) return 152;
+    if (!count[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        count[dev] = n > 0 ? n : 152;
+    }
+    return count[dev];
+}
+
+template <typename R, int N, int AXIS, bool SRC> cudaError_t colpass_pipe_n(const StepArgs<R>& a, int batch, cudaStream_t s)
+{
+    if constexpr (pipe_supported<R, N>()) {
+        const size_t sm = pipe_smem<R, N>();
+        cudaError_t e = set_smem_once<colpass_pipe_kernel<R, N, AXIS, SRC>>(sm);
+        if (e != cudaSuccess) return e;
+        const long long ntiles = (long long)((a.nx + kLanes - 1) / kLanes) * (AXIS == 1 ? a.nz : a.ny) * batch;
+        const dim3 grid((unsigned)std::min<long long>(ntiles, sm_count()));
+        return launch_step_kernel(colpass_pipe_kernel<R, N, AXIS, SRC>, grid, dim3(kLanes * Plan<N>::T), sm, s, a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
+    if constexpr (pipe_supported<R, N>())
+        if (!d) return colpass_pipe_n<R, N, 1, false>(a, batch, s);
     const size_t sm = pass_smem<R, N>();
     cudaError_t e = d ? set_smem_once<ypass_kernel<R, N, true>>(sm) : set_smem_once<ypass_kernel<R, N, false>>(sm);
     if (e != cudaSuccess) return e;
@@ -583,6 +742,8 @@ template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const Dft
 template <typename R, int N>
 cudaError_t zpass_n(const StepArgs<R>& a, const DftArgs<R>* d, bool src, int batch, cudaStream_t s)
 {
+    if constexpr (pipe_supported<R, N>())
+        if (!d) return src ? colpass_pipe_n<R, N, 2, true>(a, batch, s) : colpass_pipe_n<R, N, 2, false>(a, batch, s);
     const size_t sm = pass_smem<R, N>();
     cudaError_t e = d ? (src ? set_smem_once<zpass_kernel<R, N, true, true>>(sm) : set_smem_once<zpass_kernel<R, N, true, false>>(sm))
                       : src ? set_smem_once<zpass_kernel<R, N, false, true>>(sm) : set_smem_once<zpass_kernel<R, N, false, false>>(sm);
