@@ -60,7 +60,7 @@ ONE_STEP_SPECS = {
     "square-96x96x24": lambda mode: inputs.GridSpec(n=(96, 96, 24), d=(0.2, 0.2, 0.3), dt=0.001, abc_cells=(8, 8, 3),
                                                     tfsf_lo=(36, 36, 9), tfsf_hi=(60, 60, 15), taper_cells=2,
                                                     huygens_lo=(28, 28, 6), huygens_hi=(68, 68, 18), tfsf_mode=mode),
-    # long y and z lines: the pipelined y and z passes (FP32, N = 192 and 256)
+    # long y and z lines: the pipelined y pass (FP32, N = 192) and N = 256 z lines
     "pipe-16x192x256": lambda mode: inputs.GridSpec(n=(16, 192, 256), d=(0.3, 0.1, 0.08), dt=0.0005,
                                                     abc_cells=(2, 16, 20), tfsf_lo=(5, 60, 80), tfsf_hi=(11, 132, 176),
                                                     taper_cells=1, huygens_lo=(3, 40, 50), huygens_hi=(13, 150, 206),
