@@ -26,6 +26,7 @@ Readings where the paper is silent or garbled (each also listed in the design no
     wave enters only through V psi_inc, so that the injected wave is consistent with
     the grid's own operator; "paper" form: Eq. tildeSchrodinger verbatim;
   * the CW source is a raised-cosine ramp a(t) = (1 - cos(pi t / T_r)) / 2 for t < T_r;
+    a wave-packet source is the free Gaussian packet in closed form along d = khat . (r - r_O);
   * initial state psi^{-1} = psi^0 = 0; step n uses psi_inc at t_n = n dt and the DFT
     of step n takes the state psi^n before it is advanced;
   * normal derivatives on the virtual planes are spectral derivatives along the
@@ -146,6 +147,20 @@ def envelope(t: float, ramp_time: float) -> float:
     return 0.5 * (1.0 - math.cos(math.pi * t / ramp_time))
 
 
+def gaussian_packet(x, t: float, k: float, sigma: float, hbar: float = 1.0, mass: float = 1.0):
+    """Free 1-D Gaussian wave packet (one of the incident waves with an analytic form that
+    Section 2.2.3 names), psi(x, 0) = exp(-x^2 / (4 sigma^2) + i k x), evolved by
+    i hbar d_t psi = -hbar^2/2m d_x^2 psi:
+        psi(x, t) = (1 + i tau)^(-1/2) exp(-(x - v t)^2 / (4 sigma^2 (1 + i tau)) + i (k x - w t)),
+    tau = hbar t / (2 m sigma^2), v = hbar k / m, w = hbar k^2 / 2m."""
+    x = np.asarray(x, dtype=float)
+    tau = hbar * t / (2.0 * mass * sigma * sigma)
+    v = hbar * k / mass
+    w = hbar * k * k / (2.0 * mass)
+    q = 1.0 + 1j * tau
+    return q ** -0.5 * np.exp(-(x - v * t) ** 2 / (4.0 * sigma * sigma * q) + 1j * (k * x - w * t))
+
+
 def first_contact_corner(khat, spec) -> np.ndarray:
     """Corner O of the TF/SF box first met by the incident wavefront (Eq. Oinc).
 
@@ -221,7 +236,7 @@ def in_plane_axes(axis: int):
 class Simulation:
     """Leapfrog PSTD run of one incident plane wave on a GridSpec (Eq. PSTDupdating)."""
 
-    def __init__(self, spec, V, khat, k, ramp_time, window=None, omegas=None, probes=None):
+    def __init__(self, spec, V, khat, k, ramp_time, window=None, omegas=None, probes=None, packet=None):
         self.spec = spec
         hb, m = spec.hbar, spec.mass
         self.V = np.asarray(V, dtype=np.float64)
@@ -231,6 +246,9 @@ class Simulation:
         self.E0 = hb * hb * self.k ** 2 / (2.0 * m)
         self.w0 = self.E0 / hb
         self.ramp_time = float(ramp_time)
+        # optional Gaussian wave-packet incidence (sigma, d0): the packet's centre starts at
+        # d0 on the axis d = khat . (r - r_O) and moves along +khat (replaces the CW wave)
+        self.packet = None if packet is None else (float(packet[0]), float(packet[1]))
         self.eta = eta(self.E0, spec.dt, hb)
         self.kin_coef = hb * hb / (2.0 * m) * self.eta
         # mask Gamma = Gamma_x Gamma_y Gamma_z (Eq. Gamma)
@@ -242,6 +260,8 @@ class Simulation:
         x = [coords(spec.n[a], spec.d[a]) for a in range(3)]
         ph = [np.exp(1j * self.kvec[a] * (x[a] - self.rO[a])) for a in range(3)]
         self.inc_phase = ph[2][:, None, None] * ph[1][None, :, None] * ph[0][None, None, :]
+        dd = [self.khat[a] * (x[a] - self.rO[a]) for a in range(3)]
+        self.inc_d = dd[2][:, None, None] + dd[1][None, :, None] + dd[0][None, None, :]   # Eq. inc_d
         # taper zeta and the source factor of Eq. tildeSchrodinger
         zt = [zeta_1d(spec.n[a], spec.d[a], spec.tfsf_lo[a], spec.tfsf_hi[a], spec.taper_cells) for a in range(3)]
         Z = [z[0] for z in zt]
@@ -275,11 +295,17 @@ class Simulation:
 
     # -- incident wave ---------------------------------------------------------------
     def inc_time_factor(self, n: int) -> complex:
-        """a(t_n) exp(-i w0 t_n): the incident wave at O at step n."""
+        """The incident wave at O at step n: a(t_n) exp(-i w0 t_n), or the packet at d = 0."""
         t = n * self.spec.dt
+        if self.packet is not None:
+            sig, d0 = self.packet
+            return complex(gaussian_packet(0.0 - d0, t, self.k, sig, self.spec.hbar, self.spec.mass))
         return envelope(t, self.ramp_time) * complex(math.cos(self.w0 * t), -math.sin(self.w0 * t))
 
     def psi_inc(self, n: int) -> np.ndarray:
+        if self.packet is not None:
+            sig, d0 = self.packet
+            return gaussian_packet(self.inc_d - d0, n * self.spec.dt, self.k, sig, self.spec.hbar, self.spec.mass)
         return self.inc_time_factor(n) * self.inc_phase
 
     # -- one leapfrog step -----------------------------------------------------------
