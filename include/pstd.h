@@ -54,7 +54,7 @@ enum { PSTD_ABC_POLY = 0, PSTD_ABC_POSCHL_TELLER = 1 };     /* absorbing-layer p
 enum { PSTD_TFSF_EXACT = 0, PSTD_TFSF_PAPER = 1 };          /* TF/SF source form */
 enum { PSTD_ENV_CW_RAMP = 0 };                              /* incident-wave envelope */
 enum { PSTD_FIELD_CURRENT = 0, PSTD_FIELD_PREVIOUS = 1, PSTD_FIELD_SCATTERED = 2 };
-enum { PSTD_MAX_FREQ = 4, PSTD_MAX_BATCH = 64 };
+enum { PSTD_MAX_FREQ = 16, PSTD_MAX_BATCH = 64 };
 
 typedef struct pstd_grid pstd_grid;   /* opaque */
 
@@ -118,6 +118,19 @@ pstd_status pstd_set_potential(pstd_grid* g, const void* V, int mem, int dtype);
  * Also sets the dispersion factor eta = sinc(E dt / hbar) of member b (Eq. numdis2).
  * khat need not be normalised (it is).  EINVAL for b out of range, k <= 0, khat = 0. */
 pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double k, int envelope, double ramp_time);
+
+/* Incident Gaussian wave packet of batch member b, one of the incident waves with a closed
+ * form that Section 2.2.3 names (the broadband alternative to the CW wave):
+ *   psi_inc(r, t) = (1 + i tau)^(-1/2) exp(-(x - v t)^2 / (4 sigma^2 (1 + i tau)) + i (k x - E t / hbar)),
+ *   x = d - d0,  d = khat . (r - r_O) (Eq. inc_d),  tau = hbar t / (2 m sigma^2),  v = hbar k / m,
+ * i.e. a packet of spatial width sigma whose centre starts at d0 on the incidence axis (d0 < 0:
+ * before the first-contact corner r_O) and moves along khat.  The free packet in closed form
+ * solves the free Schrodinger equation exactly.  eta, r_O and the phase tables are set as
+ * for the CW wave (the carrier k).  Its spectrum covers E(k +- a few / sigma); the running
+ * DFT's phasors at each frequency are scaled by that frequency's incident phasor at r_O
+ * (Eq. incpsiphasor), so one run gives the scattering at every DFT frequency.
+ * EINVAL for b out of range, k <= 0, sigma <= 0, khat = 0. */
+pstd_status pstd_set_incidence_packet(pstd_grid* g, int b, const double khat[3], double k, double sigma, double d0);
 
 /* Zero both time levels, the step counter and every DFT accumulator of all members. */
 pstd_status pstd_reset(pstd_grid* g);

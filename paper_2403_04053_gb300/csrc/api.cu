@@ -34,11 +34,29 @@ struct MemberHost {
     double k = 0, E = 0, w0 = 0, eta = 1, ramp = 0;
     double rO[3] = {0, 0, 0};
     int nfreq = 0;
-    double omega[PSTD_MAX_FREQ] = {0, 0, 0, 0};
+    double omega[PSTD_MAX_FREQ] = {};
     long long first = 0, len = 0;
     long long accumulated = 0;
     cd inc_phasor[PSTD_MAX_FREQ];
+    bool packet = false;         // Gaussian wave packet (pstd_set_incidence_packet)
+    double sigma = 1.0, d0 = 0.0;
 };
+
+// The incident wave of member m at the first-contact corner r_O at time t (Eq. incpsiphasor's
+// integrand): the CW wave a(t) e^{-i w0 t}, or the packet at d = 0
+cd incident_at_origin(const MemberHost& m, double t, double hbar, double mass)
+{
+    if (m.packet) {
+        const double tau = hbar * t / (2.0 * mass * m.sigma * m.sigma);
+        const double v = hbar * m.k / mass;
+        const cd q(1.0, tau);
+        const double x = -m.d0;
+        return std::pow(q, -0.5) * std::exp(-(x - v * t) * (x - v * t) / (4.0 * m.sigma * m.sigma * q) +
+                                            cd(0.0, m.k * x - m.w0 * t));
+    }
+    const double env = (m.ramp <= 0 || t >= m.ramp) ? 1.0 : (t <= 0 ? 0.0 : 0.5 * (1.0 - std::cos(kPi * t / m.ramp)));
+    return env * std::exp(cd(0.0, -m.w0 * t));
+}
 
 struct TimedLaunch {
     int kernel;
@@ -79,6 +97,10 @@ struct pstd_grid {
     long long acc_freq_stride = 0;
     long long phasor_version = 0;
     void* tfac = nullptr;                  // [step of the call][member] a(t_n) e^{-i w0 t_n}, working precision
+    void* tenv = nullptr;                  // [step of the call][member][3] wave-packet envelope coefficients
+    size_t tenv_cap = 0;
+    void* proj[3] = {};                    // [member][i] khat_a (x_a - r_O,a), working precision
+    unsigned long long packet_mask = 0;
     size_t tfac_cap = 0;
     double2* dft_phase = nullptr;          // [member][freq][window step] e^{+i omega t_n}
     size_t dft_phase_cap = 0;
@@ -426,6 +448,7 @@ pstd_status upload_members(pstd_grid* g)
         for (int a = 0; a < 3; ++a) o.k[a] = m.k * m.khat[a];
         o.nfreq = m.nfreq;
         for (int f = 0; f < PSTD_MAX_FREQ; ++f) o.omega[f] = m.omega[f];
+        o.packet = m.packet ? 1 : 0;
     }
     CK(g, cudaMemcpyAsync(g->mem_dev, h.data(), sizeof(MemberDev) * g->batch, cudaMemcpyHostToDevice, g->stream));
     CK(g, cudaStreamSynchronize(g->stream));
@@ -462,6 +485,9 @@ template <typename R> StepArgs<R> step_args(pstd_grid* g)
     a.h2m = R(g->desc.hbar * g->desc.hbar / (2.0 * g->desc.mass));
     a.mode = g->desc.tfsf_mode;
     a.flag = g->flag;
+    a.packet_mask = g->packet_mask;
+    for (int ax = 0; ax < 3; ++ax) a.proj[ax] = static_cast<const R*>(g->proj[ax]);
+    a.tenv = static_cast<const R*>(g->tenv);
     return a;
 }
 
@@ -498,12 +524,37 @@ template <typename R> DftArgs<R> dft_args(pstd_grid* g, unsigned long long mask,
 pstd_status upload_time_factors(pstd_grid* g, long long n0, long nsteps)
 {
     std::vector<cd> tab((size_t)std::max(1L, nsteps) * g->batch);
+    std::vector<double> env((size_t)std::max(1L, nsteps) * g->batch * 3, 0.0);
+    bool any_packet = false;
     for (long s = 0; s < nsteps; ++s) {
         const double t = (n0 + s) * g->desc.dt;
         for (int b = 0; b < g->batch; ++b) {
             const MemberHost& m = g->mem[b];
-            const double env = (m.ramp <= 0 || t >= m.ramp) ? 1.0 : (t <= 0 ? 0.0 : 0.5 * (1.0 - std::cos(kPi * t / m.ramp)));
-            tab[(size_t)s * g->batch + b] = cd(env * std::cos(m.w0 * t), -env * std::sin(m.w0 * t));
+            if (m.packet) {
+                // psi_inc = [q^{-1/2} e^{-i w0 t} e^{-i k d0}] e^{i k d} exp(-alpha (d - c)^2),
+                // q = 1 + i tau, alpha = 1 / (4 sigma^2 q), c = d0 + v t
+                any_packet = true;
+                const double tau = g->desc.hbar * t / (2.0 * g->desc.mass * m.sigma * m.sigma);
+                const cd q(1.0, tau);
+                tab[(size_t)s * g->batch + b] = std::pow(q, -0.5) * std::exp(cd(0.0, -m.w0 * t - m.k * m.d0));
+                const cd alpha = 1.0 / (4.0 * m.sigma * m.sigma * q);
+                double* e = &env[3 * ((size_t)s * g->batch + b)];
+                e[0] = alpha.real();
+                e[1] = alpha.imag();
+                e[2] = m.d0 + g->desc.hbar * m.k / g->desc.mass * t;
+            } else {
+                tab[(size_t)s * g->batch + b] = incident_at_origin(m, t, g->desc.hbar, g->desc.mass);
+            }
+        }
+    }
+    if (any_packet) {
+        pstd_status st = ensure(g, &g->tenv, g->tenv_cap, env.size() * g->rsize);
+        if (st != PSTD_OK) return st;
+        if (g->prec == PSTD_F64) {
+            CK(g, cudaMemcpyAsync(g->tenv, env.data(), env.size() * 8, cudaMemcpyHostToDevice, g->stream));
+        } else {
+            std::vector<float> f(env.begin(), env.end());
+            CK(g, cudaMemcpyAsync(g->tenv, f.data(), f.size() * 4, cudaMemcpyHostToDevice, g->stream));
         }
     }
     pstd_status st = ensure(g, &g->tfac, g->tfac_cap, tab.size() * g->csize);
@@ -576,8 +627,7 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft 
             for (int b = 0; b < g->batch; ++b) {
                 if (!((mask >> b) & 1ull)) continue;
                 MemberHost& m = g->mem[b];
-                const double env = (m.ramp <= 0 || t >= m.ramp) ? 1.0 : (t <= 0 ? 0.0 : 0.5 * (1.0 - std::cos(kPi * t / m.ramp)));
-                const cd inc = env * std::exp(cd(0.0, -m.w0 * t));   // psi_inc at r_O (Eq. incpsiphasor)
+                const cd inc = incident_at_origin(m, t, g->desc.hbar, g->desc.mass);   // Eq. incpsiphasor
                 for (int f = 0; f < m.nfreq; ++f) m.inc_phasor[f] += inc * std::exp(cd(0.0, m.omega[f] * t));
                 ++m.accumulated;
             }
@@ -973,7 +1023,7 @@ pstd_status run_adjoint(pstd_grid* g, long nsteps, const double2* gph, const int
     std::vector<cd> S(nf, cd(0, 0));
     for (long long n = m.first; n < m.first + m.len; ++n) {
         const double t = n * g->desc.dt;
-        const cd inc = envelope_at(m, t) * std::exp(cd(0.0, -m.w0 * t));
+        const cd inc = incident_at_origin(m, t, g->desc.hbar, g->desc.mass);
         for (int f = 0; f < nf; ++f) S[f] += inc * std::exp(cd(0.0, m.omega[f] * t));
     }
     for (int f = 0; f < nf; ++f)
@@ -1237,6 +1287,8 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     for (int a = 0; a < 3; ++a)
         for (void* p : {g->tw[a], g->kin[a], g->mask[a], g->zeta[a], g->zeta1[a], g->zeta2[a], g->phase[a], g->dw[a]})
             if (p) cudaFree(p);
+    for (void* p : {g->tenv, g->proj[0], g->proj[1], g->proj[2]})
+        if (p) cudaFree(p);
     for (void* p : {g->adj_table, g->adj_partial, g->adj_rec, g->adj_PA, (void*)g->adj_gpts, (void*)g->adj_out, g->adj_J,
                     g->adj_ckpt, g->adj_seg, g->adj_nu, g->adj_zero, (void*)g->adj_grad})
         if (p) cudaFree(p);
@@ -1342,17 +1394,13 @@ pstd_status pstd_set_potential(pstd_grid* g, const void* V, int mem, int dtype)
     return PSTD_OK;
 }
 
-pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double k, int envelope, double ramp_time)
+namespace {
+// direction, carrier, r_O, phase and projection tables, eta and (member 0) the absorber of an
+// incident wave of member b; the envelope is set by the caller
+pstd_status set_incidence_common(pstd_grid* g, int b, const double khat[3], double k)
 {
-    if (!g || !khat) return fail(g, PSTD_EINVAL, "null argument");
-    DeviceGuard dg(g->dev);
-    g->ckpt_upto = -1;        // recorded checkpoints belong to the previous incidence
-    g->ckpt_contig = false;
-    pstd_status st = check_member(g, b);
-    if (st != PSTD_OK) return st;
-    if (envelope != PSTD_ENV_CW_RAMP) return fail(g, PSTD_EINVAL, "envelope");
     const double nrm = std::sqrt(khat[0] * khat[0] + khat[1] * khat[1] + khat[2] * khat[2]);
-    if (!(k > 0) || !(nrm > 0) || !(ramp_time >= 0)) return fail(g, PSTD_EINVAL, "k, khat or ramp_time");
+    if (!(k > 0) || !(nrm > 0)) return fail(g, PSTD_EINVAL, "k or khat");
     const pstd_grid_desc& d = g->desc;
     MemberHost& m = g->mem[b];
     m.has_inc = true;
@@ -1362,7 +1410,6 @@ pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double
     m.w0 = m.E / d.hbar;
     const double x = m.E * d.dt / d.hbar;
     m.eta = x == 0 ? 1.0 : std::sin(x) / x;   // Eq. numdis2
-    m.ramp = ramp_time;
     // first-contact corner: the TF/SF box corner minimising khat . r (Eq. Oinc)
     double best = 0;
     bool first = true;
@@ -1378,12 +1425,24 @@ pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double
                     for (int a = 0; a < 3; ++a) m.rO[a] = c[a];
                 }
             }
+    pstd_status st = PSTD_OK;
     for (int a = 0; a < 3; ++a) {
         const int n = d.n[a];
         std::vector<cd> ph(n);
-        for (int i = 0; i < n; ++i) ph[i] = std::exp(cd(0.0, k * m.khat[a] * (coord(d, a, i) - m.rO[a])));
+        std::vector<double> pr(n);
+        for (int i = 0; i < n; ++i) {
+            pr[i] = m.khat[a] * (coord(d, a, i) - m.rO[a]);   // Eq. inc_d, one axis
+            ph[i] = std::exp(cd(0.0, k * pr[i]));
+        }
         st = upload_complex(g, &g->phase[a], ph, (size_t)b * n, (size_t)n * g->batch);
         if (st != PSTD_OK) return st;
+        if (!g->proj[a]) CK(g, dalloc(&g->proj[a], (size_t)n * g->batch * g->rsize));
+        if (g->prec == PSTD_F64) {
+            CK(g, cudaMemcpy(static_cast<char*>(g->proj[a]) + (size_t)b * n * 8, pr.data(), (size_t)n * 8, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> f(pr.begin(), pr.end());
+            CK(g, cudaMemcpy(static_cast<char*>(g->proj[a]) + (size_t)b * n * 4, f.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+        }
     }
     if (b == 0) {   // absorber strength is expressed in units of member 0's E / hbar
         for (int a = 0; a < 3; ++a) {
@@ -1394,6 +1453,48 @@ pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double
         }
         g->mask_ready = true;
     }
+    return PSTD_OK;
+}
+}  // namespace
+
+pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double k, int envelope, double ramp_time)
+{
+    if (!g || !khat) return fail(g, PSTD_EINVAL, "null argument");
+    DeviceGuard dg(g->dev);
+    g->ckpt_upto = -1;        // recorded checkpoints belong to the previous incidence
+    g->ckpt_contig = false;
+    pstd_status st = check_member(g, b);
+    if (st != PSTD_OK) return st;
+    if (envelope != PSTD_ENV_CW_RAMP) return fail(g, PSTD_EINVAL, "envelope");
+    if (!(ramp_time >= 0)) return fail(g, PSTD_EINVAL, "ramp_time");
+    st = set_incidence_common(g, b, khat, k);
+    if (st != PSTD_OK) return st;
+    MemberHost& m = g->mem[b];
+    m.ramp = ramp_time;
+    m.packet = false;
+    g->packet_mask &= ~(1ull << b);
+    return upload_members(g);
+}
+
+pstd_status pstd_set_incidence_packet(pstd_grid* g, int b, const double khat[3], double k, double sigma, double d0)
+{
+    if (!g || !khat) return fail(g, PSTD_EINVAL, "null argument");
+    DeviceGuard dg(g->dev);
+    g->ckpt_upto = -1;
+    g->ckpt_contig = false;
+    pstd_status st = check_member(g, b);
+    if (st != PSTD_OK) return st;
+    if (!(sigma > 0) || !std::isfinite(d0)) return fail(g, PSTD_EINVAL, "sigma or d0");
+    if (g->desc.tfsf_mode != PSTD_TFSF_EXACT)
+        return fail(g, PSTD_EINVAL, "wave-packet incidence needs the EXACT TF/SF form (V (psi + psi_inc))");
+    st = set_incidence_common(g, b, khat, k);
+    if (st != PSTD_OK) return st;
+    MemberHost& m = g->mem[b];
+    m.ramp = 0.0;
+    m.packet = true;
+    m.sigma = sigma;
+    m.d0 = d0;
+    g->packet_mask |= 1ull << b;
     return upload_members(g);
 }
 
@@ -1747,6 +1848,7 @@ pstd_status pstd_adjoint_gradient(pstd_grid* g, long nsteps, const void* dl_dpha
     DeviceGuard dg(g->dev);
     const MemberHost& m = g->mem[0];
     if (!m.has_inc) return fail(g, PSTD_ESTATE, "pstd_set_incidence first");
+    if (m.packet) return fail(g, PSTD_EINVAL, "the adjoint supports the CW incidence");
     if (m.nfreq < 1 || m.len < 1) return fail(g, PSTD_ESTATE, "pstd_huygens_dft first (the loss is a function of the phasors)");
     if (m.first + m.len > nsteps) return fail(g, PSTD_EINVAL, "the DFT window must end within nsteps");
     for (int a = 0; a < 3; ++a)

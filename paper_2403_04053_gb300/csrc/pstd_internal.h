@@ -19,6 +19,7 @@ struct MemberDev {
     double k[3];    // wave vector k * khat
     double omega[PSTD_MAX_FREQ];   // DFT angular frequencies
     int nfreq;
+    int packet;     // incident Gaussian wave packet (else CW)
     int dft_active; // set per step by the host (bit mask passed separately)
 };
 
@@ -48,6 +49,11 @@ template <typename R> struct StepArgs {
     int* flag;               // bit 0: non-finite value written
     const C* tfac;           // a(t_n) e^{-i w0 t_n}: [(n - tfac_base) * batch + member], evaluated in FP64 on the host
     long long tfac_base;
+    // wave-packet members: psi_inc = tfac * phases * exp(-alpha_n (d - c_n)^2), d = sum of the
+    // per-axis projections khat_a (x_a - r_O,a); tenv = [(n - tfac_base) * batch + member][Re alpha, Im alpha, c]
+    unsigned long long packet_mask;
+    const R* proj[3];        // [member * n_a + i]
+    const R* tenv;
     int batch;
 };
 

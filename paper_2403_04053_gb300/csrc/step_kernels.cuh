@@ -416,8 +416,37 @@ __global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid
 // ---------------------------------------------------------------------------------
 constexpr int kSourceZ = 4;   // z planes per thread of the source kernel
 
+// Gaussian envelope of a wave-packet member at node (x, y, z):
+// exp(-alpha_n (d - c_n)^2) with d = khat . (r - r_O) from the per-axis projection tables
+template <typename R, typename C>
+__device__ __forceinline__ C packet_envelope(const StepArgs<R>& a, int b, int x, int y, int z)
+{
+    const R* e = a.tenv + 3 * ((a.step - a.tfac_base) * a.batch + b);
+    const R d = a.proj[0][b * a.nx + x] + a.proj[1][b * a.ny + y] + a.proj[2][b * a.nz + z];
+    const R u = d - e[2];
+    const R u2 = u * u;
+    R sn, cs, mag;
+    if constexpr (sizeof(R) == 4) {
+        sincosf(-e[1] * u2, &sn, &cs);
+        mag = expf(-e[0] * u2);
+    } else {
+        sincos(-e[1] * u2, &sn, &cs);
+        mag = exp(-e[0] * u2);
+    }
+    return mk<C>(mag * cs, mag * sn);
+}
+
+// the incident wave of member b at node (x, y, z), step a.step; s = the member's time factor
+template <typename R, typename C>
+__device__ __forceinline__ C incident_wave(const StepArgs<R>& a, int b, C s, int x, int y, int z)
+{
+    C w = incident_at<R, C>(a, b, s, x, y, z);
+    if ((a.packet_mask >> b) & 1ull) w = cmul(w, packet_envelope<R, C>(a, b, x, y, z));
+    return w;
+}
+
 // V-term + source at node (x, y, z) of member b (before the factor -(2 i dt / hbar));
-// s = a(t_n) e^{-i w0 t_n}, idx the node's state index
+// s = the member's incident time factor at step n, idx the node's state index
 template <typename R, typename C>
 __device__ __forceinline__ C source_acc(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
 {
@@ -427,7 +456,7 @@ __device__ __forceinline__ C source_acc(const StepArgs<R>& a, int b, C s, int x,
         const int vnx = a.vhi[0] - a.vlo[0], vny = a.vhi[1] - a.vlo[1];
         const R Vv = a.V[((long long)(z - a.vlo[2]) * vny + (y - a.vlo[1])) * vnx + (x - a.vlo[0])];
         C src = a.cur[idx];
-        if (!paper) src = cadd(src, incident_at<R, C>(a, b, s, x, y, z));
+        if (!paper) src = cadd(src, incident_wave<R, C>(a, b, s, x, y, z));
         acc = cscale(src, Vv);
     }
     if (paper && x > a.tf_lo[0] && x < a.tf_hi[0] && y > a.tf_lo[1] && y < a.tf_hi[1] && z > a.tf_lo[2] && z < a.tf_hi[2]) {
@@ -437,7 +466,7 @@ __device__ __forceinline__ C source_acc(const StepArgs<R>& a, int b, C s, int x,
         const R lap = zx2 * zy * zz + zx * zy2 * zz + zx * zy * zz2;
         const MemberDev& md = a.mem[b];
         const R kg = R(md.k[0]) * zx1 * zy * zz + R(md.k[1]) * zx * zy1 * zz + R(md.k[2]) * zx * zy * zz1;
-        acc = cadd(acc, cscale(cmul(incident_at<R, C>(a, b, s, x, y, z), mk<C>(lap, R(2) * kg)), a.h2m));
+        acc = cadd(acc, cscale(cmul(incident_at<R, C>(a, b, s, x, y, z), mk<C>(lap, R(2) * kg)), a.h2m));   // CW only
     }
     return acc;
 }

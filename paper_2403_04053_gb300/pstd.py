@@ -23,7 +23,7 @@ ABC_POLY, ABC_POSCHL_TELLER = 0, 1
 TFSF_EXACT, TFSF_PAPER = 0, 1
 ENV_CW_RAMP = 0
 FIELD_CURRENT, FIELD_PREVIOUS, FIELD_SCATTERED = 0, 1, 2
-MAX_FREQ = 4
+MAX_FREQ = 16
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ESTATE", 6: "ENONFINITE", 7: "ETIMEOUT"}
 KERNELS = {"xpass": 0, "ypass": 1, "zpass": 2, "xypass": 3, "prepare": 4, "transform": 5, "far_field": 6, "source": 7}
@@ -69,6 +69,7 @@ _SIGS = {
     "pstd_transform_adjoint": (c_int, [c_void_p, c_int, c_int, c_void_p, c_long, c_void_p, c_void_p, c_int]),
     "pstd_adjoint_gradient": (c_int, [c_void_p, c_long, c_void_p, POINTER(c_int), POINTER(c_int), c_long, c_void_p, c_int]),
     "pstd_set_checkpointing": (c_int, [c_void_p, c_long, c_long]),
+    "pstd_set_incidence_packet": (c_int, [c_void_p, c_int, POINTER(c_double), c_double, c_double, c_double]),
 }
 
 _lib = None
@@ -198,6 +199,12 @@ class Grid:
     def set_incidence(self, b: int, khat, k: float, ramp_time: float, envelope: int = ENV_CW_RAMP):
         kh = (c_double * 3)(*[float(v) for v in khat])
         self._c(self.lib.pstd_set_incidence(self.h, b, kh, float(k), envelope, float(ramp_time)), "pstd_set_incidence")
+
+    def set_incidence_packet(self, b: int, khat, k: float, sigma: float, d0: float):
+        """Gaussian wave-packet incidence of member b (pstd_set_incidence_packet)."""
+        kh = (c_double * 3)(*[float(v) for v in khat])
+        self._c(self.lib.pstd_set_incidence_packet(self.h, b, kh, float(k), float(sigma), float(d0)),
+                "pstd_set_incidence_packet")
 
     def reset(self):
         self._c(self.lib.pstd_reset(self.h), "pstd_reset")

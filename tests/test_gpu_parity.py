@@ -442,3 +442,104 @@ def test_batched_256_cube_matches_separate_runs():
             assert rel(got[i][0], g1.get_field(1)) < 1e-6
             for a, b in zip(got[i][1], g1.get_phasors(1, 0)):
                 assert rel(a[0], b[0]) < 1e-6 and rel(a[1], b[1]) < 1e-6
+
+
+# ----------------------------------------------------------------------------------
+# Gaussian wave-packet incidence and many DFT frequencies
+# ----------------------------------------------------------------------------------
+PACKET = (0.6, -1.0)   # sigma, d0: the packet overlaps the scatterer within a few steps
+
+
+@pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-12), (pstd.F32, 2e-6)])
+def test_packet_one_step_matches_oracle(prec, tol):
+    spec = ragged_spec("exact")
+    V = random_core_V(spec, 3)
+    khat = (0.3, -0.5, 0.81)
+    prev = inputs.random_field(spec.shape, 5)
+    cur = inputs.random_field(spec.shape, 6)
+    sim = po.Simulation(spec, V, khat, K, 0.0, packet=PACKET)
+    sim.prev, sim.cur, sim.n = prev.copy(), cur.copy(), 17
+    sim.step(1)
+    cd = np.complex128 if prec == pstd.F64 else np.complex64
+    with pstd.Grid(spec, precision=prec) as g:
+        g.set_potential(V)
+        g.set_incidence_packet(0, khat, K, *PACKET)
+        g.set_field(0, prev.astype(cd), cur.astype(cd), 17)
+        g.step(1)
+        assert rel(g.get_field(0), sim.cur) < tol
+
+
+@pytest.mark.parametrize("prec,tol_state,tol_out", [(pstd.F64, 1e-12, 1e-10), (pstd.F32, 2e-5, 2e-4)])
+def test_packet_run_with_many_frequencies(prec, tol_state, tol_out):
+    # 60 steps, a 40-step window, 9 DFT frequencies across the packet's spectrum
+    spec = ragged_spec("exact")
+    V = random_core_V(spec, 1)
+    khat = (0.3, -0.5, 0.81)
+    om = list(np.linspace(0.8, 1.2, 9) * E0)
+    sim = po.Simulation(spec, V, khat, K, 0.0, window=(20, 40), omegas=om, packet=PACKET)
+    sim.step(60)
+    pts = np.array([[3.0, -2.0, 5.5], [-4.0, 6.0, 1.0], [30.0, 10.0, 40.0]])
+    with pstd.Grid(spec, precision=prec) as g:
+        g.set_potential(V)
+        g.set_incidence_packet(0, khat, K, *PACKET)
+        g.huygens_dft(0, om, 20, 40)
+        g.step(60)
+        assert rel(g.get_field(0), sim.cur) < tol_state
+        for f in (0, 4, 8):
+            ref = sim.scaled_phasors(f)
+            got = g.get_phasors(0, f)
+            for a, b in zip(got, ref):
+                assert rel(a[0], b[0]) < tol_out and rel(a[1], b[1]) < tol_out
+            kf = math.sqrt(2 * om[f])
+            assert rel(g.transform_to_points(0, f, pts), no.transform_to_points(spec, kf, ref, pts)) < tol_out
+
+
+@pytest.mark.parametrize("prec", [pstd.F64, pstd.F32])
+def test_packet_run_reproduces_cw_cross_sections(prec):
+    # one packet run gives, at each DFT frequency, the scattering of a CW wave of that energy
+    spec = inputs.GridSpec(n=(24, 24, 24), d=(0.25, 0.25, 0.25), dt=0.004, abc_cells=(4, 4, 4), tfsf_lo=(6, 6, 6),
+                           tfsf_hi=(17, 17, 17), taper_cells=2, huygens_lo=(5, 5, 5), huygens_hi=(18, 18, 18))
+    x = [spec.coords(a) for a in range(3)]
+    Z, Y, X = np.meshgrid(x[2], x[1], x[0], indexing="ij")
+    V = 6.0 * np.exp(-(X ** 2 + Y ** 2 + Z ** 2) / (2 * 0.5 ** 2))
+    c = spec.core_box()
+    inside = np.zeros(spec.shape, bool)
+    inside[c[2][0]:c[2][1] + 1, c[1][0]:c[1][1] + 1, c[0][0]:c[0][1] + 1] = True
+    V[~inside] = 0
+    oms = [0.9 * E0, E0, 1.1 * E0]
+    th, ph = np.deg2rad([10.0, 60.0, 120.0, 170.0]), np.zeros(4)
+    with pstd.Grid(spec, precision=prec) as g:
+        g.set_potential(V)
+        g.set_incidence_packet(0, (0, 0, 1), K, 1.0, -6.0)
+        g.huygens_dft(0, oms, 0, 1200)
+        g.step(1200)
+        fp = [g.cross_section(0, i, th, ph)[1] for i in range(3)]
+    for i, (w, tol) in enumerate(zip(oms, (2e-2, 1e-3, 2e-2))):
+        kw = math.sqrt(2 * w)
+        with pstd.Grid(spec, precision=prec) as g:
+            g.set_potential(V)
+            g.set_incidence(0, (0, 0, 1), kw, 0.5)
+            g.huygens_dft(0, [w], *inputs.dft_window(w, spec.dt, 900))
+            g.step(900)
+            fc = g.cross_section(0, 0, th, ph)[1]
+        assert rel(fp[i], fc) < tol
+
+
+def test_packet_call_errors():
+    with pstd.Grid(ragged_spec("paper"), precision=pstd.F32) as g:
+        with pytest.raises(pstd.PstdError) as e:
+            g.set_incidence_packet(0, (0, 0, 1), K, 1.0, -2.0)
+        assert e.value.code == "EINVAL"        # the packet needs the EXACT form
+    with pstd.Grid(ragged_spec("exact"), precision=pstd.F32) as g:
+        for sig in (0.0, -1.0):
+            with pytest.raises(pstd.PstdError) as e:
+                g.set_incidence_packet(0, (0, 0, 1), K, sig, -2.0)
+            assert e.value.code == "EINVAL"
+        with pytest.raises(pstd.PstdError) as e:
+            g.huygens_dft(0, [E0] * (pstd.MAX_FREQ + 1), 0, 10)
+        assert e.value.code == "EINVAL"
+        g.set_incidence_packet(0, (0, 0, 1), K, 1.0, -2.0)
+        g.huygens_dft(0, [E0] * pstd.MAX_FREQ, 0, 10)
+        with pytest.raises(pstd.PstdError) as e:
+            g.adjoint_gradient(10, [np.zeros(g.phasor_count() * pstd.MAX_FREQ)], (0, 0, 0), (4, 4, 4))
+        assert e.value.code == "EINVAL"        # the adjoint supports the CW incidence
