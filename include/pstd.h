@@ -149,7 +149,8 @@ pstd_status pstd_step(pstd_grid* g, long nsteps);
 
 /* Scattered wave function at M points xyz[3*i + {0,1,2}] from the DFT of member b at
  * frequency index f, scaled by the incident phasor at r_O (Eqs. scaledphsiphasor,
- * scaleddpsiphasor): the per-cell semi-analytic surface integral of Eqs. bottomPsi_lm,
+ * scaleddpsiphasor), with the Green's function of that energy, k = sqrt(2 m omega_f) / hbar
+ * (the carrier k at omega_f = E / hbar): the per-cell semi-analytic surface integral of Eqs. bottomPsi_lm,
  * topPsi_lm, backfrontPsi_mn, leftrightPsi_ln summed per Eq. Psi, each cell integral
  * evaluated by tensor Gauss-Legendre quadrature of the trigonometric interpolant
  * (Eq. AnBottomPsi) times the linearised Green's phase.  out_psi: M complex128.

@@ -664,6 +664,16 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft 
 // -------------------------------------------------------------------------------------
 // transform preparation
 // -------------------------------------------------------------------------------------
+// Wavenumber of the free wave at DFT frequency f of member b, k = sqrt(2 m omega_f / hbar): the
+// Green's function of the transform (Eq. NTDF) at the energy hbar omega_f of those phasors
+// (the carrier k when omega_f = E / hbar)
+double wavenumber_of(const pstd_grid* g, int b, int f)
+{
+    const MemberHost& m = g->mem[b];
+    const double w = (f >= 0 && f < m.nfreq) ? m.omega[f] : m.w0;
+    return std::sqrt(2.0 * g->desc.mass * w / g->desc.hbar);
+}
+
 pstd_status setup_transform(pstd_grid* g)
 {
     if (g->MbT[0]) return PSTD_OK;
@@ -865,7 +875,7 @@ pstd_status run_far(pstd_grid* g, int b, int f, const double* theta, const doubl
     a.theta = theta;
     a.phi = phi;
     a.M = M;
-    a.k = g->mem[b].k;
+    a.k = wavenumber_of(g, b, f);
     // few directions: one CTA per (direction block, face) for parallelism; many: faces summed in-CTA
     const long long blocks = (M + 31) / 32;
     int nsm = 152;
@@ -897,7 +907,7 @@ pstd_status run_transform(pstd_grid* g, int b, int f, const double* pts, long M,
     for (int fi = 0; fi < 6; ++fi) a.face[fi] = g->faces[fi];
     a.pts = pts;
     a.M = M;
-    a.k = g->mem[b].k;
+    a.k = wavenumber_of(g, b, f);
     for (int q = 0; q < g->G; ++q) a.gl_node[q] = g->gl_x[q];
     const long long per_block = 128 * PSTD_TRANSFORM_PT;
     const long long blocks = (M + per_block - 1) / per_block;
@@ -945,7 +955,7 @@ double envelope_at(const MemberHost& m, double t)
 // gradient with respect to member b's scaled phasors (phasor layout, one frequency) of a
 // real loss of the transformed field at M points, given dL/dPsi there (device arrays)
 template <typename R>
-pstd_status run_transform_adjoint(pstd_grid* g, int b, const double* pts, const double2* gpts, long M, double2* out)
+pstd_status run_transform_adjoint(pstd_grid* g, int b, int f, const double* pts, const double2* gpts, long M, double2* out)
 {
     pstd_status st = setup_transform(g);
     if (st != PSTD_OK) return st;
@@ -957,7 +967,7 @@ pstd_status run_transform_adjoint(pstd_grid* g, int b, const double* pts, const 
     a.pts = pts;
     a.gpts = gpts;
     a.M = M;
-    a.k = g->mem[b].k;
+    a.k = wavenumber_of(g, b, f);
     for (int q = 0; q < G; ++q) a.gl_node[q] = g->gl_x[q];
     a.ncells = g->ncells;
     st = ensure(g, &g->adj_table, g->adj_table_cap, (size_t)6 * M * sizeof(AdjPoint<R>));
@@ -1831,8 +1841,8 @@ pstd_status pstd_transform_adjoint(pstd_grid* g, int b, int f, const double* xyz
             pts = g->pts_dev;
             gp = g->adj_gpts;
         }
-        st = g->prec == PSTD_F64 ? run_transform_adjoint<double>(g, b, pts, gp, M, g->adj_out)
-                                 : run_transform_adjoint<float>(g, b, pts, gp, M, g->adj_out);
+        st = g->prec == PSTD_F64 ? run_transform_adjoint<double>(g, b, f, pts, gp, M, g->adj_out)
+                                 : run_transform_adjoint<float>(g, b, f, pts, gp, M, g->adj_out);
         if (st != PSTD_OK) return st;
     }
     return copy_out(g, out, g->adj_out, count * sizeof(double2), mem);

@@ -112,8 +112,9 @@ def short_run(request):
     pts = np.array([[3.0, -2.0, 5.5], [-4.0, 6.0, 1.0], [0.5, 0.2, -9.0], [30.0, 10.0, 40.0], [-200.0, 50.0, 120.0]])
     th = np.deg2rad(np.array([0.0, 33.0, 90.0, 140.0, 180.0]))
     ph = np.deg2rad(np.array([0.0, 20.0, 200.0, 300.0, 10.0]))
-    ref = {f: (sim.scaled_phasors(f), no.transform_to_points(spec, K, sim.scaled_phasors(f), pts),
-               no.cross_section(spec, K, sim.scaled_phasors(f), th, ph)) for f in range(2)}
+    # the transform of frequency f's phasors uses the free wavenumber at that energy, sqrt(2 w_f)
+    ref = {f: (sim.scaled_phasors(f), no.transform_to_points(spec, math.sqrt(2 * om[f]), sim.scaled_phasors(f), pts),
+               no.cross_section(spec, math.sqrt(2 * om[f]), sim.scaled_phasors(f), th, ph)) for f in range(2)}
     return dict(spec=spec, V=V, khat=khat, win=win, om=om, sim=sim, pts=pts, th=th, ph=ph, ref=ref)
 
 
