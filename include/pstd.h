@@ -253,6 +253,14 @@ pstd_status pstd_adjoint_gradient(pstd_grid* g, long nsteps, const void* dl_dpha
  * discard the record; pstd_set_field stops it.  interval 0 stops recording.  Batch-1 grids. */
 pstd_status pstd_set_checkpointing(pstd_grid* g, long interval, long max_steps);
 
+/* CUDA-graph replay of pstd_step (on by default).  A pstd_step call that repeats the previous
+ * call's first step, step count and level parity with no set-up call in between (e.g. reset +
+ * step(N) per pass) is captured into a CUDA graph once and replayed from then on, instead of
+ * launching its 2-4 kernels per step one by one.  Not used while per-kernel timing or
+ * checkpoint recording is on; if capture is unavailable the grid falls back to direct launches.
+ * enable = 0 turns it off (and drops a captured graph); synchronises. */
+pstd_status pstd_set_graphs(pstd_grid* g, int enable);
+
 /* Message of the last failure on g (or of the last failed pstd_create_grid when g is NULL). */
 const char* pstd_last_error(const pstd_grid* g);
 

@@ -58,6 +58,20 @@ cd incident_at_origin(const MemberHost& m, double t, double hbar, double mass)
     return env * std::exp(cd(0.0, -m.w0 * t));
 }
 
+struct GraphKey {
+    bool valid = false;
+    long long n0 = 0, nsteps = 0;
+    int cur = 0;
+    long long version = 0;
+    const void* tfac = nullptr;
+    const void* tenv = nullptr;
+    bool operator==(const GraphKey& o) const
+    {
+        return valid && o.valid && n0 == o.n0 && nsteps == o.nsteps && cur == o.cur && version == o.version &&
+               tfac == o.tfac && tenv == o.tenv;
+    }
+};
+
 struct TimedLaunch {
     int kernel;
     cudaEvent_t a, b;
@@ -171,7 +185,13 @@ struct pstd_grid {
     size_t dsdo_cap = 0;
     // instrumentation
     bool timing = false;
-    bool use_xy = false;                    // fused x + y pass on steps without plane DFT
+    bool use_xy = false;                    // fused x + y pass (every step; with the plane DFT on window steps)
+    // CUDA-graph replay of repeated runs (see run_steps)
+    bool graphs = true;
+    long long config_version = 0;           // bumped by every call that changes kernel arguments
+    GraphKey seen_key, graph_key;
+    cudaGraphExec_t graph_exec = nullptr;
+    long long graph_launches = 0;
     std::vector<TimedLaunch> timed;
     std::vector<cudaEvent_t> event_pool;
     long long launches = 0;
@@ -603,26 +623,30 @@ pstd_status enqueue_step(pstd_grid* g, const StepArgs<R>& a, unsigned long long 
     return PSTD_OK;
 }
 
-// nsteps leapfrog steps from the grid's current state.  dft = false leaves the running DFT
-// (device sums and host incident phasors) untouched; a non-null `save` receives, in stream
-// order, the state after each step: save + (s + 1) * ncell for step s (batch 1).
-template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft = true, void* save = nullptr)
+// One planned leapfrog step: its kernel arguments and which members accumulate the DFT.
+template <typename R> struct PlannedStep {
+    StepArgs<R> a;
+    DftArgs<R> d[3];
+    unsigned long long mask;
+};
+
+// Host side of nsteps steps from the grid's current state: kernel arguments per step, and the
+// host bookkeeping of the running DFT (incident phasors at r_O, Eq. incpsiphasor), the step
+// counter and the level parity.  dft = false leaves the running DFT untouched.
+template <typename R> void plan_steps(pstd_grid* g, long nsteps, bool dft, long long n0, std::vector<PlannedStep<R>>* out)
 {
-    const long long n0 = g->n;
-    pstd_status st0 = upload_time_factors(g, n0, nsteps);
-    if (st0 != PSTD_OK) return st0;
-    const bool need_src = g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0];
     for (long s = 0; s < nsteps; ++s) {
         unsigned long long mask = 0;
         for (int b = 0; b < g->batch && dft; ++b) {
             const MemberHost& m = g->mem[b];
             if (m.nfreq > 0 && g->n >= m.first && g->n < m.first + m.len) mask |= 1ull << b;
         }
-        DftArgs<R> dx, dy, dz;
+        PlannedStep<R> p;
+        p.mask = mask;
+        if (mask && out) {
+            for (int ax = 0; ax < 3; ++ax) p.d[ax] = dft_args<R>(g, mask, ax);
+        }
         if (mask) {
-            dx = dft_args<R>(g, mask, 0);
-            dy = dft_args<R>(g, mask, 1);
-            dz = dft_args<R>(g, mask, 2);
             const double t = g->n * g->desc.dt;
             for (int b = 0; b < g->batch; ++b) {
                 if (!((mask >> b) & 1ull)) continue;
@@ -633,32 +657,109 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft 
             }
             ++g->phasor_version;
         }
-        // checkpoint recording for the adjoint: steps of the run from rest, recorded from step 0 on
-        if (dft && !save && g->ckpt_record && g->ckpt_contig && g->n == 0) g->ckpt_upto = 0;
-        const bool record = dft && !save && g->ckpt_record && g->ckpt_contig && g->ckpt_upto == g->n;
-        if (record && g->n % g->ckpt_K == 0) {
-            const long slot = (long)(g->n / g->ckpt_K);
-            if (slot < g->ckpt_slots) {
-                const size_t sb = (size_t)g->ncell * g->csize;
-                char* ck = static_cast<char*>(g->adj_ckpt);
-                CK(g, cudaMemcpyAsync(ck + (size_t)(2 * slot) * sb, g->buf[g->cur ^ 1], sb, cudaMemcpyDeviceToDevice, g->stream));
-                CK(g, cudaMemcpyAsync(ck + (size_t)(2 * slot + 1) * sb, g->buf[g->cur], sb, cudaMemcpyDeviceToDevice, g->stream));
-            }
+        if (out) {
+            p.a = step_args<R>(g);
+            p.a.tfac = static_cast<const typename StepArgs<R>::C*>(g->tfac);
+            p.a.tfac_base = n0;
+            p.a.batch = g->batch;
+            out->push_back(p);
         }
-        StepArgs<R> a = step_args<R>(g);
-        a.tfac = static_cast<const typename StepArgs<R>::C*>(g->tfac);
-        a.tfac_base = n0;
-        a.batch = g->batch;
-        pstd_status st = enqueue_step<R>(g, a, mask, &dx, &dy, &dz, need_src);
-        if (st != PSTD_OK) return st;
         g->cur ^= 1;
         ++g->n;
-        if (record) g->ckpt_upto = g->n;
-        if (save)
-            CK(g, cudaMemcpyAsync(static_cast<char*>(save) + (size_t)(s + 1) * g->ncell * g->csize, g->buf[g->cur],
-                                  (size_t)g->ncell * g->csize, cudaMemcpyDeviceToDevice, g->stream));
+    }
+}
+
+// Enqueue planned steps.  With `record` the checkpoints of the run from rest are copied aside
+// before steps n = s K; with `save` the state after each step goes to save + (s + 1) * ncell.
+template <typename R>
+pstd_status enqueue_steps(pstd_grid* g, const std::vector<PlannedStep<R>>& plan, bool record, void* save)
+{
+    const bool need_src = g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0];
+    const size_t sb = (size_t)g->ncell * g->csize;
+    for (size_t s = 0; s < plan.size(); ++s) {
+        const PlannedStep<R>& p = plan[s];
+        const long long n = p.a.step;
+        if (record && n % g->ckpt_K == 0 && n / g->ckpt_K < g->ckpt_slots) {
+            char* ck = static_cast<char*>(g->adj_ckpt);
+            const size_t slot = (size_t)(n / g->ckpt_K);
+            CK(g, cudaMemcpyAsync(ck + 2 * slot * sb, p.a.prev, sb, cudaMemcpyDeviceToDevice, g->stream));
+            CK(g, cudaMemcpyAsync(ck + (2 * slot + 1) * sb, p.a.cur, sb, cudaMemcpyDeviceToDevice, g->stream));
+        }
+        pstd_status st = enqueue_step<R>(g, p.a, p.mask, &p.d[0], &p.d[1], &p.d[2], need_src);
+        if (st != PSTD_OK) return st;
+        if (save) CK(g, cudaMemcpyAsync(static_cast<char*>(save) + (s + 1) * sb, p.a.prev, sb, cudaMemcpyDeviceToDevice, g->stream));
     }
     return PSTD_OK;
+}
+
+void drop_graph(pstd_grid* g)
+{
+    if (g->graph_exec) cudaGraphExecDestroy(g->graph_exec);
+    g->graph_exec = nullptr;
+    g->graph_key.valid = false;
+}
+
+// nsteps leapfrog steps from the grid's current state.  dft = false leaves the running DFT
+// (device sums and host incident phasors) untouched; a non-null `save` receives, in stream
+// order, the state after each step: save + (s + 1) * ncell for step s (batch 1).
+//
+// A run that repeats the previous run's key (first step, count, level parity, table pointers
+// and configuration version: everything the kernel arguments hold) is captured once into a
+// CUDA graph and replayed from then on; the host bookkeeping still runs step by step.
+template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft = true, void* save = nullptr)
+{
+    const long long n0 = g->n;
+    pstd_status st0 = upload_time_factors(g, n0, nsteps);
+    if (st0 != PSTD_OK) return st0;
+    // checkpoint recording for the adjoint: steps of the run from rest, recorded from step 0 on
+    if (dft && !save && g->ckpt_record && g->ckpt_contig && g->n == 0) g->ckpt_upto = 0;
+    const bool record = dft && !save && g->ckpt_record && g->ckpt_contig && g->ckpt_upto == g->n;
+    GraphKey key;
+    key.valid = true;
+    key.n0 = n0;
+    key.nsteps = nsteps;
+    key.cur = g->cur;
+    key.version = g->config_version;
+    key.tfac = g->tfac;
+    key.tenv = g->tenv;
+    const bool graphable = g->graphs && dft && !save && !record && !g->timing && nsteps >= 2;
+    if (graphable && g->graph_exec && g->graph_key == key) {
+        plan_steps<R>(g, nsteps, dft, n0, nullptr);
+        CK(g, cudaGraphLaunch(g->graph_exec, g->stream));
+        g->launches += g->graph_launches;
+        return PSTD_OK;
+    }
+    std::vector<PlannedStep<R>> plan;
+    plan.reserve(nsteps);
+    plan_steps<R>(g, nsteps, dft, n0, &plan);
+    if (record) g->ckpt_upto = g->n;
+    if (graphable && g->seen_key == key) {
+        // second run with this key: capture it
+        drop_graph(g);
+        const long long launches0 = g->launches;
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        if (ok) {
+            const pstd_status st = enqueue_steps<R>(g, plan, false, nullptr);
+            ok = cudaStreamEndCapture(g->stream, &graph) == cudaSuccess && st == PSTD_OK && graph;
+        }
+        cudaGraphExec_t exec = nullptr;
+        if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (ok) {
+            g->graph_exec = exec;
+            g->graph_key = key;
+            g->graph_launches = g->launches - launches0;
+            CK(g, cudaGraphLaunch(exec, g->stream));
+            return PSTD_OK;
+        }
+        // capture is not available here: launch directly from now on
+        cudaGetLastError();
+        g->launches = launches0;
+        g->graphs = false;
+    }
+    g->seen_key = key;
+    return enqueue_steps<R>(g, plan, record, save);
 }
 
 // -------------------------------------------------------------------------------------
@@ -1297,6 +1398,7 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     for (int a = 0; a < 3; ++a)
         for (void* p : {g->tw[a], g->kin[a], g->mask[a], g->zeta[a], g->zeta1[a], g->zeta2[a], g->phase[a], g->dw[a]})
             if (p) cudaFree(p);
+    drop_graph(g);
     for (void* p : {g->tenv, g->proj[0], g->proj[1], g->proj[2]})
         if (p) cudaFree(p);
     for (void* p : {g->adj_table, g->adj_partial, g->adj_rec, g->adj_PA, (void*)g->adj_gpts, (void*)g->adj_out, g->adj_J,
@@ -1342,6 +1444,7 @@ pstd_status pstd_set_potential(pstd_grid* g, const void* V, int mem, int dtype)
 {
     if (!g || !V) return fail(g, PSTD_EINVAL, "null argument");
     DeviceGuard dg(g->dev);
+    ++g->config_version;      // kernel arguments change: no graph replay of earlier runs
     g->ckpt_upto = -1;        // recorded checkpoints belong to the previous potential
     g->ckpt_contig = false;
     if (dtype != PSTD_DTYPE_F32 && dtype != PSTD_DTYPE_F64) return fail(g, PSTD_EINVAL, "dtype");
@@ -1471,6 +1574,7 @@ pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double
 {
     if (!g || !khat) return fail(g, PSTD_EINVAL, "null argument");
     DeviceGuard dg(g->dev);
+    ++g->config_version;      // kernel arguments change: no graph replay of earlier runs
     g->ckpt_upto = -1;        // recorded checkpoints belong to the previous incidence
     g->ckpt_contig = false;
     pstd_status st = check_member(g, b);
@@ -1490,6 +1594,7 @@ pstd_status pstd_set_incidence_packet(pstd_grid* g, int b, const double khat[3],
 {
     if (!g || !khat) return fail(g, PSTD_EINVAL, "null argument");
     DeviceGuard dg(g->dev);
+    ++g->config_version;      // kernel arguments change: no graph replay of earlier runs
     g->ckpt_upto = -1;
     g->ckpt_contig = false;
     pstd_status st = check_member(g, b);
@@ -1512,6 +1617,7 @@ pstd_status pstd_huygens_dft(pstd_grid* g, int b, const double* omega, int nfreq
 {
     if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
     DeviceGuard dg(g->dev);
+    ++g->config_version;      // kernel arguments change: no graph replay of earlier runs
     if (nfreq < 0 || nfreq > PSTD_MAX_FREQ || (nfreq > 0 && !omega)) return fail(g, PSTD_EINVAL, "nfreq");
     if (first_step < 0 || n_steps < 0) return fail(g, PSTD_EINVAL, "window");
     if (b < -1 || b >= g->batch) return fail(g, PSTD_EINVAL, "batch member out of range");
@@ -1889,6 +1995,7 @@ pstd_status pstd_set_checkpointing(pstd_grid* g, long interval, long max_steps)
     if (interval < 0 || max_steps < 0) return fail(g, PSTD_EINVAL, "interval / max_steps");
     if (interval > 0 && g->batch != 1) return fail(g, PSTD_EINVAL, "checkpoints are recorded on grids with batch 1");
     DeviceGuard dg(g->dev);
+    ++g->config_version;      // kernel arguments change: no graph replay of earlier runs
     g->ckpt_upto = -1;
     if (interval == 0) {
         g->ckpt_record = false;
@@ -1901,5 +2008,16 @@ pstd_status pstd_set_checkpointing(pstd_grid* g, long interval, long max_steps)
     g->ckpt_record = true;
     g->ckpt_K = interval;
     g->ckpt_slots = (long)(g->adj_ckpt_cap / (2 * sbytes));
+    return PSTD_OK;
+}
+
+pstd_status pstd_set_graphs(pstd_grid* g, int enable)
+{
+    if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
+    DeviceGuard dg(g->dev);
+    CK(g, cudaStreamSynchronize(g->stream));
+    g->graphs = enable != 0;
+    drop_graph(g);
+    g->seen_key.valid = false;
     return PSTD_OK;
 }

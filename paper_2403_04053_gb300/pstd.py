@@ -70,6 +70,7 @@ _SIGS = {
     "pstd_adjoint_gradient": (c_int, [c_void_p, c_long, c_void_p, POINTER(c_int), POINTER(c_int), c_long, c_void_p, c_int]),
     "pstd_set_checkpointing": (c_int, [c_void_p, c_long, c_long]),
     "pstd_set_incidence_packet": (c_int, [c_void_p, c_int, POINTER(c_double), c_double, c_double, c_double]),
+    "pstd_set_graphs": (c_int, [c_void_p, c_int]),
 }
 
 _lib = None
@@ -286,6 +287,10 @@ class Grid:
                                                 g.ctypes.data_as(c_void_p), out.ctypes.data_as(c_void_p), MEM_HOST),
                 "pstd_transform_adjoint")
         return self.split_phasors(out)
+
+    def set_graphs(self, enable: bool):
+        """CUDA-graph replay of repeated step() runs (pstd_set_graphs; on by default)."""
+        self._c(self.lib.pstd_set_graphs(self.h, 1 if enable else 0), "pstd_set_graphs")
 
     def set_checkpointing(self, interval: int, max_steps: int):
         """Record adjoint checkpoints during step() (pstd_set_checkpointing); interval 0 stops."""

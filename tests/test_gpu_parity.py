@@ -544,3 +544,42 @@ def test_packet_call_errors():
         with pytest.raises(pstd.PstdError) as e:
             g.adjoint_gradient(10, [np.zeros(g.phasor_count() * pstd.MAX_FREQ)], (0, 0, 0), (4, 4, 4))
         assert e.value.code == "EINVAL"        # the adjoint supports the CW incidence
+
+
+# ----------------------------------------------------------------------------------
+# CUDA-graph replay of repeated runs
+# ----------------------------------------------------------------------------------
+def _windowed_runs(spec, V, graphs, passes, V_after=None):
+    out = []
+    with pstd.Grid(spec, precision=pstd.F32) as g:
+        g.set_graphs(graphs)
+        g.set_potential(V)
+        g.set_incidence(0, (0.3, -0.5, 0.81), K, 0.05)
+        g.huygens_dft(0, [E0], 10, 10)
+        for p in range(passes):
+            if V_after is not None and p == passes - 1:
+                g.set_potential(V_after)
+            g.reset()
+            g.step(30)
+            out.append((g.get_field(0), g.join_phasors(g.get_phasors(0, 0)), g.launch_count()))
+    return out
+
+
+def test_graph_replay_matches_direct_launches():
+    # pass 1 launches directly, pass 2 is captured, pass 3 replays the graph
+    spec = ONE_STEP_SPECS["square-64x64x48"]("exact")
+    V = random_core_V(spec, 4)
+    direct = _windowed_runs(spec, V, False, 3)
+    graphed = _windowed_runs(spec, V, True, 3)
+    for (s0, p0, _), (s1, p1, _) in zip(direct, graphed):
+        assert np.array_equal(s0, s1) and np.array_equal(p0, p1)
+    # the replayed passes count the same kernel launches as the direct ones
+    assert [n for _, _, n in direct] == [n for _, _, n in graphed]
+
+
+def test_graph_is_not_replayed_after_a_new_potential():
+    spec = ONE_STEP_SPECS["square-64x64x48"]("exact")
+    V1, V2 = random_core_V(spec, 4), random_core_V(spec, 5)
+    graphed = _windowed_runs(spec, V1, True, 3, V_after=V2)
+    fresh = _windowed_runs(spec, V2, False, 1)
+    assert np.array_equal(graphed[-1][0], fresh[0][0]) and np.array_equal(graphed[-1][1], fresh[0][1])
