@@ -260,6 +260,20 @@ pstd_status pstd_set_checkpointing(pstd_grid* g, long interval, long max_steps);
  * checkpoint recording is on; if capture is unavailable the grid falls back to direct launches.
  * enable = 0 turns it off (and drops a captured graph); synchronises. */
 pstd_status pstd_set_graphs(pstd_grid* g, int enable);
+/* Number of pstd_step calls of g that ran as one CUDA-graph launch. */
+pstd_status pstd_graph_replays(pstd_grid* g, long* count);
+
+/* Step-kernel variants: the tile shape of the x and y transforms (fused: one CTA applies
+ * K_x + K_y to a whole z plane in shared memory; separate: 1-D line passes) and, for 192- and
+ * 256-point y lines, the pipelined y pass (the next tile staged with cp.async while the current
+ * one is transformed).  All variants compute the same step.  pstd_set_variants forces them
+ * (EINVAL where a variant does not exist for the grid: fused needs FP32 square 64/96/128
+ * planes, pipelined FP32 192/256-point y lines); pstd_autotune times trial_steps steps of
+ * every available combination from the grid's current state, keeps the fastest and puts the
+ * state back (step counter included; the running DFT is not touched).  out_variants (may be
+ * NULL): {fused_xy, pipelined_y} chosen.  Both synchronise. */
+pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int pipelined_y);
+pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants);
 
 /* Message of the last failure on g (or of the last failed pstd_create_grid when g is NULL). */
 const char* pstd_last_error(const pstd_grid* g);

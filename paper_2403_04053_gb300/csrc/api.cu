@@ -186,12 +186,15 @@ struct pstd_grid {
     // instrumentation
     bool timing = false;
     bool use_xy = false;                    // fused x + y pass (every step; with the plane DFT on window steps)
+    bool pipe_y = false;                    // pipelined y pass (192/256-point lines)
     // CUDA-graph replay of repeated runs (see run_steps)
     bool graphs = true;
     long long config_version = 0;           // bumped by every call that changes kernel arguments
     GraphKey seen_key, graph_key;
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_launches = 0;
+    long long graph_replays = 0;            // pstd_step calls run as one graph launch
+    cudaStream_t cap_stream = nullptr;      // private stream for graph capture
     std::vector<TimedLaunch> timed;
     std::vector<cudaEvent_t> event_pool;
     long long launches = 0;
@@ -506,6 +509,7 @@ template <typename R> StepArgs<R> step_args(pstd_grid* g)
     a.mode = g->desc.tfsf_mode;
     a.flag = g->flag;
     a.packet_mask = g->packet_mask;
+    a.pipe_y = g->pipe_y ? 1 : 0;
     for (int ax = 0; ax < 3; ++ax) a.proj[ax] = static_cast<const R*>(g->proj[ax]);
     a.tenv = static_cast<const R*>(g->tenv);
     return a;
@@ -727,6 +731,7 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft 
         plan_steps<R>(g, nsteps, dft, n0, nullptr);
         CK(g, cudaGraphLaunch(g->graph_exec, g->stream));
         g->launches += g->graph_launches;
+        ++g->graph_replays;
         return PSTD_OK;
     }
     std::vector<PlannedStep<R>> plan;
@@ -735,13 +740,19 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft 
     if (record) g->ckpt_upto = g->n;
     if (graphable && g->seen_key == key) {
         // second run with this key: capture it
+        // (captured on a private stream: the grid's stream may be the legacy default stream,
+        // which cannot be captured; nothing executes during capture)
         drop_graph(g);
         const long long launches0 = g->launches;
         cudaGraph_t graph = nullptr;
-        bool ok = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        bool ok = g->cap_stream || cudaStreamCreateWithFlags(&g->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+        cudaStream_t real = g->stream;
+        if (ok) ok = cudaStreamBeginCapture(g->cap_stream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
         if (ok) {
+            g->stream = g->cap_stream;
             const pstd_status st = enqueue_steps<R>(g, plan, false, nullptr);
-            ok = cudaStreamEndCapture(g->stream, &graph) == cudaSuccess && st == PSTD_OK && graph;
+            g->stream = real;
+            ok = cudaStreamEndCapture(g->cap_stream, &graph) == cudaSuccess && st == PSTD_OK && graph;
         }
         cudaGraphExec_t exec = nullptr;
         if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
@@ -751,6 +762,7 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft 
             g->graph_key = key;
             g->graph_launches = g->launches - launches0;
             CK(g, cudaGraphLaunch(exec, g->stream));
+            ++g->graph_replays;
             return PSTD_OK;
         }
         // capture is not available here: launch directly from now on
@@ -1321,6 +1333,7 @@ pstd_status pstd_create_grid(const pstd_grid_desc* desc, pstd_grid** out)
     g->stream = static_cast<cudaStream_t>(desc->stream);
     g->prec = desc->precision;
     g->use_xy = g->prec == PSTD_F32 ? xypass_available<float>(desc->n[0], desc->n[1]) : false;
+    g->pipe_y = g->prec == PSTD_F32 ? pipe_y_available<float>(desc->n[1]) : false;
     g->rsize = g->prec == PSTD_F64 ? 8 : 4;
     g->csize = 2 * g->rsize;
     g->ncell = (long long)desc->n[0] * desc->n[1] * desc->n[2];
@@ -1399,6 +1412,7 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
         for (void* p : {g->tw[a], g->kin[a], g->mask[a], g->zeta[a], g->zeta1[a], g->zeta2[a], g->phase[a], g->dw[a]})
             if (p) cudaFree(p);
     drop_graph(g);
+    if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     for (void* p : {g->tenv, g->proj[0], g->proj[1], g->proj[2]})
         if (p) cudaFree(p);
     for (void* p : {g->adj_table, g->adj_partial, g->adj_rec, g->adj_PA, (void*)g->adj_gpts, (void*)g->adj_out, g->adj_J,
@@ -2019,5 +2033,94 @@ pstd_status pstd_set_graphs(pstd_grid* g, int enable)
     g->graphs = enable != 0;
     drop_graph(g);
     g->seen_key.valid = false;
+    return PSTD_OK;
+}
+
+namespace {
+bool xy_possible(const pstd_grid* g) { return g->prec == PSTD_F32 && xypass_available<float>(g->desc.n[0], g->desc.n[1]); }
+bool pipe_possible(const pstd_grid* g) { return g->prec == PSTD_F32 && pipe_y_available<float>(g->desc.n[1]); }
+}  // namespace
+
+pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int pipelined_y)
+{
+    if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
+    if ((fused_xy && !xy_possible(g)) || (pipelined_y && !pipe_possible(g)))
+        return fail(g, PSTD_EINVAL, "variant not available for this grid");
+    DeviceGuard dg(g->dev);
+    ++g->config_version;
+    g->use_xy = fused_xy != 0;
+    g->pipe_y = pipelined_y != 0;
+    return PSTD_OK;
+}
+
+pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants)
+{
+    if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
+    if (trial_steps < 1) return fail(g, PSTD_EINVAL, "trial_steps");
+    DeviceGuard dg(g->dev);
+    for (int b = 0; b < g->batch; ++b)
+        if (!g->mem[b].has_inc) return fail(g, PSTD_ESTATE, "every batch member needs its incidence before tuning");
+    // the trials step a copy of the current state (no DFT); the state is put back afterwards
+    const size_t sbytes = (size_t)g->batch * g->ncell * g->csize;
+    void* saved = nullptr;
+    if (dalloc(&saved, 2 * sbytes) != cudaSuccess) return fail(g, PSTD_ENOMEM, "tuning copy");
+    const long long n_saved = g->n;
+    const int cur_saved = g->cur;
+    const bool timing_saved = g->timing;
+    g->timing = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    pstd_status st = PSTD_OK;
+    float best = -1;
+    int best_xy = g->use_xy, best_pipe = g->pipe_y;
+    auto restore = [&]() -> pstd_status {
+        CK(g, cudaMemcpyAsync(g->buf[0], saved, sbytes, cudaMemcpyDeviceToDevice, g->stream));
+        CK(g, cudaMemcpyAsync(g->buf[1], static_cast<char*>(saved) + sbytes, sbytes, cudaMemcpyDeviceToDevice, g->stream));
+        g->n = n_saved;
+        g->cur = cur_saved;
+        return PSTD_OK;
+    };
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = fail(g, PSTD_ECUDA, "events");
+    if (st == PSTD_OK) {
+        cudaMemcpyAsync(saved, g->buf[0], sbytes, cudaMemcpyDeviceToDevice, g->stream);
+        cudaMemcpyAsync(static_cast<char*>(saved) + sbytes, g->buf[1], sbytes, cudaMemcpyDeviceToDevice, g->stream);
+    }
+    for (int xy = xy_possible(g) ? 1 : 0; xy >= 0 && st == PSTD_OK; --xy)
+        for (int pp = pipe_possible(g) ? 1 : 0; pp >= 0 && st == PSTD_OK; --pp) {
+            g->use_xy = xy;
+            g->pipe_y = pp;
+            st = restore();
+            if (st != PSTD_OK) break;
+            st = g->prec == PSTD_F64 ? run_steps<double>(g, 2, false) : run_steps<float>(g, 2, false);   // warm-up
+            if (st != PSTD_OK) break;
+            cudaEventRecord(e0, g->stream);
+            st = g->prec == PSTD_F64 ? run_steps<double>(g, trial_steps, false) : run_steps<float>(g, trial_steps, false);
+            if (st != PSTD_OK) break;
+            cudaEventRecord(e1, g->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(g, PSTD_ECUDA, "tuning events"); break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (best < 0 || ms < best) { best = ms; best_xy = xy; best_pipe = pp; }
+        }
+    const pstd_status rs = restore();
+    if (st == PSTD_OK) st = rs;
+    CK(g, cudaStreamSynchronize(g->stream));
+    cudaFree(saved);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    g->timing = timing_saved;
+    g->use_xy = best_xy;
+    g->pipe_y = best_pipe;
+    ++g->config_version;
+    if (out_variants) {
+        out_variants[0] = g->use_xy ? 1 : 0;
+        out_variants[1] = g->pipe_y ? 1 : 0;
+    }
+    return st;
+}
+
+pstd_status pstd_graph_replays(pstd_grid* g, long* count)
+{
+    if (!g || !count) return fail(g, PSTD_EINVAL, "null argument");
+    *count = (long)g->graph_replays;
     return PSTD_OK;
 }

@@ -8,6 +8,7 @@ template cudaError_t launch_ypass<float>(const StepArgs<float>&, const DftArgs<f
 template cudaError_t launch_zpass<float>(const StepArgs<float>&, const DftArgs<float>*, bool, int, cudaStream_t);
 template cudaError_t launch_source<float>(const StepArgs<float>&, int, cudaStream_t);
 template bool xypass_available<float>(int, int);
+template bool pipe_y_available<float>(int);
 template cudaError_t launch_xypass<float>(const StepArgs<float>&, const DftArgs<float>*, const DftArgs<float>*, int, cudaStream_t);
 template cudaError_t launch_transform<float>(const TransformArgs<float>&, int, int, cudaStream_t);
 template cudaError_t launch_farfield<float>(const FarArgs<float>&, cudaStream_t);

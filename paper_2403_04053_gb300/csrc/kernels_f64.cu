@@ -8,6 +8,7 @@ template cudaError_t launch_ypass<double>(const StepArgs<double>&, const DftArgs
 template cudaError_t launch_zpass<double>(const StepArgs<double>&, const DftArgs<double>*, bool, int, cudaStream_t);
 template cudaError_t launch_source<double>(const StepArgs<double>&, int, cudaStream_t);
 template bool xypass_available<double>(int, int);
+template bool pipe_y_available<double>(int);
 template cudaError_t launch_xypass<double>(const StepArgs<double>&, const DftArgs<double>*, const DftArgs<double>*, int, cudaStream_t);
 template cudaError_t launch_transform<double>(const TransformArgs<double>&, int, int, cudaStream_t);
 template cudaError_t launch_farfield<double>(const FarArgs<double>&, cudaStream_t);

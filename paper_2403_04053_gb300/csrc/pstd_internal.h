@@ -46,6 +46,7 @@ template <typename R> struct StepArgs {
     R c2;                    // 2 dt / hbar, rounded once on the host
     R h2m;                   // hbar^2 / 2m
     int mode;                // PSTD_TFSF_EXACT / PSTD_TFSF_PAPER
+    int pipe_y;              // pipelined y pass where available (chosen by the autotuner)
     int* flag;               // bit 0: non-finite value written
     const C* tfac;           // a(t_n) e^{-i w0 t_n}: [(n - tfac_base) * batch + member], evaluated in FP64 on the host
     long long tfac_base;
@@ -90,6 +91,7 @@ template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, const DftAr
 template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch, cudaStream_t s);
 // fused x + y pass (one CTA per z plane); available for FP32 square planes of 64, 96, 128
 template <typename R> bool xypass_available(int nx, int ny);
+template <typename R> bool pipe_y_available(int ny);
 template <typename R>
 cudaError_t launch_xypass(const StepArgs<R>& a, const DftArgs<R>* dx, const DftArgs<R>* dy, int batch, cudaStream_t s);
 

@@ -762,7 +762,7 @@ template <typename R, int N, int AXIS, bool SRC> cudaError_t colpass_pipe_n(cons
 template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
     if constexpr (pipe_supported<R, N>())
-        if (!d) return colpass_pipe_n<R, N, 1, false>(a, batch, s);
+        if (!d && a.pipe_y) return colpass_pipe_n<R, N, 1, false>(a, batch, s);
     const size_t sm = pass_smem<R, N>();
     cudaError_t e = d ? set_smem_once<ypass_kernel<R, N, true>>(sm) : set_smem_once<ypass_kernel<R, N, false>>(sm);
     if (e != cudaSuccess) return e;
@@ -837,6 +837,11 @@ template <typename R>
 cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, bool src, int batch, cudaStream_t s)
 {
     PSTD_SIZE_DISPATCH(zpass_n, a.nz, a, d, src, batch, s)
+}
+// pipelined y pass: FP32, 192- or 256-point y lines
+template <typename R> bool pipe_y_available(int ny)
+{
+    return (ny == 192 && pipe_supported<R, 192>()) || (ny == 256 && pipe_supported<R, 256>());
 }
 // fused xy pass: FP32, square planes of 64, 96 or 128 (one CTA per plane)
 template <typename R> bool xypass_available(int nx, int ny)

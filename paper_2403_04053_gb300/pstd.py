@@ -71,6 +71,9 @@ _SIGS = {
     "pstd_set_checkpointing": (c_int, [c_void_p, c_long, c_long]),
     "pstd_set_incidence_packet": (c_int, [c_void_p, c_int, POINTER(c_double), c_double, c_double, c_double]),
     "pstd_set_graphs": (c_int, [c_void_p, c_int]),
+    "pstd_graph_replays": (c_int, [c_void_p, POINTER(c_long)]),
+    "pstd_set_variants": (c_int, [c_void_p, c_int, c_int]),
+    "pstd_autotune": (c_int, [c_void_p, c_long, POINTER(c_int)]),
 }
 
 _lib = None
@@ -287,6 +290,22 @@ class Grid:
                                                 g.ctypes.data_as(c_void_p), out.ctypes.data_as(c_void_p), MEM_HOST),
                 "pstd_transform_adjoint")
         return self.split_phasors(out)
+
+    def set_variants(self, fused_xy: bool, pipelined_y: bool):
+        """Force the step-kernel variants (pstd_set_variants)."""
+        self._c(self.lib.pstd_set_variants(self.h, int(bool(fused_xy)), int(bool(pipelined_y))), "pstd_set_variants")
+
+    def autotune(self, trial_steps: int = 20):
+        """Time the available step-kernel variants and keep the fastest (pstd_autotune);
+        returns {"fused_xy": bool, "pipelined_y": bool}."""
+        out = (c_int * 2)()
+        self._c(self.lib.pstd_autotune(self.h, int(trial_steps), out), "pstd_autotune")
+        return {"fused_xy": bool(out[0]), "pipelined_y": bool(out[1])}
+
+    def graph_replays(self) -> int:
+        n = c_long()
+        self._c(self.lib.pstd_graph_replays(self.h, byref(n)), "pstd_graph_replays")
+        return n.value
 
     def set_graphs(self, enable: bool):
         """CUDA-graph replay of repeated step() runs (pstd_set_graphs; on by default)."""

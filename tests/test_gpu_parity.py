@@ -562,6 +562,7 @@ def _windowed_runs(spec, V, graphs, passes, V_after=None):
             g.reset()
             g.step(30)
             out.append((g.get_field(0), g.join_phasors(g.get_phasors(0, 0)), g.launch_count()))
+        out.append(g.graph_replays())
     return out
 
 
@@ -571,10 +572,11 @@ def test_graph_replay_matches_direct_launches():
     V = random_core_V(spec, 4)
     direct = _windowed_runs(spec, V, False, 3)
     graphed = _windowed_runs(spec, V, True, 3)
-    for (s0, p0, _), (s1, p1, _) in zip(direct, graphed):
+    assert direct[-1] == 0 and graphed[-1] == 2        # passes 2 and 3 ran as graph launches
+    for (s0, p0, _), (s1, p1, _) in zip(direct[:-1], graphed[:-1]):
         assert np.array_equal(s0, s1) and np.array_equal(p0, p1)
     # the replayed passes count the same kernel launches as the direct ones
-    assert [n for _, _, n in direct] == [n for _, _, n in graphed]
+    assert [n for _, _, n in direct[:-1]] == [n for _, _, n in graphed[:-1]]
 
 
 def test_graph_is_not_replayed_after_a_new_potential():
@@ -582,4 +584,44 @@ def test_graph_is_not_replayed_after_a_new_potential():
     V1, V2 = random_core_V(spec, 4), random_core_V(spec, 5)
     graphed = _windowed_runs(spec, V1, True, 3, V_after=V2)
     fresh = _windowed_runs(spec, V2, False, 1)
-    assert np.array_equal(graphed[-1][0], fresh[0][0]) and np.array_equal(graphed[-1][1], fresh[0][1])
+    assert graphed[-1] == 1                            # only pass 2 replayed; pass 3 had a new V
+    assert np.array_equal(graphed[-2][0], fresh[0][0]) and np.array_equal(graphed[-2][1], fresh[0][1])
+
+
+# ----------------------------------------------------------------------------------
+# step-kernel variants and the autotuner
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("name,variants", [("square-64x64x48", (True, False)), ("square-64x64x48", (False, False)),
+                                           ("pipe-16x192x256", (False, True)), ("pipe-16x192x256", (False, False))])
+def test_every_variant_matches_oracle(name, variants):
+    spec = ONE_STEP_SPECS[name]("exact")
+    V = random_core_V(spec, 3)
+    khat = (0.3, -0.5, 0.81)
+    prev = inputs.random_field(spec.shape, 5)
+    cur = inputs.random_field(spec.shape, 6)
+    sim = po.Simulation(spec, V, khat, K, 0.05)
+    sim.prev, sim.cur, sim.n = prev.copy(), cur.copy(), 17
+    sim.step(1)
+    with pstd.Grid(spec, precision=pstd.F32) as g:
+        g.set_variants(*variants)
+        g.set_potential(V)
+        g.set_incidence(0, khat, K, 0.05)
+        g.set_field(0, prev.astype(np.complex64), cur.astype(np.complex64), 17)
+        g.step(1)
+        assert rel(g.get_field(0), sim.cur) < 2e-6
+
+
+def test_autotune_keeps_the_state_and_picks_available_variants():
+    spec = ONE_STEP_SPECS["square-64x64x48"]("exact")
+    V = random_core_V(spec, 3)
+    with pstd.Grid(spec, precision=pstd.F32) as g:
+        g.set_potential(V)
+        g.set_incidence(0, (0.3, -0.5, 0.81), K, 0.05)
+        g.step(7)
+        before, n = g.get_field(0), g.get_step()
+        chosen = g.autotune(10)
+        assert chosen["pipelined_y"] is False            # not available for 64-point y lines
+        assert g.get_step() == n and np.array_equal(g.get_field(0), before)
+        with pytest.raises(pstd.PstdError) as e:
+            g.set_variants(False, True)
+        assert e.value.code == "EINVAL"
