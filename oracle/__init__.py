@@ -14,6 +14,8 @@ Modules
                 sum of Eqs. bottomPsi_lm ... Psi, and its far-field limit
   analytic    : textbook closed forms that pin the oracle (partial waves, Born,
                 spherical wave, leapfrog mode evolution)
+  spinor_oracle : the two-component leapfrog with a gamma sigma . B coupling (EXACT form),
+                pinned by its exact splitting into two scalar problems for B = b(r) nhat
   adjoint_oracle : the discrete adjoint (transpose) of the leapfrog run, of the running
                 DFT and of the surface transform, and the gradient of a Fresnel-field
                 magnitude misfit with respect to V (no counterpart in the paper; pinned by
