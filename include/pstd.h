@@ -132,6 +132,23 @@ pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double
  * EINVAL for b out of range, k <= 0, sigma <= 0, khat = 0. */
 pstd_status pstd_set_incidence_packet(pstd_grid* g, int b, const double khat[3], double k, double sigma, double d0);
 
+/* Spin-dependent scattering (the paper's motivating magnetic case; the paper itself treats a
+ * scalar wave function): the grid's batch members pair up as the spin-up and spin-down
+ * components (2p, 2p + 1) of spinors p, coupled by W = V I + gamma sigma . B(r),
+ *   sigma . B = [[Bz, Bx - i By], [Bx + i By, -Bz]],
+ * in the EXACT TF/SF form (W (u + chi psi_inc)).  Bx, By, Bz: real full-grid arrays like V;
+ * B must vanish where zeta < 1, and dt must satisfy Eq. PSTDstability with |V|max +
+ * |gamma| |B|max (EUNSTABLE).  EINVAL for an odd batch, the PAPER form or packet members. */
+pstd_status pstd_set_magnetic_field(pstd_grid* g, const void* Bx, const void* By, const void* Bz, double gamma, int mem,
+                                    int dtype);
+
+/* CW incidence of spinor p (members 2p, 2p + 1): the plane wave of pstd_set_incidence times the
+ * spin state chi = (chi[0] + i chi[1], chi[2] + i chi[3]) (up, down).  Each component's phasors
+ * are scaled by the scalar plane wave's incident phasor at r_O, so that the transforms give the
+ * spin-resolved amplitudes (spin flip included) for the incident spin state chi. */
+pstd_status pstd_set_incidence_spinor(pstd_grid* g, int p, const double khat[3], double k, double ramp_time,
+                                      const double chi[4]);
+
 /* Zero both time levels, the step counter and every DFT accumulator of all members. */
 pstd_status pstd_reset(pstd_grid* g);
 

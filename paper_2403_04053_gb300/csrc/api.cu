@@ -40,6 +40,7 @@ struct MemberHost {
     cd inc_phasor[PSTD_MAX_FREQ];
     bool packet = false;         // Gaussian wave packet (pstd_set_incidence_packet)
     double sigma = 1.0, d0 = 0.0;
+    cd chi = cd(1.0, 0.0);       // spinor component's incident amplitude (pstd_set_incidence_spinor)
 };
 
 // The incident wave of member m at the first-contact corner r_O at time t (Eq. incpsiphasor's
@@ -99,6 +100,11 @@ struct pstd_grid {
     void* phase[3] = {};
     void* dw[3] = {};
     void* V = nullptr;
+    // spinor grids (pstd_set_magnetic_field): gamma B on its support box, components = member pairs
+    bool spinor = false;
+    void* B[3] = {};
+    int blo[3] = {0, 0, 0}, bhi[3] = {0, 0, 0};
+    double gamma_b = 0, bmax = 0;
     int vlo[3] = {0, 0, 0}, vhi[3] = {0, 0, 0};
     double vmax = 0;
     bool mask_ready = false;
@@ -510,6 +516,13 @@ template <typename R> StepArgs<R> step_args(pstd_grid* g)
     a.flag = g->flag;
     a.packet_mask = g->packet_mask;
     a.pipe_y = g->pipe_y ? 1 : 0;
+    a.spinor = g->spinor ? 1 : 0;
+    for (int ax = 0; ax < 3; ++ax) {
+        a.B[ax] = static_cast<const R*>(g->B[ax]);
+        a.blo[ax] = g->blo[ax];
+        a.bhi[ax] = g->bhi[ax];
+    }
+    a.gamma = R(g->gamma_b);
     for (int ax = 0; ax < 3; ++ax) a.proj[ax] = static_cast<const R*>(g->proj[ax]);
     a.tenv = static_cast<const R*>(g->tenv);
     return a;
@@ -560,14 +573,14 @@ pstd_status upload_time_factors(pstd_grid* g, long long n0, long nsteps)
                 any_packet = true;
                 const double tau = g->desc.hbar * t / (2.0 * g->desc.mass * m.sigma * m.sigma);
                 const cd q(1.0, tau);
-                tab[(size_t)s * g->batch + b] = std::pow(q, -0.5) * std::exp(cd(0.0, -m.w0 * t - m.k * m.d0));
+                tab[(size_t)s * g->batch + b] = m.chi * std::pow(q, -0.5) * std::exp(cd(0.0, -m.w0 * t - m.k * m.d0));
                 const cd alpha = 1.0 / (4.0 * m.sigma * m.sigma * q);
                 double* e = &env[3 * ((size_t)s * g->batch + b)];
                 e[0] = alpha.real();
                 e[1] = alpha.imag();
                 e[2] = m.d0 + g->desc.hbar * m.k / g->desc.mass * t;
             } else {
-                tab[(size_t)s * g->batch + b] = incident_at_origin(m, t, g->desc.hbar, g->desc.mass);
+                tab[(size_t)s * g->batch + b] = m.chi * incident_at_origin(m, t, g->desc.hbar, g->desc.mass);
             }
         }
     }
@@ -678,7 +691,7 @@ template <typename R> void plan_steps(pstd_grid* g, long nsteps, bool dft, long 
 template <typename R>
 pstd_status enqueue_steps(pstd_grid* g, const std::vector<PlannedStep<R>>& plan, bool record, void* save)
 {
-    const bool need_src = g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0];
+    const bool need_src = g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0] || (g->spinor && g->bhi[0] > g->blo[0]);
     const size_t sb = (size_t)g->ncell * g->csize;
     for (size_t s = 0; s < plan.size(); ++s) {
         const PlannedStep<R>& p = plan[s];
@@ -1413,6 +1426,8 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
             if (p) cudaFree(p);
     drop_graph(g);
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
+    for (void* p : {g->B[0], g->B[1], g->B[2]})
+        if (p) cudaFree(p);
     for (void* p : {g->tenv, g->proj[0], g->proj[1], g->proj[2]})
         if (p) cudaFree(p);
     for (void* p : {g->adj_table, g->adj_partial, g->adj_rec, g->adj_PA, (void*)g->adj_gpts, (void*)g->adj_out, g->adj_J,
@@ -1499,7 +1514,8 @@ pstd_status pstd_set_potential(pstd_grid* g, const void* V, int mem, int dtype)
                 lo[2] = std::min(lo[2], k); hi[2] = std::max(hi[2], k);
                 vmax = std::max(vmax, std::fabs(v));
             }
-    if (d.dt > dt_bound(d, vmax)) return fail(g, PSTD_EUNSTABLE, "dt above the stability bound with this |V|max (Eq. PSTDstability)");
+    if (d.dt > dt_bound(d, vmax + std::fabs(g->gamma_b) * g->bmax))
+        return fail(g, PSTD_EUNSTABLE, "dt above the stability bound with this |V|max (Eq. PSTDstability)");
     std::vector<double> box;
     if (hi[0] < 0) {   // V == 0 everywhere
         for (int a = 0; a < 3; ++a) { g->vlo[a] = 0; g->vhi[a] = 0; }
@@ -1595,11 +1611,13 @@ pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double
     if (st != PSTD_OK) return st;
     if (envelope != PSTD_ENV_CW_RAMP) return fail(g, PSTD_EINVAL, "envelope");
     if (!(ramp_time >= 0)) return fail(g, PSTD_EINVAL, "ramp_time");
+    if (g->spinor) return fail(g, PSTD_EINVAL, "spinor grids take pstd_set_incidence_spinor");
     st = set_incidence_common(g, b, khat, k);
     if (st != PSTD_OK) return st;
     MemberHost& m = g->mem[b];
     m.ramp = ramp_time;
     m.packet = false;
+    m.chi = cd(1.0, 0.0);
     g->packet_mask &= ~(1ull << b);
     return upload_members(g);
 }
@@ -1616,11 +1634,13 @@ pstd_status pstd_set_incidence_packet(pstd_grid* g, int b, const double khat[3],
     if (!(sigma > 0) || !std::isfinite(d0)) return fail(g, PSTD_EINVAL, "sigma or d0");
     if (g->desc.tfsf_mode != PSTD_TFSF_EXACT)
         return fail(g, PSTD_EINVAL, "wave-packet incidence needs the EXACT TF/SF form (V (psi + psi_inc))");
+    if (g->spinor) return fail(g, PSTD_EINVAL, "spinor grids take pstd_set_incidence_spinor");
     st = set_incidence_common(g, b, khat, k);
     if (st != PSTD_OK) return st;
     MemberHost& m = g->mem[b];
     m.ramp = 0.0;
     m.packet = true;
+    m.chi = cd(1.0, 0.0);
     m.sigma = sigma;
     m.d0 = d0;
     g->packet_mask |= 1ull << b;
@@ -2123,4 +2143,120 @@ pstd_status pstd_graph_replays(pstd_grid* g, long* count)
     if (!g || !count) return fail(g, PSTD_EINVAL, "null argument");
     *count = (long)g->graph_replays;
     return PSTD_OK;
+}
+
+namespace {
+// a real full-grid array ([z][y][x], f32/f64, host or device) into host doubles
+pstd_status read_grid_array(pstd_grid* g, const void* src, int mem, int dtype, std::vector<double>& h)
+{
+    const size_t n = (size_t)g->ncell;
+    h.resize(n);
+    if (dtype != PSTD_DTYPE_F32 && dtype != PSTD_DTYPE_F64) return fail(g, PSTD_EINVAL, "dtype");
+    if (mem == PSTD_MEM_HOST) {
+        if (dtype == PSTD_DTYPE_F64) std::memcpy(h.data(), src, n * 8);
+        else for (size_t i = 0; i < n; ++i) h[i] = static_cast<const float*>(src)[i];
+    } else if (mem == PSTD_MEM_DEVICE) {
+        CK(g, cudaStreamSynchronize(g->stream));
+        if (dtype == PSTD_DTYPE_F64) {
+            CK(g, cudaMemcpy(h.data(), src, n * 8, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> f(n);
+            CK(g, cudaMemcpy(f.data(), src, n * 4, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < n; ++i) h[i] = f[i];
+        }
+    } else {
+        return fail(g, PSTD_EINVAL, "mem");
+    }
+    return PSTD_OK;
+}
+}  // namespace
+
+pstd_status pstd_set_magnetic_field(pstd_grid* g, const void* Bx, const void* By, const void* Bz, double gamma, int mem,
+                                    int dtype)
+{
+    if (!g || !Bx || !By || !Bz) return fail(g, PSTD_EINVAL, "null argument");
+    DeviceGuard dg(g->dev);
+    ++g->config_version;
+    g->ckpt_upto = -1;
+    g->ckpt_contig = false;
+    if (g->batch % 2) return fail(g, PSTD_EINVAL, "spinor grids pair the batch members: the batch must be even");
+    if (g->desc.tfsf_mode != PSTD_TFSF_EXACT) return fail(g, PSTD_EINVAL, "spinor grids use the EXACT TF/SF form");
+    if (!std::isfinite(gamma)) return fail(g, PSTD_EINVAL, "gamma");
+    if (g->packet_mask) return fail(g, PSTD_EINVAL, "spinor grids take pstd_set_incidence_spinor");
+    const pstd_grid_desc& d = g->desc;
+    std::vector<double> h[3];
+    for (int a = 0; a < 3; ++a) {
+        pstd_status st = read_grid_array(g, a == 0 ? Bx : a == 1 ? By : Bz, mem, dtype, h[a]);
+        if (st != PSTD_OK) return st;
+    }
+    int lo[3] = {d.n[0], d.n[1], d.n[2]}, hi[3] = {-1, -1, -1};
+    double bmax = 0;
+    for (int k = 0; k < d.n[2]; ++k)
+        for (int j = 0; j < d.n[1]; ++j)
+            for (int i = 0; i < d.n[0]; ++i) {
+                const size_t e = ((size_t)k * d.n[1] + j) * d.n[0] + i;
+                const double bx = h[0][e], by = h[1][e], bz = h[2][e];
+                if (!std::isfinite(bx) || !std::isfinite(by) || !std::isfinite(bz)) return fail(g, PSTD_EINVAL, "B is not finite");
+                if (bx == 0.0 && by == 0.0 && bz == 0.0) continue;
+                if (i < d.tfsf_lo[0] + d.taper_cells || i > d.tfsf_hi[0] - d.taper_cells || j < d.tfsf_lo[1] + d.taper_cells ||
+                    j > d.tfsf_hi[1] - d.taper_cells || k < d.tfsf_lo[2] + d.taper_cells || k > d.tfsf_hi[2] - d.taper_cells)
+                    return fail(g, PSTD_EINVAL, "B must vanish outside the zeta == 1 core");
+                lo[0] = std::min(lo[0], i); hi[0] = std::max(hi[0], i);
+                lo[1] = std::min(lo[1], j); hi[1] = std::max(hi[1], j);
+                lo[2] = std::min(lo[2], k); hi[2] = std::max(hi[2], k);
+                bmax = std::max(bmax, std::sqrt(bx * bx + by * by + bz * bz));
+            }
+    // the eigenvalues of V + gamma sigma . B lie within |V| + |gamma| |B|
+    if (d.dt > dt_bound(d, g->vmax + std::fabs(gamma) * bmax))
+        return fail(g, PSTD_EUNSTABLE, "dt above the stability bound with |V|max + |gamma| |B|max (Eq. PSTDstability)");
+    CK(g, cudaStreamSynchronize(g->stream));
+    for (int a = 0; a < 3; ++a) {
+        if (g->B[a]) cudaFree(g->B[a]);
+        g->B[a] = nullptr;
+    }
+    std::vector<double> box[3];
+    if (hi[0] < 0) {
+        for (int a = 0; a < 3; ++a) { g->blo[a] = 0; g->bhi[a] = 0; box[a].assign(1, 0.0); }
+    } else {
+        for (int a = 0; a < 3; ++a) { g->blo[a] = lo[a]; g->bhi[a] = hi[a] + 1; }
+        const int bx = g->bhi[0] - g->blo[0], by = g->bhi[1] - g->blo[1], bz = g->bhi[2] - g->blo[2];
+        for (int a = 0; a < 3; ++a) {
+            box[a].resize((size_t)bx * by * bz);
+            for (int k = 0; k < bz; ++k)
+                for (int j = 0; j < by; ++j)
+                    for (int i = 0; i < bx; ++i)
+                        box[a][((size_t)k * by + j) * bx + i] = h[a][((size_t)(k + lo[2]) * d.n[1] + (j + lo[1])) * d.n[0] + (i + lo[0])];
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        pstd_status st = upload_real(g, &g->B[a], box[a]);
+        if (st != PSTD_OK) return st;
+    }
+    g->spinor = true;
+    g->gamma_b = gamma;
+    g->bmax = bmax;
+    return PSTD_OK;
+}
+
+pstd_status pstd_set_incidence_spinor(pstd_grid* g, int p, const double khat[3], double k, double ramp_time,
+                                      const double chi[4])
+{
+    if (!g || !khat || !chi) return fail(g, PSTD_EINVAL, "null argument");
+    DeviceGuard dg(g->dev);
+    ++g->config_version;
+    g->ckpt_upto = -1;
+    g->ckpt_contig = false;
+    if (g->batch % 2 || p < 0 || 2 * p + 1 >= g->batch) return fail(g, PSTD_EINVAL, "spinor index out of range");
+    if (!(ramp_time >= 0)) return fail(g, PSTD_EINVAL, "ramp_time");
+    for (int c = 0; c < 2; ++c) {
+        const int b = 2 * p + c;
+        pstd_status st = set_incidence_common(g, b, khat, k);
+        if (st != PSTD_OK) return st;
+        MemberHost& m = g->mem[b];
+        m.ramp = ramp_time;
+        m.packet = false;
+        m.chi = cd(chi[2 * c], chi[2 * c + 1]);
+        g->packet_mask &= ~(1ull << b);
+    }
+    return upload_members(g);
 }

@@ -55,6 +55,12 @@ template <typename R> struct StepArgs {
     unsigned long long packet_mask;
     const R* proj[3];        // [member * n_a + i]
     const R* tenv;
+    // spinor grids: members (2p, 2p+1) are the up and down components of spinor p, coupled by
+    // W = V I + gamma sigma . B on the node box [blo, bhi) where B is stored
+    int spinor;
+    const R* B[3];
+    int blo[3], bhi[3];
+    R gamma;
     int batch;
 };
 

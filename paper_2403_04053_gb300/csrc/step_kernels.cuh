@@ -445,11 +445,41 @@ __device__ __forceinline__ C incident_wave(const StepArgs<R>& a, int b, C s, int
     return w;
 }
 
+// spinor member b: W (u + psi_inc) of its component, with W = V I + gamma sigma . B,
+// sigma . B = [[Bz, Bx - i By], [Bx + i By, -Bz]] (EXACT form); the partner component b ^ 1
+// is read at the same node
+template <typename R, typename C>
+__device__ __forceinline__ C spinor_acc(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
+{
+    const int bo = b ^ 1;
+    const long long idx_o = idx + (b & 1 ? -a.ncell : a.ncell);
+    const C so = a.tfac[(a.step - a.tfac_base) * a.batch + bo];
+    const C ts = cadd(a.cur[idx], incident_wave<R, C>(a, b, s, x, y, z));
+    const C to = cadd(a.cur[idx_o], incident_wave<R, C>(a, bo, so, x, y, z));
+    R Vv = R(0), Bx = R(0), By = R(0), Bz = R(0);
+    if (x >= a.vlo[0] && x < a.vhi[0] && y >= a.vlo[1] && y < a.vhi[1] && z >= a.vlo[2] && z < a.vhi[2]) {
+        const int vnx = a.vhi[0] - a.vlo[0], vny = a.vhi[1] - a.vlo[1];
+        Vv = a.V[((long long)(z - a.vlo[2]) * vny + (y - a.vlo[1])) * vnx + (x - a.vlo[0])];
+    }
+    if (x >= a.blo[0] && x < a.bhi[0] && y >= a.blo[1] && y < a.bhi[1] && z >= a.blo[2] && z < a.bhi[2]) {
+        const int bnx = a.bhi[0] - a.blo[0], bny = a.bhi[1] - a.blo[1];
+        const long long e = ((long long)(z - a.blo[2]) * bny + (y - a.blo[1])) * bnx + (x - a.blo[0]);
+        Bx = a.gamma * a.B[0][e];
+        By = a.gamma * a.B[1][e];
+        Bz = a.gamma * a.B[2][e];
+    }
+    const bool up = (b & 1) == 0;
+    const R wss = Vv + (up ? Bz : -Bz);
+    const C wso = mk<C>(Bx, up ? -By : By);   // up: gamma (Bx - i By); down: gamma (Bx + i By)
+    return cadd(cscale(ts, wss), cmul(wso, to));
+}
+
 // V-term + source at node (x, y, z) of member b (before the factor -(2 i dt / hbar));
 // s = the member's incident time factor at step n, idx the node's state index
 template <typename R, typename C>
 __device__ __forceinline__ C source_acc(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
 {
+    if (a.spinor) return spinor_acc<R, C>(a, b, s, x, y, z, idx);
     const bool paper = a.mode == PSTD_TFSF_PAPER;
     C acc = mk<C>(R(0), R(0));
     if (x >= a.vlo[0] && x < a.vhi[0] && y >= a.vlo[1] && y < a.vhi[1] && z >= a.vlo[2] && z < a.vhi[2]) {
@@ -478,6 +508,14 @@ template <typename R> __host__ __device__ inline void source_box(const StepArgs<
     for (int d = 0; d < 3; ++d) {
         if (a.mode == PSTD_TFSF_PAPER) { lo[d] = a.tf_lo[d] + 1; hi[d] = a.tf_hi[d]; }
         else { lo[d] = a.vlo[d]; hi[d] = a.vhi[d]; }
+    }
+    // spinor grids: the union with B's box (an empty box has lo == hi)
+    if (a.spinor && a.bhi[0] > a.blo[0]) {
+        const bool vempty = !(a.vhi[0] > a.vlo[0]);
+        for (int d = 0; d < 3; ++d) {
+            lo[d] = vempty ? a.blo[d] : (a.blo[d] < lo[d] ? a.blo[d] : lo[d]);
+            hi[d] = vempty ? a.bhi[d] : (a.bhi[d] > hi[d] ? a.bhi[d] : hi[d]);
+        }
     }
 }
 

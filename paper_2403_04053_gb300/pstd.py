@@ -71,6 +71,8 @@ _SIGS = {
     "pstd_set_checkpointing": (c_int, [c_void_p, c_long, c_long]),
     "pstd_set_incidence_packet": (c_int, [c_void_p, c_int, POINTER(c_double), c_double, c_double, c_double]),
     "pstd_set_graphs": (c_int, [c_void_p, c_int]),
+    "pstd_set_magnetic_field": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int, c_int]),
+    "pstd_set_incidence_spinor": (c_int, [c_void_p, c_int, POINTER(c_double), c_double, c_double, POINTER(c_double)]),
     "pstd_graph_replays": (c_int, [c_void_p, POINTER(c_long)]),
     "pstd_set_variants": (c_int, [c_void_p, c_int, c_int]),
     "pstd_autotune": (c_int, [c_void_p, c_long, POINTER(c_int)]),
@@ -203,6 +205,18 @@ class Grid:
     def set_incidence(self, b: int, khat, k: float, ramp_time: float, envelope: int = ENV_CW_RAMP):
         kh = (c_double * 3)(*[float(v) for v in khat])
         self._c(self.lib.pstd_set_incidence(self.h, b, kh, float(k), envelope, float(ramp_time)), "pstd_set_incidence")
+
+    def set_magnetic_field(self, B, gamma: float):
+        """Spinor coupling gamma sigma . B (pstd_set_magnetic_field); B = (Bx, By, Bz) host arrays."""
+        arrs = [np.ascontiguousarray(b, dtype=np.float64) for b in B]
+        self._c(self.lib.pstd_set_magnetic_field(self.h, *[a.ctypes.data_as(c_void_p) for a in arrs], float(gamma),
+                                                 MEM_HOST, DTYPE_F64), "pstd_set_magnetic_field")
+
+    def set_incidence_spinor(self, p: int, khat, k: float, ramp_time: float, chi):
+        """CW incidence of spinor p with spin state chi = (up, down) (pstd_set_incidence_spinor)."""
+        kh = (c_double * 3)(*[float(v) for v in khat])
+        c = (c_double * 4)(complex(chi[0]).real, complex(chi[0]).imag, complex(chi[1]).real, complex(chi[1]).imag)
+        self._c(self.lib.pstd_set_incidence_spinor(self.h, p, kh, float(k), float(ramp_time), c), "pstd_set_incidence_spinor")
 
     def set_incidence_packet(self, b: int, khat, k: float, sigma: float, d0: float):
         """Gaussian wave-packet incidence of member b (pstd_set_incidence_packet)."""
