@@ -259,6 +259,8 @@ def run_gpu(args):
     adjoint = None if args.skip_adjoint else adjoint_leg(pstd, inputs, stream, dev)
     # batched leg: 16 incidences against one potential on a 256^3 grid (HBM-bound regime)
     batched = None if args.skip_batched else batched_leg(pstd, inputs, stream, dev, flush)
+    # spinor leg: two spin states of a sigma . B scattering problem on a 384^3 grid
+    spinor = None if args.skip_spinor else spinor_leg(pstd, inputs, stream, dev, flush)
 
     out = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
@@ -276,6 +278,7 @@ def run_gpu(args):
         "fp64": fp64,
         "adjoint": adjoint,
         "batched": batched,
+        "spinor": spinor,
     }
     if rank == 0:
         out["clocks"] = clk.summary()
@@ -334,6 +337,68 @@ def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80):
             "roofline": {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(achieved / hbm, 4), "algorithmic_bytes_per_launch": 24 * ncell * B,
                          "traffic": BATCHED_TRAFFIC.get(top) if B == 16 else None}}
+
+
+def spinor_leg(pstd, inputs, stream, dev, flush, nsteps=80):
+    """Cell-updates/s of the 384^3 spinor configuration (sigma . B of a point dipole, two spin
+    states as two spinors = four batch members) over `nsteps` steps, the last half in the DFT
+    window; then the 512^2-point Fresnel transform and the 361 x 180 spin-resolved far field of
+    every member, each timed with CUDA events."""
+    import torch
+    wl = inputs.spinor_workload()
+    spec = wl.spec
+    inc = wl.incidences[0]
+    w0 = spec.hbar * inc.k ** 2 / (2 * spec.mass)
+    B = 2 * len(wl.chis)
+    g = pstd.Grid(spec, precision=pstd.F32, batch=B, stream=stream.cuda_stream)
+    g.set_potential(torch.from_numpy(wl.V).to(dev))
+    g.set_magnetic_field(wl.B, wl.gamma)
+    for p, chi in enumerate(wl.chis):
+        g.set_incidence_spinor(p, inc.khat, inc.k, inc.ramp_time, chi)
+    g.huygens_dft(-1, [w0], nsteps // 2, nsteps - nsteps // 2)
+    ncell = int(np.prod(spec.n))
+
+    def timed(fn):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        out = fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / 1e3, out
+
+    times = []
+    for rep in range(3):   # the first repetition is a warm-up
+        g.reset()
+        flush.fill_(1.0)
+        times.append(timed(lambda: g.step(nsteps))[0])
+    t = statistics.median(times[1:])
+    g.reset()
+    g.set_timing(True)
+    g.step(nsteps)
+    ks = {name: g.kernel_stats(name) for name in ("xpass", "ypass", "zpass", "source")}
+    g.set_timing(False)
+    pts = torch.from_numpy(wl.fresnel_points).to(dev)
+    th, ph = torch.from_numpy(wl.far_theta).to(dev), torch.from_numpy(wl.far_phi).to(dev)
+    t_tr = sum(timed(lambda: g.transform_to_points(b, 0, pts))[0] for b in range(B))
+    t_ff = sum(timed(lambda: g.cross_section(b, 0, th, ph))[0] for b in range(B))
+    g.close()
+    top = max(("xpass", "ypass", "zpass"), key=lambda n: ks[n][1])
+    nl, ms = ks[top]
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    achieved = 24.0 * ncell * B / (ms / nl / 1e3) / 1e9
+    return {"workload": f"spinor-384^3: gamma sigma . B of a point dipole (cut off inside r = 1 and outside r = 12), "
+                        f"unpolarised incidence as 2 spinors = {B} members, FP32, {nsteps} steps "
+                        f"({nsteps - nsteps // 2} in the DFT window)",
+            "value": B * ncell * nsteps / t, "unit": "cell-updates/s", "ms_per_step": t / nsteps * 1e3,
+            "state_bytes": 2 * B * ncell * 8,
+            "kernels_us": {n: round(v[1] / max(1, v[0]) * 1e3, 1) for n, v in ks.items()},
+            "fresnel_transform_ms": round(t_tr * 1e3, 2), "fresnel_points_per_member": len(wl.fresnel_points),
+            "far_field_ms": round(t_ff * 1e3, 2), "far_field_directions": len(wl.far_theta),
+            "roofline": {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                         "frac": round(achieved / hbm, 4), "algorithmic_bytes_per_launch": 24 * ncell * B,
+                         "traffic": None}}
 
 
 def adjoint_leg(pstd, inputs, stream, dev):
@@ -453,6 +518,9 @@ def main():
     p.add_argument("--skip-e2e", action="store_true")
     p.add_argument("--skip-adjoint", action="store_true")
     p.add_argument("--skip-batched", action="store_true")
+    p.add_argument("--skip-spinor", action="store_true")
+    p.add_argument("--spinor-only", action="store_true",
+                   help="run only the 384^3 spinor leg and print its JSON object (profiling)")
     p.add_argument("--batched-only", action="store_true",
                    help="run only the batched leg (with --batched-members / --batched-steps) and print it")
     p.add_argument("--batched-members", type=int, default=0)
@@ -467,6 +535,12 @@ def main():
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         print(json.dumps(batched_leg(pstd, inputs, torch.cuda.current_stream(), dev, flush,
                                      args.batched_members or None, args.batched_steps)), flush=True)
+    elif args.spinor_only:
+        import torch
+        from paper_2403_04053_gb300 import inputs, pstd
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        print(json.dumps(spinor_leg(pstd, inputs, torch.cuda.current_stream(), dev, flush)), flush=True)
     else:
         run_gpu(args)
 

@@ -19,7 +19,8 @@ import math
 
 import numpy as np
 
-from .pstd_oracle import Simulation, kinetic
+from .pstd_oracle import (AXES_NP, Simulation, apply_axis, coords, envelope, eta, first_contact_corner, kinetic,
+                          mask_1d)
 
 
 def coupling(V, B, gamma):
@@ -80,3 +81,52 @@ def eigen_spin(nhat):
     M = np.array([[nz, nx - 1j * ny], [nx + 1j * ny, -nz]])
     w, v = np.linalg.eigh(M)
     return v[:, 1], v[:, 0]
+
+
+def kinetic_at(u, d, node):
+    """(K u) at one node (i, j, k) of a [z, y, x] array from the three grid lines through it: the
+    spectral Laplacian of Eq. spatialFFTeigen is a sum of one-axis operators, so each term needs
+    only the line along its axis."""
+    i, j, k = node
+    lines = (u[k, j, :], u[k, :, i], u[:, j, i])
+    out = 0j
+    for a in range(3):
+        shp = [1, 1, 1]
+        shp[AXES_NP[a]] = -1
+        line = np.asarray(lines[a], dtype=np.complex128).reshape(shp)
+        pos = (i, j, k)[a]
+        out += complex(apply_axis(line, a, d[a], lambda q: q * q).ravel()[pos])
+    return out
+
+
+def step_at_nodes(spec, V, B, gamma, khat, k, ramp_time, chi, prev, cur, n, nodes):
+    """psi^{n+1} of both spinor components at the given nodes (i, j, k), the update of
+    SpinorSimulation evaluated node by node (for grids too large for the whole-array oracle).
+
+    prev, cur: pairs of [z, y, x] arrays (up, down) at levels n-1 and n; V, B: the potential and
+    the three induction components, [z, y, x] arrays.  Returns a (len(nodes), 2) complex array."""
+    hb, m = spec.hbar, spec.mass
+    kh = np.asarray(khat, dtype=float) / np.linalg.norm(khat)
+    E0 = hb * hb * k * k / (2.0 * m)
+    w0 = E0 / hb
+    kin_coef = hb * hb / (2.0 * m) * eta(E0, spec.dt, hb)
+    gam = [mask_1d(spec.n[a], spec.abc_cells[a], spec.abc_profile, spec.abc_param, E0, spec.dt, hb) for a in range(3)]
+    rO = first_contact_corner(kh, spec)
+    x = [coords(spec.n[a], spec.d[a]) for a in range(3)]
+    t = n * spec.dt
+    tf = envelope(t, ramp_time) * complex(math.cos(w0 * t), -math.sin(w0 * t))
+    c = 2j * spec.dt / hb
+    ch = (complex(chi[0]), complex(chi[1]))
+    out = np.zeros((len(nodes), 2), dtype=np.complex128)
+    for q, (i, j, kk) in enumerate(nodes):
+        r = np.array([x[0][i], x[1][j], x[2][kk]])
+        pinc = tf * complex(np.exp(1j * k * float(kh @ (r - rO))))
+        Wuu, Wud, Wdu, Wdd = coupling(V[kk, j, i], [b[kk, j, i] for b in B], gamma)
+        tot = [complex(cur[0][kk, j, i]) + ch[0] * pinc, complex(cur[1][kk, j, i]) + ch[1] * pinc]
+        H = [kin_coef * kinetic_at(cur[0], spec.d, (i, j, kk)) + Wuu * tot[0] + Wud * tot[1],
+             kin_coef * kinetic_at(cur[1], spec.d, (i, j, kk)) + Wdu * tot[0] + Wdd * tot[1]]
+        G = gam[0][i] * gam[1][j] * gam[2][kk]
+        for s in range(2):
+            out[q, s] = G * (complex(prev[s][kk, j, i]) - c * H[s])
+    return out
+

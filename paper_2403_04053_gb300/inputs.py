@@ -231,6 +231,13 @@ def random_field(shape, seed: int, dtype=np.complex128, scale: float = 1.0) -> n
     return (scale * a).astype(dtype)
 
 
+def random_field_c64(shape, seed: int) -> np.ndarray:
+    """complex64 white noise with unit-variance real and imaginary parts, drawn in float32
+    (for full-size grids, where a complex128 draw would double the host memory)."""
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal((*shape, 2), dtype=np.float32).view(np.complex64)[..., 0]
+
+
 def smooth_random_field(spec: GridSpec, seed: int, kmax_frac: float = 0.5) -> np.ndarray:
     """Band-limited random complex field (modes with |k_a| <= kmax_frac * Nyquist)."""
     rng = np.random.default_rng(seed)
@@ -399,3 +406,78 @@ def batched_workload(n: int = 256, dx: float = 0.25, nsteps: int = 3000, seed: i
                   window_first=windows[0][0], window_len=windows[0][1])
     wl.windows = windows
     return wl
+
+
+def smooth_window(r, r_in: float, r_out: float):
+    """C1 radial window: 0 for r <= r_in / 2, 1 on [r_in, r_out - 1], 0 for r >= r_out, joined by
+    the smoothstep t^2 (3 - 2t) over [r_in / 2, r_in] and [r_out - 1, r_out]."""
+    def step(t):
+        t = np.clip(t, 0.0, 1.0)
+        return t * t * (3.0 - 2.0 * t)
+    return step((r - 0.5 * r_in) / (0.5 * r_in)) * (1.0 - step(r - (r_out - 1.0)))
+
+
+def _dipole_box(spec: GridSpec, mhat, r_in: float, r_out: float):
+    """(sub-box slices [z, y, x], (Bx, By, Bz) on that box) of dipole_field."""
+    m = np.asarray(mhat, dtype=float)
+    m = m / np.linalg.norm(m)
+    sl, xs = [], []
+    for a in range(3):
+        x = spec.coords(a)
+        idx = np.nonzero(np.abs(x) <= r_out)[0]
+        sl.append(slice(idx[0], idx[-1] + 1))
+        xs.append(x[idx])
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    w = smooth_window(r, r_in, r_out)
+    rs = np.where(r > 0, r, 1.0)
+    mr = (m[0] * X + m[1] * Y + m[2] * Z) / rs
+    box = tuple(np.where(r > 0, w * (3.0 * mr * comp / rs - m[a]) / rs ** 3, 0.0) for a, comp in enumerate((X, Y, Z)))
+    return (sl[2], sl[1], sl[0]), box
+
+
+def dipole_field(spec: GridSpec, mhat, r_in: float = 1.0, r_out: float = 12.0, scale: float = 1.0):
+    """Point-dipole induction B = scale (3 (m . rhat) rhat - m) / r^3 of a unit moment along mhat
+    at the origin, times smooth_window(r, r_in, r_out).  Evaluated on the sub-box |x_a| <= r_out
+    and embedded in zeros; returns (Bx, By, Bz) as [z, y, x] float64 arrays."""
+    sl, box = _dipole_box(spec, mhat, r_in, r_out)
+    out = [np.zeros(spec.shape) for _ in range(3)]
+    for o, b in zip(out, box):
+        o[sl] = scale * b
+    return tuple(out)
+
+
+def spinor_workload(n: int = 384, dx: float = 0.25, nsteps: int = 6000, seed: int = 2409, abc: int = 24,
+                    tf=(128, 256), taper: int = 4, hb=(120, 264), gamma: float = 1.0, strength: float = 0.5,
+                    fresnel_count: int = 512, with_outputs: bool = True) -> Workload:
+    """Spin-dependent scattering by a point-dipole field: H = -lap/2 + gamma sigma . B(r), V = 0.
+
+    B is dipole_field with a seeded moment direction, cut off smoothly inside r = 1 and outside
+    r = 12, scaled so that gamma |B|max = strength * E (E = k^2 / 2 at k = 2 pi).  Unpolarised
+    incidence is the pair of spin states up and down along z, run as two spinors (four batch
+    members) along one seeded direction; dt = 0.9 x the stability bound with |gamma B|max; the
+    DFT window is the last three carrier periods.  Outputs: a fresnel_count^2 plane normal to
+    khat at D^2/(4 lambda) (D = side of the zeta = 1 core), side 1.5 D, and the 361 x 180 far
+    field.  wl.B, wl.gamma and wl.chis hold the field, the coupling and the spin states."""
+    k = 2 * math.pi
+    E0 = 0.5 * k * k
+    spec = GridSpec(n=(n, n, n), d=(dx, dx, dx), dt=1.0, abc_cells=(abc,) * 3,
+                    tfsf_lo=(tf[0],) * 3, tfsf_hi=(tf[1],) * 3, taper_cells=taper,
+                    huygens_lo=(hb[0],) * 3, huygens_hi=(hb[1],) * 3)
+    mhat = seeded_direction(seed)
+    _, box = _dipole_box(spec, mhat, 1.0, 12.0)
+    bmax = float(np.max(np.sqrt(box[0] ** 2 + box[1] ** 2 + box[2] ** 2)))
+    B = dipole_field(spec, mhat, scale=strength * E0 / (abs(gamma) * bmax))
+    spec.dt = stable_dt(spec.n, spec.d, strength * E0)
+    khat = seeded_direction(seed + 1)
+    n0, M = dft_window(E0, spec.dt, nsteps)
+    wl = Workload(name=f"spinor-dipole-{n}^3-x2", spec=spec, V=np.zeros(spec.shape),
+                  incidences=[Incidence(tuple(khat), k, 0.5)], nsteps=nsteps, window_first=n0, window_len=M)
+    wl.B, wl.gamma, wl.chis = B, gamma, [(1.0, 0.0), (0.0, 1.0)]
+    if with_outputs:
+        D = (tf[1] - taper - (tf[0] + taper)) * dx
+        lam = 2 * math.pi / k
+        wl.fresnel_points = plane_points(khat, D * D / (4 * lam), 1.5 * D, fresnel_count)
+        wl.far_theta, wl.far_phi = far_field_grid()
+    return wl
+

@@ -65,6 +65,16 @@ ONE_STEP_SPECS = {
                                                     abc_cells=(2, 16, 20), tfsf_lo=(5, 60, 80), tfsf_hi=(11, 132, 176),
                                                     taper_cells=1, huygens_lo=(3, 40, 50), huygens_hi=(13, 150, 206),
                                                     tfsf_mode=mode),
+    # 384-point lines (radix 12 x 8 x 4) along each axis in turn
+    "line384-x": lambda mode: inputs.GridSpec(n=(384, 16, 12), d=(0.1, 0.3, 0.4), dt=0.0015, abc_cells=(24, 2, 1),
+                                              tfsf_lo=(120, 5, 4), tfsf_hi=(264, 11, 8), taper_cells=1,
+                                              huygens_lo=(100, 3, 2), huygens_hi=(284, 13, 10), tfsf_mode=mode),
+    "line384-y": lambda mode: inputs.GridSpec(n=(16, 384, 12), d=(0.3, 0.1, 0.4), dt=0.0015, abc_cells=(2, 24, 1),
+                                              tfsf_lo=(5, 120, 4), tfsf_hi=(11, 264, 8), taper_cells=1,
+                                              huygens_lo=(3, 100, 2), huygens_hi=(13, 284, 10), tfsf_mode=mode),
+    "line384-z": lambda mode: inputs.GridSpec(n=(12, 16, 384), d=(0.4, 0.3, 0.1), dt=0.0015, abc_cells=(1, 2, 24),
+                                              tfsf_lo=(4, 5, 120), tfsf_hi=(8, 11, 264), taper_cells=1,
+                                              huygens_lo=(2, 3, 100), huygens_hi=(10, 13, 284), tfsf_mode=mode),
     "radix3-12x192x8": lambda mode: inputs.GridSpec(n=(12, 192, 8), d=(0.3, 0.1, 0.4), dt=0.001, abc_cells=(2, 16, 1),
                                                     tfsf_lo=(4, 60, 3), tfsf_hi=(8, 132, 5), taper_cells=1,
                                                     huygens_lo=(3, 40, 2), huygens_hi=(9, 150, 6), tfsf_mode=mode),

@@ -222,3 +222,71 @@ def test_spinor_call_errors():
         assert e.value.code == "EUNSTABLE"
     with pstd.Grid(spec, precision=pstd.F32, batch=2) as g:
         g.set_potential(Vbig)                                           # stable without B
+
+
+# ----------------------------------------------------------------------------------
+# the 384^3 point-dipole configuration at full size, in the bench's launch configuration
+# (two spinors = four members, FP32): sampled nodes against the node-by-node oracle
+# ----------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def dipole():
+    return inputs.spinor_workload(with_outputs=True)
+
+
+def _dipole_grid(wl):
+    g = pstd.Grid(wl.spec, precision=pstd.F32, batch=2 * len(wl.chis))
+    g.set_potential(wl.V)
+    g.set_magnetic_field(wl.B, wl.gamma)
+    inc = wl.incidences[0]
+    for p, chi in enumerate(wl.chis):
+        g.set_incidence_spinor(p, inc.khat, inc.k, inc.ramp_time, chi)
+    return g
+
+
+def test_384_cubed_spinor_one_step_sampled(dipole):
+    wl = dipole
+    sp, inc = wl.spec, wl.incidences[0]
+    n = 300                                     # past the ramp: the full incident amplitude
+    prev = [inputs.random_field_c64(sp.shape, 40 + b) for b in range(4)]
+    cur = [inputs.random_field_c64(sp.shape, 50 + b) for b in range(4)]
+    rng = np.random.default_rng(12)
+    nodes = [(0, 0, 0), (383, 383, 383), (5, 200, 379), (192, 192, 192), (150, 240, 145), (239, 145, 200),
+             (130, 130, 130), (253, 128, 190)]
+    nodes += [tuple(int(v) for v in rng.integers(0, 384, 3)) for _ in range(24)]          # anywhere
+    nodes += [tuple(int(v) for v in rng.integers(145, 240, 3)) for _ in range(24)]        # inside B's support
+    with _dipole_grid(wl) as g:
+        for b in range(4):
+            g.set_field(b, prev[b], cur[b], n)
+        g.step(1)
+        got = [g.get_field(b) for b in range(4)]
+    for p, chi in enumerate(wl.chis):
+        ref = so.step_at_nodes(sp, wl.V, wl.B, wl.gamma, inc.khat, inc.k, inc.ramp_time, chi,
+                               prev[2 * p:2 * p + 2], cur[2 * p:2 * p + 2], n, nodes)
+        scale = np.max(np.abs(ref))
+        for q, (i, j, k) in enumerate(nodes):
+            for s in range(2):
+                assert abs(got[2 * p + s][k, j, i] - ref[q, s]) < 4e-5 * scale
+
+
+def test_384_cubed_spinor_sampled_transform(dipole):
+    """Phasors of a short full-size run; the transform at a sampled Fresnel-plane point (spin-flip
+    members) and the far field at sampled directions (every member) against the oracle's mode
+    sums on the GPU's own phasors."""
+    wl = dipole
+    w0 = K * K / 2
+    with _dipole_grid(wl) as g:
+        g.huygens_dft(-1, [w0], 30, 30)
+        g.step(60)
+        phs = [g.get_phasors(b, 0) for b in range(4)]
+        pt = wl.fresnel_points[[131000]]
+        psi = {b: g.transform_to_points(b, 0, pt) for b in (1, 2)}
+        th = np.deg2rad([5.0, 91.0, 170.0])
+        ph = np.deg2rad([10.0, 250.0, 0.0])
+        far = [g.cross_section(b, 0, th, ph)[1] for b in range(4)]
+    for b in (1, 2):
+        ref = no.transform_to_points(wl.spec, K, phs[b], pt)
+        assert np.max(np.abs(psi[b] - ref) / np.abs(ref)) < 1e-4
+    for b in range(4):
+        _, fref = no.cross_section(wl.spec, K, phs[b], th, ph)
+        assert np.max(np.abs(far[b] - fref) / np.abs(fref)) < 1e-4
+

@@ -81,3 +81,26 @@ def test_planted_by_sign_error_is_caught(monkeypatch):
     dn.step(30)
     ref = a * ep[1] * up.cur + c * em[1] * dn.cur
     assert np.linalg.norm(sim.cur[1] - ref) > 1e-3 * np.linalg.norm(ref)
+
+
+def test_node_sampled_step_equals_whole_array_step():
+    # the node-by-node update (three grid lines per node) against the whole-array step, on nodes
+    # in the absorber, at the grid's edges, in the taper and inside B's support
+    sp = spec()
+    V, B, _ = fields(sp, (0.3, -0.6, 0.74))
+    rng = np.random.default_rng(9)
+    B = [b + np.where(b != 0, rng.uniform(-1, 1, sp.shape), 0.0) for b in B]     # a varying direction
+    prev = [inputs.random_field(sp.shape, 20 + s) for s in range(2)]
+    cur = [inputs.random_field(sp.shape, 22 + s) for s in range(2)]
+    gamma, chi = 1.3, (0.6, 0.8j)
+    sim = so.SpinorSimulation(sp, V, B, gamma, KHAT, K, 0.05, chi)
+    for s in range(2):
+        sim.comp[s].prev, sim.comp[s].cur, sim.comp[s].n = prev[s].copy(), cur[s].copy(), 9
+    sim.n = 9
+    sim.step(1)
+    nodes = [(0, 0, 0), (23, 23, 23), (1, 12, 22), (7, 8, 9), (12, 12, 12), (11, 13, 10)]
+    nodes += [tuple(int(v) for v in rng.integers(0, 24, 3)) for _ in range(40)]
+    got = so.step_at_nodes(sp, V, B, gamma, KHAT, K, 0.05, chi, prev, cur, 9, nodes)
+    for q, (i, j, k) in enumerate(nodes):
+        for s in range(2):
+            assert abs(got[q, s] - sim.cur[s][k, j, i]) <= 1e-12 * (1 + abs(sim.cur[s][k, j, i]))
