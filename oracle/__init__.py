@@ -16,6 +16,8 @@ Modules
                 spherical wave, leapfrog mode evolution)
   spinor_oracle : the two-component leapfrog with a gamma sigma . B coupling (EXACT form),
                 pinned by its exact splitting into two scalar problems for B = b(r) nhat
+  aux_oracle  : the 1-D auxiliary incident wave of Section 2.2.3 (free 1-D leapfrog along
+                the incidence axis, read at each node's d by Eqs. pstd_psiinc, pstd_dpsiinc)
   adjoint_oracle : the discrete adjoint (transpose) of the leapfrog run, of the running
                 DFT and of the surface transform, and the gradient of a Fresnel-field
                 magnitude misfit with respect to V (no counterpart in the paper; pinned by

@@ -236,7 +236,7 @@ def in_plane_axes(axis: int):
 class Simulation:
     """Leapfrog PSTD run of one incident plane wave on a GridSpec (Eq. PSTDupdating)."""
 
-    def __init__(self, spec, V, khat, k, ramp_time, window=None, omegas=None, probes=None, packet=None):
+    def __init__(self, spec, V, khat, k, ramp_time, window=None, omegas=None, probes=None, packet=None, aux=None):
         self.spec = spec
         hb, m = spec.hbar, spec.mass
         self.V = np.asarray(V, dtype=np.float64)
@@ -249,6 +249,9 @@ class Simulation:
         # optional Gaussian wave-packet incidence (sigma, d0): the packet's centre starts at
         # d0 on the axis d = khat . (r - r_O) and moves along +khat (replaces the CW wave)
         self.packet = None if packet is None else (float(packet[0]), float(packet[1]))
+        # optional 1-D auxiliary incident wave (aux_oracle.AuxSource1D, Section 2.2.3): read at
+        # d = khat . (r - r_O); replaces the CW wave (k sets eta and the default DFT frequency)
+        self.aux = aux
         self.eta = eta(self.E0, spec.dt, hb)
         self.kin_coef = hb * hb / (2.0 * m) * self.eta
         # mask Gamma = Gamma_x Gamma_y Gamma_z (Eq. Gamma)
@@ -277,6 +280,7 @@ class Simulation:
                        + self.kvec[2] * outer(Z[0], Z[1], Z1[2]))
         # hbar^2/2m (lap(zeta) psi_inc + 2 grad(zeta) . grad(psi_inc)), grad psi_inc = i k psi_inc
         self.src_factor = hb * hb / (2.0 * m) * (lap_zeta + 2j * k_grad_zeta)
+        self.lap_zeta, self.khat_grad_zeta = lap_zeta, k_grad_zeta / self.k
         if spec.tfsf_mode == "paper" and np.any((self.zeta < 1.0) & (self.V != 0.0)):
             raise ValueError("V must vanish where zeta < 1 ((zeta - 1) V = 0)")
         self.prev = np.zeros(spec.shape, dtype=np.complex128)
@@ -297,12 +301,16 @@ class Simulation:
     def inc_time_factor(self, n: int) -> complex:
         """The incident wave at O at step n: a(t_n) exp(-i w0 t_n), or the packet at d = 0."""
         t = n * self.spec.dt
+        if self.aux is not None:
+            return complex(self.aux.value(n, 0.0))
         if self.packet is not None:
             sig, d0 = self.packet
             return complex(gaussian_packet(0.0 - d0, t, self.k, sig, self.spec.hbar, self.spec.mass))
         return envelope(t, self.ramp_time) * complex(math.cos(self.w0 * t), -math.sin(self.w0 * t))
 
     def psi_inc(self, n: int) -> np.ndarray:
+        if self.aux is not None:
+            return self.aux.value(n, self.inc_d)
         if self.packet is not None:
             sig, d0 = self.packet
             return gaussian_packet(self.inc_d - d0, n * self.spec.dt, self.k, sig, self.spec.hbar, self.spec.mass)
@@ -317,6 +325,10 @@ class Simulation:
         pinc = self.psi_inc(n)
         if spec.tfsf_mode == "exact":
             Hu = Hu + self.V * (cur + pinc)
+        elif spec.tfsf_mode == "paper" and self.aux is not None:
+            # grad psi_inc = khat d psi_inc / d d (Eq. pstd_dpsiinc)
+            dpinc = self.aux.derivative(n, self.inc_d)
+            Hu = Hu + self.V * cur + hb * hb / (2.0 * spec.mass) * (self.lap_zeta * pinc + 2.0 * self.khat_grad_zeta * dpinc)
         elif spec.tfsf_mode == "paper":
             Hu = Hu + self.V * cur + self.src_factor * pinc
         else:
