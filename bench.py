@@ -261,6 +261,8 @@ def run_gpu(args):
     batched = None if args.skip_batched else batched_leg(pstd, inputs, stream, dev, flush)
     # spinor leg: two spin states of a sigma . B scattering problem on a 384^3 grid
     spinor = None if args.skip_spinor else spinor_leg(pstd, inputs, stream, dev, flush)
+    # auxiliary-wave leg: arbitrary incident packets from the 1-D auxiliary axis
+    aux = None if args.skip_aux else aux_leg(pstd, inputs, stream, dev, flush)
 
     out = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
@@ -279,6 +281,7 @@ def run_gpu(args):
         "adjoint": adjoint,
         "batched": batched,
         "spinor": spinor,
+        "aux_source": aux,
     }
     if rank == 0:
         out["clocks"] = clk.summary()
@@ -401,6 +404,57 @@ def spinor_leg(pstd, inputs, stream, dev, flush, nsteps=80):
                          "traffic": None}}
 
 
+def aux_leg(pstd, inputs, stream, dev, flush, nsteps=300):
+    """The 128^3 Gaussian-sum workload driven by the 1-D auxiliary incident wave (a Gaussian
+    profile, sigma = 1, on a 512-point axis) against the same steps with the CW wave: cell-updates/s
+    of both, and the per-step cost of evaluating the auxiliary wave on the potential's box."""
+    import torch
+    wl = inputs.gaussian_sum_workload(with_outputs=False)
+    spec, inc = wl.spec, wl.incidences[0]
+    w0 = spec.hbar * inc.k ** 2 / (2 * spec.mass)
+    # the profile decays to 1e-17 at both ends of the periodic axis (no wrap-around edge)
+    d_lo, dd, n1, sigma, d0 = -16.5, 0.15, 512, 1.0, -4.0
+    d = d_lo + dd * np.arange(n1)
+    x = d - d0
+    prof = np.exp(-x * x / (4 * sigma * sigma) + 1j * inc.k * x)
+    ncell = int(np.prod(spec.n))
+    out = {}
+    for kind in ("cw", "aux"):
+        g = pstd.Grid(spec, precision=pstd.F32, stream=stream.cuda_stream)
+        g.set_potential(torch.from_numpy(wl.V).to(dev))
+        if kind == "aux":
+            g.set_incidence_aux(0, inc.khat, inc.k, d_lo, dd, prof)
+        else:
+            g.set_incidence(0, inc.khat, inc.k, inc.ramp_time)
+        g.huygens_dft(0, [w0], nsteps - 60, 60)
+        times = []
+        for rep in range(4):   # the first repetition is a warm-up
+            g.reset()
+            flush.fill_(1.0)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            torch.cuda.synchronize()
+            ev[0].record(stream)
+            g.step(nsteps)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            times.append(ev[0].elapsed_time(ev[1]) / 1e3)
+        t = statistics.median(times[1:])
+        g.reset()
+        g.set_timing(True)
+        g.step(nsteps)
+        n_aux, ms_aux = g.kernel_stats("aux")
+        g.set_timing(False)
+        g.close()
+        out[kind] = {"value": ncell * nsteps / t, "ms_per_step": t / nsteps * 1e3}
+        if kind == "aux":
+            out[kind]["aux_kernel_us_per_step"] = round(ms_aux / nsteps * 1e3, 2)
+            out[kind]["aux_launches"] = n_aux
+    return {"workload": f"gaussian-sum-128^3, {nsteps} steps (60 in the DFT window), incident wave from the 1-D "
+                        f"auxiliary axis ({n1} points, dd = {dd}, Gaussian profile sigma = {sigma}) vs the CW wave",
+            "unit": "cell-updates/s", "aux": out["aux"], "cw": out["cw"],
+            "aux_overhead": round(out["aux"]["ms_per_step"] / out["cw"]["ms_per_step"] - 1.0, 4)}
+
+
 def adjoint_leg(pstd, inputs, stream, dev):
     """Forward run + loss, then the discrete adjoint (transform adjoint + backward sweep with
     sqrt(N) checkpoints), each timed with CUDA events on the library's stream."""
@@ -519,6 +573,8 @@ def main():
     p.add_argument("--skip-adjoint", action="store_true")
     p.add_argument("--skip-batched", action="store_true")
     p.add_argument("--skip-spinor", action="store_true")
+    p.add_argument("--skip-aux", action="store_true")
+    p.add_argument("--aux-only", action="store_true", help="run only the auxiliary-wave leg and print it")
     p.add_argument("--spinor-only", action="store_true",
                    help="run only the 384^3 spinor leg and print its JSON object (profiling)")
     p.add_argument("--batched-only", action="store_true",
@@ -535,6 +591,12 @@ def main():
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         print(json.dumps(batched_leg(pstd, inputs, torch.cuda.current_stream(), dev, flush,
                                      args.batched_members or None, args.batched_steps)), flush=True)
+    elif args.aux_only:
+        import torch
+        from paper_2403_04053_gb300 import inputs, pstd
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        print(json.dumps(aux_leg(pstd, inputs, torch.cuda.current_stream(), dev, flush)), flush=True)
     elif args.spinor_only:
         import torch
         from paper_2403_04053_gb300 import inputs, pstd

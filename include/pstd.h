@@ -132,6 +132,21 @@ pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double
  * EINVAL for b out of range, k <= 0, sigma <= 0, khat = 0. */
 pstd_status pstd_set_incidence_packet(pstd_grid* g, int b, const double khat[3], double k, double sigma, double d0);
 
+/* Incidence of member b from the 1-D auxiliary wave of Section 2.2.3: a packet of any shape.
+ * The free 1-D Schroedinger equation is solved along the incidence axis d = khat . (r - r_O)
+ * (Eq. inc_d) by the 1-D leapfrog of Eq. PSTDupdating with this run's dt and eta(k); each node
+ * reads psi_inc and d psi_inc / d d from the 1-D grid's Fourier series (Eqs. pstd_psiinc,
+ * pstd_dpsiinc).  EXACT and PAPER forms.
+ *   psi0   2 * n1 doubles, interleaved (re, im): the profile psi1(d_lo + m dd, t = 0), m < n1;
+ *          copied; the 1-D run starts from it and from its exact backward step.
+ *   n1     a power of two in [8, 65536]; the axis is periodic, [d_lo, d_lo + n1 dd).
+ *   k      the carrier: eta and the default DFT frequency hbar k^2 / 2m.
+ * EINVAL: the axis does not cover the TF/SF box (d_lo > 0 or d_lo + n1 dd below the box's
+ * largest d), a non-finite profile, a spinor grid.  EUNSTABLE: dt eta hbar (pi/dd)^2 / 2m > 1.
+ * The adjoint rejects such members (EINVAL).  Kernel id 8 times the per-step evaluation. */
+pstd_status pstd_set_incidence_aux(pstd_grid* g, int b, const double khat[3], double k, double d_lo, double dd, long n1,
+                                   const double* psi0);
+
 /* Spin-dependent scattering (the paper's motivating magnetic case; the paper itself treats a
  * scalar wave function): the grid's batch members pair up as the spin-up and spin-down
  * components (2p, 2p + 1) of spinors p, coupled by W = V I + gamma sigma . B(r),
@@ -222,7 +237,8 @@ pstd_status pstd_stability_dt_max(const pstd_grid_desc* desc, double vmax, doubl
 /* Per-kernel timing with CUDA events on the grid's stream (off by default).  Kernel ids:
  * 0 x-pass, 1 y-pass, 2 z-pass (on DFT-window steps these also accumulate the running DFT),
  * 3 fused x+y pass (FP32 square planes of 64, 96 or 128, on steps without the DFT),
- * 4 transform/node preparation, 5 point transform, 6 far field, 7 V-term and TF/SF source.
+ * 4 transform/node preparation, 5 point transform, 6 far field, 7 V-term and TF/SF source,
+ * 8 the 1-D auxiliary incident wave (per-call coefficient table and per-step evaluation).
  * pstd_kernel_stats returns the launches and summed milliseconds since the last
  * pstd_set_timing(g, 1) (synchronises).  pstd_launch_count counts every kernel the grid
  * launched since creation. */

@@ -19,7 +19,7 @@ namespace {
 thread_local std::string g_create_error;
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kSizes[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384};
-constexpr int kKernelIds = 8;
+constexpr int kKernelIds = 9;
 
 bool supported_size(int n)
 {
@@ -41,12 +41,24 @@ struct MemberHost {
     bool packet = false;         // Gaussian wave packet (pstd_set_incidence_packet)
     double sigma = 1.0, d0 = 0.0;
     cd chi = cd(1.0, 0.0);       // spinor component's incident amplitude (pstd_set_incidence_spinor)
+    // 1-D auxiliary incident wave (pstd_set_incidence_aux): its Fourier modes l0 .. l0 + G0.size() - 1,
+    // psi_inc^n(d) = sum_m G0_m e^{i (q_m d - theta_m n)}
+    bool aux = false;
+    double aux_dt = 0, aux_dq = 0;
+    std::vector<cd> aux_G0;
+    std::vector<double> aux_theta, aux_q;
 };
 
 // The incident wave of member m at the first-contact corner r_O at time t (Eq. incpsiphasor's
 // integrand): the CW wave a(t) e^{-i w0 t}, or the packet at d = 0
 cd incident_at_origin(const MemberHost& m, double t, double hbar, double mass)
 {
+    if (m.aux) {   // d = 0 (Eq. pstd_psiinc)
+        const double n = std::nearbyint(t / m.aux_dt);
+        cd s(0.0, 0.0);
+        for (size_t i = 0; i < m.aux_G0.size(); ++i) s += m.aux_G0[i] * std::exp(cd(0.0, -m.aux_theta[i] * n));
+        return s;
+    }
     if (m.packet) {
         const double tau = hbar * t / (2.0 * mass * m.sigma * m.sigma);
         const double v = hbar * m.k / mass;
@@ -66,10 +78,12 @@ struct GraphKey {
     long long version = 0;
     const void* tfac = nullptr;
     const void* tenv = nullptr;
+    const void* aux_tab = nullptr;
+    const void* aux_inc = nullptr;
     bool operator==(const GraphKey& o) const
     {
         return valid && o.valid && n0 == o.n0 && nsteps == o.nsteps && cur == o.cur && version == o.version &&
-               tfac == o.tfac && tenv == o.tenv;
+               tfac == o.tfac && tenv == o.tenv && aux_tab == o.aux_tab && aux_inc == o.aux_inc;
     }
 };
 
@@ -121,6 +135,24 @@ struct pstd_grid {
     size_t tenv_cap = 0;
     void* proj[3] = {};                    // [member][i] khat_a (x_a - r_O,a), working precision
     unsigned long long packet_mask = 0;
+    // 1-D auxiliary incident waves (slots = aux members in member order)
+    unsigned long long aux_mask = 0;
+    int aux_nslot = 0, aux_nm = 0;          // slots; modes per slot (a multiple of 32, zero padded)
+    void* aux_t0[3] = {};                   // [slot][i] e^{i q_0 khat_a (x_a - r_O,a)}, working precision
+    void* aux_t1[3] = {};                   // ... e^{i dq ...}
+    void* aux_t32[3] = {};                  // ... e^{i 32 dq ...}
+    double2* aux_G0 = nullptr;              // [slot][m]
+    double* aux_theta = nullptr;
+    double* aux_q = nullptr;
+    void* aux_tab = nullptr;                // [slot][step of the call][m] G_m^n, working precision
+    size_t aux_tab_cap = 0;
+    void* aux_dtab = nullptr;               // i q_m G_m^n (PAPER form)
+    size_t aux_dtab_cap = 0;
+    void* aux_inc = nullptr;                // [slot][box node] psi_inc of the current step
+    size_t aux_inc_cap = 0;
+    void* aux_dinc = nullptr;               // d psi_inc / d d (PAPER form)
+    size_t aux_dinc_cap = 0;
+    long aux_call_steps = 0;                // steps of the call the table holds
     size_t tfac_cap = 0;
     double2* dft_phase = nullptr;          // [member][freq][window step] e^{+i omega t_n}
     size_t dft_phase_cap = 0;
@@ -478,10 +510,22 @@ pstd_status upload_members(pstd_grid* g)
         o.nfreq = m.nfreq;
         for (int f = 0; f < PSTD_MAX_FREQ; ++f) o.omega[f] = m.omega[f];
         o.packet = m.packet ? 1 : 0;
+        for (int a = 0; a < 3; ++a) o.khat[a] = m.khat[a];
     }
     CK(g, cudaMemcpyAsync(g->mem_dev, h.data(), sizeof(MemberDev) * g->batch, cudaMemcpyHostToDevice, g->stream));
     CK(g, cudaStreamSynchronize(g->stream));
     return PSTD_OK;
+}
+
+// the node box on which aux members need psi_inc: the V box (EXACT form) or the interior of
+// the TF/SF box, where the taper's derivatives live (PAPER form); n[] = 0 when empty
+void aux_box(const pstd_grid* g, int lo[3], int n[3])
+{
+    for (int a = 0; a < 3; ++a) {
+        if (g->desc.tfsf_mode == PSTD_TFSF_PAPER) { lo[a] = g->desc.tfsf_lo[a] + 1; n[a] = g->desc.tfsf_hi[a] - lo[a]; }
+        else { lo[a] = g->vlo[a]; n[a] = g->vhi[a] - g->vlo[a]; }
+    }
+    if (n[0] <= 0 || n[1] <= 0 || n[2] <= 0) n[0] = n[1] = n[2] = 0;
 }
 
 template <typename R> StepArgs<R> step_args(pstd_grid* g)
@@ -525,6 +569,10 @@ template <typename R> StepArgs<R> step_args(pstd_grid* g)
     a.gamma = R(g->gamma_b);
     for (int ax = 0; ax < 3; ++ax) a.proj[ax] = static_cast<const R*>(g->proj[ax]);
     a.tenv = static_cast<const R*>(g->tenv);
+    a.aux_mask = g->aux_mask;
+    a.aux_inc = static_cast<const C*>(g->aux_inc);
+    a.aux_dinc = static_cast<const C*>(g->aux_dinc);
+    aux_box(g, a.abox_lo, a.abox_n);
     return a;
 }
 
@@ -579,6 +627,8 @@ pstd_status upload_time_factors(pstd_grid* g, long long n0, long nsteps)
                 e[0] = alpha.real();
                 e[1] = alpha.imag();
                 e[2] = m.d0 + g->desc.hbar * m.k / g->desc.mass * t;
+            } else if (m.aux) {
+                tab[(size_t)s * g->batch + b] = m.chi;   // psi_inc itself comes from aux_eval_kernel
             } else {
                 tab[(size_t)s * g->batch + b] = m.chi * incident_at_origin(m, t, g->desc.hbar, g->desc.mass);
             }
@@ -615,6 +665,31 @@ pstd_status enqueue_step(pstd_grid* g, const StepArgs<R>& a, unsigned long long 
     // the V-term and source: folded into the z pass when x and y run fused; their own kernel
     // ahead of the separate x and y passes otherwise (where the DFT variants are heavier)
     const bool src_in_z = need_src && (g->use_xy || !mask);
+    if (g->aux_mask && need_src) {
+        // psi_inc of the aux members on the source box for this step (Eqs. pstd_psiinc, pstd_dpsiinc)
+        AuxEvalArgs<R> x;
+        std::memset(&x, 0, sizeof(x));
+        using C = typename StepArgs<R>::C;
+        for (int ax = 0; ax < 3; ++ax) {
+            x.t0[ax] = static_cast<const C*>(g->aux_t0[ax]);
+            x.t1[ax] = static_cast<const C*>(g->aux_t1[ax]);
+            x.t32[ax] = static_cast<const C*>(g->aux_t32[ax]);
+            x.n[ax] = g->desc.n[ax];
+            x.lo[ax] = a.abox_lo[ax];
+            x.bn[ax] = a.abox_n[ax];
+        }
+        const bool paper = g->desc.tfsf_mode == PSTD_TFSF_PAPER;
+        x.G = static_cast<const C*>(g->aux_tab);
+        x.dG = paper ? static_cast<const C*>(g->aux_dtab) : nullptr;
+        x.nm = g->aux_nm;
+        x.step_off = a.step - a.tfac_base;
+        x.slot_stride = (long long)g->aux_nm * g->aux_call_steps;
+        x.nslot = g->aux_nslot;
+        x.out = static_cast<C*>(g->aux_inc);
+        x.dout = paper ? static_cast<C*>(g->aux_dinc) : nullptr;
+        Timer t(g, 8);
+        CK(g, launch_aux_eval<R>(x, g->stream));
+    }
     if (need_src && !src_in_z) {
         Timer t(g, 7);
         CK(g, launch_source<R>(a, g->batch, g->stream));
@@ -693,6 +768,14 @@ pstd_status enqueue_steps(pstd_grid* g, const std::vector<PlannedStep<R>>& plan,
 {
     const bool need_src = g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0] || (g->spinor && g->bhi[0] > g->blo[0]);
     const size_t sb = (size_t)g->ncell * g->csize;
+    if (g->aux_mask && need_src && !plan.empty()) {
+        // the aux members' Fourier coefficients for every step of this call
+        using C = typename StepArgs<R>::C;
+        Timer t(g, 8);
+        CK(g, launch_aux_table<R>(g->aux_G0, g->aux_theta, g->aux_q, g->aux_nslot, g->aux_nm, plan[0].a.step, (long)plan.size(),
+                                  g->desc.tfsf_mode == PSTD_TFSF_PAPER, static_cast<C*>(g->aux_tab),
+                                  static_cast<C*>(g->aux_dtab), g->stream));
+    }
     for (size_t s = 0; s < plan.size(); ++s) {
         const PlannedStep<R>& p = plan[s];
         const long long n = p.a.step;
@@ -728,6 +811,20 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft 
     const long long n0 = g->n;
     pstd_status st0 = upload_time_factors(g, n0, nsteps);
     if (st0 != PSTD_OK) return st0;
+    if (g->aux_mask) {
+        int lo[3], bn[3];
+        aux_box(g, lo, bn);
+        const size_t nb = (size_t)bn[0] * bn[1] * bn[2];
+        const size_t tab = (size_t)g->aux_nslot * std::max(1L, nsteps) * g->aux_nm * g->csize;
+        const size_t inc = (size_t)g->aux_nslot * std::max<size_t>(1, nb) * g->csize;
+        const bool paper = g->desc.tfsf_mode == PSTD_TFSF_PAPER;
+        st0 = ensure(g, &g->aux_tab, g->aux_tab_cap, tab);
+        if (st0 == PSTD_OK) st0 = ensure(g, &g->aux_inc, g->aux_inc_cap, inc);
+        if (st0 == PSTD_OK && paper) st0 = ensure(g, &g->aux_dtab, g->aux_dtab_cap, tab);
+        if (st0 == PSTD_OK && paper) st0 = ensure(g, &g->aux_dinc, g->aux_dinc_cap, inc);
+        if (st0 != PSTD_OK) return st0;
+        g->aux_call_steps = std::max(1L, nsteps);
+    }
     // checkpoint recording for the adjoint: steps of the run from rest, recorded from step 0 on
     if (dft && !save && g->ckpt_record && g->ckpt_contig && g->n == 0) g->ckpt_upto = 0;
     const bool record = dft && !save && g->ckpt_record && g->ckpt_contig && g->ckpt_upto == g->n;
@@ -739,6 +836,8 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft 
     key.version = g->config_version;
     key.tfac = g->tfac;
     key.tenv = g->tenv;
+    key.aux_tab = g->aux_tab;
+    key.aux_inc = g->aux_inc;
     const bool graphable = g->graphs && dft && !save && !record && !g->timing && nsteps >= 2;
     if (graphable && g->graph_exec && g->graph_key == key) {
         plan_steps<R>(g, nsteps, dft, n0, nullptr);
@@ -1428,6 +1527,11 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     if (g->cap_stream) cudaStreamDestroy(g->cap_stream);
     for (void* p : {g->B[0], g->B[1], g->B[2]})
         if (p) cudaFree(p);
+    for (int a = 0; a < 3; ++a)
+        for (void* p : {g->aux_t0[a], g->aux_t1[a], g->aux_t32[a]})
+            if (p) cudaFree(p);
+    for (void* p : {(void*)g->aux_G0, (void*)g->aux_theta, (void*)g->aux_q, g->aux_tab, g->aux_dtab, g->aux_inc, g->aux_dinc})
+        if (p) cudaFree(p);
     for (void* p : {g->tenv, g->proj[0], g->proj[1], g->proj[2]})
         if (p) cudaFree(p);
     for (void* p : {g->adj_table, g->adj_partial, g->adj_rec, g->adj_PA, (void*)g->adj_gpts, (void*)g->adj_out, g->adj_J,
@@ -1600,6 +1704,176 @@ pstd_status set_incidence_common(pstd_grid* g, int b, const double khat[3], doub
 }
 }  // namespace
 
+namespace {
+// Forward DFT in place, X_l = sum_j x_j e^{-2 pi i j l / n} (n a power of two; radix 2).
+void fft_pow2(std::vector<cd>& a)
+{
+    const size_t n = a.size();
+    for (size_t i = 1, j = 0; i < n; ++i) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        for (size_t i = 0; i < n; i += len)
+            for (size_t j = 0; j < len / 2; ++j) {
+                const cd w = std::exp(cd(0.0, -2.0 * kPi * (double)j / (double)len));
+                const cd u = a[i + j], v = a[i + j + len / 2] * w;
+                a[i + j] = u + v;
+                a[i + j + len / 2] = u - v;
+            }
+    }
+}
+
+// Device tables of every aux member (slots in member order), rebuilt whenever one changes.
+pstd_status rebuild_aux(pstd_grid* g)
+{
+    CK(g, cudaStreamSynchronize(g->stream));
+    for (int a = 0; a < 3; ++a)
+        for (void** p : {&g->aux_t0[a], &g->aux_t1[a], &g->aux_t32[a]}) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+    for (void* p : {(void*)g->aux_G0, (void*)g->aux_theta, (void*)g->aux_q})
+        if (p) cudaFree(p);
+    g->aux_G0 = nullptr;
+    g->aux_theta = g->aux_q = nullptr;
+    g->aux_mask = 0;
+    g->aux_nslot = g->aux_nm = 0;
+    std::vector<int> slots;
+    size_t nm = 0;
+    for (int b = 0; b < g->batch; ++b)
+        if (g->mem[b].aux) {
+            g->aux_mask |= 1ull << b;
+            slots.push_back(b);
+            nm = std::max(nm, g->mem[b].aux_G0.size());
+        }
+    if (slots.empty()) return PSTD_OK;
+    nm = (nm + 31) / 32 * 32;
+    const int ns = (int)slots.size();
+    std::vector<double2> G0(ns * nm, make_double2(0.0, 0.0));
+    std::vector<double> th(ns * nm, 0.0), q(ns * nm, 0.0);
+    const pstd_grid_desc& d = g->desc;
+    std::vector<cd> t0[3], t1[3], t32[3];
+    for (int a = 0; a < 3; ++a) { t0[a].resize((size_t)ns * d.n[a]); t1[a] = t0[a]; t32[a] = t0[a]; }
+    for (int s = 0; s < ns; ++s) {
+        const MemberHost& m = g->mem[slots[s]];
+        const size_t cnt = m.aux_G0.size();
+        const double q0 = m.aux_q[0], dq = cnt > 1 ? m.aux_q[1] - m.aux_q[0] : m.aux_dq;
+        for (size_t i = 0; i < nm; ++i) {
+            const size_t k = (size_t)s * nm + i;
+            if (i < cnt) {
+                G0[k] = make_double2(m.aux_G0[i].real(), m.aux_G0[i].imag());
+                th[k] = m.aux_theta[i];
+                q[k] = m.aux_q[i];
+            } else {
+                q[k] = q0 + (double)i * dq;   // padding: G0 = 0
+            }
+        }
+        for (int a = 0; a < 3; ++a)
+            for (int i = 0; i < d.n[a]; ++i) {
+                const double pr = m.khat[a] * (coord(d, a, i) - m.rO[a]);   // Eq. inc_d, one axis
+                t0[a][(size_t)s * d.n[a] + i] = std::exp(cd(0.0, q0 * pr));
+                t1[a][(size_t)s * d.n[a] + i] = std::exp(cd(0.0, dq * pr));
+                t32[a][(size_t)s * d.n[a] + i] = std::exp(cd(0.0, 32.0 * dq * pr));
+            }
+    }
+    for (int a = 0; a < 3; ++a) {
+        pstd_status st = upload_complex(g, &g->aux_t0[a], t0[a]);
+        if (st == PSTD_OK) st = upload_complex(g, &g->aux_t1[a], t1[a]);
+        if (st == PSTD_OK) st = upload_complex(g, &g->aux_t32[a], t32[a]);
+        if (st != PSTD_OK) return st;
+    }
+    CK(g, dalloc(&g->aux_G0, G0.size() * sizeof(double2)));
+    CK(g, dalloc(&g->aux_theta, th.size() * sizeof(double)));
+    CK(g, dalloc(&g->aux_q, q.size() * sizeof(double)));
+    CK(g, cudaMemcpy(g->aux_G0, G0.data(), G0.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    CK(g, cudaMemcpy(g->aux_theta, th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(g, cudaMemcpy(g->aux_q, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice));
+    g->aux_nslot = ns;
+    g->aux_nm = (int)nm;
+    return PSTD_OK;
+}
+
+// member b no longer uses the auxiliary wave
+pstd_status drop_aux(pstd_grid* g, int b)
+{
+    if (!g->mem[b].aux) return PSTD_OK;
+    g->mem[b].aux = false;
+    return rebuild_aux(g);
+}
+}  // namespace
+
+pstd_status pstd_set_incidence_aux(pstd_grid* g, int b, const double khat[3], double k, double d_lo, double dd, long n1,
+                                   const double* psi0)
+{
+    if (!g || !khat || !psi0) return fail(g, PSTD_EINVAL, "null argument");
+    DeviceGuard dg(g->dev);
+    ++g->config_version;
+    g->ckpt_upto = -1;
+    g->ckpt_contig = false;
+    pstd_status st = check_member(g, b);
+    if (st != PSTD_OK) return st;
+    if (g->spinor) return fail(g, PSTD_EINVAL, "spinor grids take pstd_set_incidence_spinor");
+    if (n1 < 8 || n1 > (1L << 16) || (n1 & (n1 - 1))) return fail(g, PSTD_EINVAL, "n1 must be a power of two in [8, 65536]");
+    if (!(dd > 0) || !std::isfinite(d_lo)) return fail(g, PSTD_EINVAL, "d_lo or dd");
+    for (long i = 0; i < 2 * n1; ++i)
+        if (!std::isfinite(psi0[i])) return fail(g, PSTD_EINVAL, "the profile is not finite");
+    st = set_incidence_common(g, b, khat, k);
+    if (st != PSTD_OK) return st;
+    MemberHost& m = g->mem[b];
+    const pstd_grid_desc& d = g->desc;
+    // the axis must hold every node of the TF/SF box: d in [0, dmax] from the first-contact corner
+    double dmax = 0;
+    for (int c = 0; c < 8; ++c) {
+        double v = 0;
+        for (int a = 0; a < 3; ++a) v += m.khat[a] * (coord(d, a, (c >> a) & 1 ? d.tfsf_hi[a] : d.tfsf_lo[a]) - m.rO[a]);
+        dmax = std::max(dmax, v);
+    }
+    if (d_lo > 0 || d_lo + (double)n1 * dd < dmax)
+        return fail(g, PSTD_EINVAL, "the 1-D axis [d_lo, d_lo + n1 dd) must cover the TF/SF box, d in [0, khat . diagonal]");
+    // every mode of the 1-D leapfrog must be stable: dt eta hbar q^2 / 2m <= 1 (Eq. PSTDstability, 1-D)
+    const double qn = kPi / dd;
+    if (d.dt * m.eta * d.hbar * qn * qn / (2.0 * d.mass) > 1.0)
+        return fail(g, PSTD_EUNSTABLE, "the 1-D auxiliary axis is too fine for dt (dt eta hbar (pi/dd)^2 / 2m > 1)");
+    std::vector<cd> F(n1);
+    for (long i = 0; i < n1; ++i) F[i] = cd(psi0[2 * i], psi0[2 * i + 1]);
+    fft_pow2(F);
+    double fmax = 0;
+    for (const cd& v : F) fmax = std::max(fmax, std::abs(v));
+    // modes in signed order l = -n1/2 .. n1/2 - 1 (FFT index (l + n1) mod n1); keep the span of
+    // those above 1e-15 (FP64) or 1e-10 (FP32) of the largest: the n1 <= 65536 dropped ones sum
+    // below the working precision's rounding of psi_inc
+    const double cut = (g->prec == PSTD_F64 ? 1e-15 : 1e-10) * fmax;
+    long lo = n1, hi = -n1;
+    for (long l = -n1 / 2; l < n1 / 2; ++l)
+        if (std::abs(F[(l + n1) % n1]) > cut) { lo = std::min(lo, l); hi = std::max(hi, l); }
+    if (hi < lo) lo = hi = 0;
+    m.aux_G0.clear();
+    m.aux_theta.clear();
+    m.aux_q.clear();
+    for (long l = lo; l <= hi; ++l) {
+        const double ql = 2.0 * kPi * (double)l / ((double)n1 * dd);
+        const double al = d.dt * m.eta * d.hbar * ql * ql / (2.0 * d.mass);
+        // F_l^n = F_l^0 z^n, z = -i a + sqrt(1 - a^2) = e^{-i asin a} (the scheme's physical root;
+        // psi1^{-1} is its exact backward step); the phase at d: e^{i q_l (d - d_lo)}
+        m.aux_G0.push_back(F[(l + n1) % n1] / (double)n1 * std::exp(cd(0.0, -ql * d_lo)));
+        m.aux_theta.push_back(std::asin(al));
+        m.aux_q.push_back(ql);
+    }
+    m.aux_dq = 2.0 * kPi / ((double)n1 * dd);
+    m.aux_dt = d.dt;
+    m.aux = true;
+    m.ramp = 0.0;
+    m.packet = false;
+    m.chi = cd(1.0, 0.0);
+    g->packet_mask &= ~(1ull << b);
+    st = rebuild_aux(g);
+    if (st != PSTD_OK) return st;
+    return upload_members(g);
+}
+
 pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double k, int envelope, double ramp_time)
 {
     if (!g || !khat) return fail(g, PSTD_EINVAL, "null argument");
@@ -1619,6 +1893,8 @@ pstd_status pstd_set_incidence(pstd_grid* g, int b, const double khat[3], double
     m.packet = false;
     m.chi = cd(1.0, 0.0);
     g->packet_mask &= ~(1ull << b);
+    st = drop_aux(g, b);
+    if (st != PSTD_OK) return st;
     return upload_members(g);
 }
 
@@ -1644,6 +1920,8 @@ pstd_status pstd_set_incidence_packet(pstd_grid* g, int b, const double khat[3],
     m.sigma = sigma;
     m.d0 = d0;
     g->packet_mask |= 1ull << b;
+    st = drop_aux(g, b);
+    if (st != PSTD_OK) return st;
     return upload_members(g);
 }
 
@@ -1805,15 +2083,25 @@ pstd_status pstd_get_field(pstd_grid* g, int b, int which, void* out, int mem)
         const double t = g->n * d.dt;
         const double env = (m.ramp <= 0 || t >= m.ramp) ? 1.0 : (t <= 0 ? 0.0 : 0.5 * (1.0 - std::cos(kPi * t / m.ramp)));
         const cd s = env * std::exp(cd(0.0, -m.w0 * t));
+        std::vector<cd> Gn;   // aux members: the step's coefficients, psi_inc(d) = sum Gn_m e^{i q_m d}
+        if (m.aux)
+            for (size_t i = 0; i < m.aux_G0.size(); ++i) Gn.push_back(m.aux_G0[i] * std::exp(cd(0.0, -m.aux_theta[i] * (double)g->n)));
         for (int k = 0; k < d.n[2]; ++k)
             for (int j = 0; j < d.n[1]; ++j)
                 for (int i = 0; i < d.n[0]; ++i) {
                     const double zz = z[0][i] * z[1][j] * z[2][k];
                     if (zz == 0.0) continue;
                     const double r[3] = {coord(d, 0, i), coord(d, 1, j), coord(d, 2, k)};
-                    double ph = 0;
-                    for (int a = 0; a < 3; ++a) ph += m.k * m.khat[a] * (r[a] - m.rO[a]);
-                    const cd v = zz * s * std::exp(cd(0.0, ph));
+                    double dd = 0;
+                    for (int a = 0; a < 3; ++a) dd += m.khat[a] * (r[a] - m.rO[a]);
+                    cd v;
+                    if (m.aux) {
+                        cd w(0.0, 0.0);
+                        for (size_t q = 0; q < Gn.size(); ++q) w += Gn[q] * std::exp(cd(0.0, m.aux_q[q] * dd));
+                        v = zz * w;
+                    } else {
+                        v = zz * s * std::exp(cd(0.0, m.k * dd));
+                    }
                     const size_t idx = ((size_t)k * d.n[1] + j) * d.n[0] + i;
                     if (g->prec == PSTD_F64) {
                         double* o = static_cast<double*>(out) + 2 * idx;
@@ -1998,7 +2286,7 @@ pstd_status pstd_adjoint_gradient(pstd_grid* g, long nsteps, const void* dl_dpha
     DeviceGuard dg(g->dev);
     const MemberHost& m = g->mem[0];
     if (!m.has_inc) return fail(g, PSTD_ESTATE, "pstd_set_incidence first");
-    if (m.packet) return fail(g, PSTD_EINVAL, "the adjoint supports the CW incidence");
+    if (m.packet || m.aux) return fail(g, PSTD_EINVAL, "the adjoint supports the CW incidence");
     if (m.nfreq < 1 || m.len < 1) return fail(g, PSTD_ESTATE, "pstd_huygens_dft first (the loss is a function of the phasors)");
     if (m.first + m.len > nsteps) return fail(g, PSTD_EINVAL, "the DFT window must end within nsteps");
     for (int a = 0; a < 3; ++a)
@@ -2182,7 +2470,7 @@ pstd_status pstd_set_magnetic_field(pstd_grid* g, const void* Bx, const void* By
     if (g->batch % 2) return fail(g, PSTD_EINVAL, "spinor grids pair the batch members: the batch must be even");
     if (g->desc.tfsf_mode != PSTD_TFSF_EXACT) return fail(g, PSTD_EINVAL, "spinor grids use the EXACT TF/SF form");
     if (!std::isfinite(gamma)) return fail(g, PSTD_EINVAL, "gamma");
-    if (g->packet_mask) return fail(g, PSTD_EINVAL, "spinor grids take pstd_set_incidence_spinor");
+    if (g->packet_mask || g->aux_mask) return fail(g, PSTD_EINVAL, "spinor grids take pstd_set_incidence_spinor");
     const pstd_grid_desc& d = g->desc;
     std::vector<double> h[3];
     for (int a = 0; a < 3; ++a) {
@@ -2257,6 +2545,8 @@ pstd_status pstd_set_incidence_spinor(pstd_grid* g, int p, const double khat[3],
         m.packet = false;
         m.chi = cd(chi[2 * c], chi[2 * c + 1]);
         g->packet_mask &= ~(1ull << b);
+        st = drop_aux(g, b);
+        if (st != PSTD_OK) return st;
     }
     return upload_members(g);
 }

@@ -7,6 +7,9 @@ template cudaError_t launch_xpass<float>(const StepArgs<float>&, const DftArgs<f
 template cudaError_t launch_ypass<float>(const StepArgs<float>&, const DftArgs<float>*, int, cudaStream_t);
 template cudaError_t launch_zpass<float>(const StepArgs<float>&, const DftArgs<float>*, bool, int, cudaStream_t);
 template cudaError_t launch_source<float>(const StepArgs<float>&, int, cudaStream_t);
+template cudaError_t launch_aux_table<float>(const double2*, const double*, const double*, int, int, long long, long, bool,
+                                           float2*, float2*, cudaStream_t);
+template cudaError_t launch_aux_eval<float>(const AuxEvalArgs<float>&, cudaStream_t);
 template bool xypass_available<float>(int, int);
 template bool pipe_y_available<float>(int);
 template cudaError_t launch_xypass<float>(const StepArgs<float>&, const DftArgs<float>*, const DftArgs<float>*, int, cudaStream_t);

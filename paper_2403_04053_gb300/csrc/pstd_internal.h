@@ -20,6 +20,7 @@ struct MemberDev {
     double omega[PSTD_MAX_FREQ];   // DFT angular frequencies
     int nfreq;
     int packet;     // incident Gaussian wave packet (else CW)
+    double khat[3]; // unit incidence direction (the 1-D auxiliary wave's d axis)
     int dft_active; // set per step by the host (bit mask passed separately)
 };
 
@@ -61,8 +62,43 @@ template <typename R> struct StepArgs {
     const R* B[3];
     int blo[3], bhi[3];
     R gamma;
+    // members driven by the 1-D auxiliary incident wave (pstd_set_incidence_aux): psi_inc (and,
+    // for the PAPER form, d psi_inc / d d) at the source box's nodes for the current step, from
+    // aux_eval_kernel; [slot][node of the box], slot = rank of the member among aux_mask's bits
+    unsigned long long aux_mask;
+    const C* aux_inc;
+    const C* aux_dinc;
+    int abox_lo[3], abox_n[3];
     int batch;
 };
+
+// The 1-D auxiliary incident wave of one step (Eqs. pstd_psiinc, pstd_dpsiinc) on a node box:
+// psi_inc(d) = sum_m G_m^n e^{i q_m d}, q_m = q_0 + m dq, d = khat . (r - r_O), with
+// e^{i q_0 d}, e^{i dq d} and e^{i 32 dq d} as products of per-axis tables.
+template <typename R> struct AuxEvalArgs {
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const C* t0[3];           // e^{i q_0 khat_a (x_a - r_O,a)}: [slot * n_a + i]
+    const C* t1[3];           // e^{i dq khat_a (x_a - r_O,a)}
+    const C* t32[3];          // e^{i 32 dq khat_a (x_a - r_O,a)}
+    const C* G;               // G_m^n: [slot][step of the call][m], nm a multiple of 32 (zero padded)
+    const C* dG;              // i q_m G_m^n (PAPER form), same layout; null for the EXACT form
+    int nm;
+    long long slot_stride;    // entries per slot of G (steps of the call * nm)
+    long long step_off;       // (step - first step of the call)
+    int nslot;
+    int n[3];                 // grid size
+    int lo[3], bn[3];         // the box
+    C* out;                   // [slot][box node]
+    C* dout;                  // PAPER form: d psi_inc / d d
+};
+
+// G_m^n = G0_m e^{-i theta_m n} (and i q_m G_m^n) for steps [n0, n0 + nsteps) of every slot,
+// phases in FP64; G0, theta, q: [slot][m] doubles (G0 complex)
+template <typename R>
+cudaError_t launch_aux_table(const double2* G0, const double* theta, const double* q, int nslot, int nm, long long n0,
+                             long nsteps, bool deriv, typename std::conditional<sizeof(R) == 4, float2, double2>::type* G,
+                             typename std::conditional<sizeof(R) == 4, float2, double2>::type* dG, cudaStream_t s);
+template <typename R> cudaError_t launch_aux_eval(const AuxEvalArgs<R>& a, cudaStream_t s);
 
 // Running-DFT arguments for the passes that accumulate on DFT-window steps.
 template <typename R> struct DftArgs {

@@ -437,9 +437,19 @@ __device__ __forceinline__ C packet_envelope(const StepArgs<R>& a, int b, int x,
 }
 
 // the incident wave of member b at node (x, y, z), step a.step; s = the member's time factor
+// index of (x, y, z) in the auxiliary-wave buffers of member b (an aux member, node in the box)
+template <typename R>
+__device__ __forceinline__ long long aux_index(const StepArgs<R>& a, int b, int x, int y, int z)
+{
+    const int slot = __popcll(a.aux_mask & ((1ull << b) - 1ull));
+    const long long nb = (long long)a.abox_n[0] * a.abox_n[1] * a.abox_n[2];
+    return slot * nb + ((long long)(z - a.abox_lo[2]) * a.abox_n[1] + (y - a.abox_lo[1])) * a.abox_n[0] + (x - a.abox_lo[0]);
+}
+
 template <typename R, typename C>
 __device__ __forceinline__ C incident_wave(const StepArgs<R>& a, int b, C s, int x, int y, int z)
 {
+    if ((a.aux_mask >> b) & 1ull) return cmul(s, a.aux_inc[aux_index(a, b, x, y, z)]);
     C w = incident_at<R, C>(a, b, s, x, y, z);
     if ((a.packet_mask >> b) & 1ull) w = cmul(w, packet_envelope<R, C>(a, b, x, y, z));
     return w;
@@ -495,8 +505,15 @@ __device__ __forceinline__ C source_acc(const StepArgs<R>& a, int b, C s, int x,
         const R zz = a.zeta[2][z], zz1 = a.zeta1[2][z], zz2 = a.zeta2[2][z];
         const R lap = zx2 * zy * zz + zx * zy2 * zz + zx * zy * zz2;
         const MemberDev& md = a.mem[b];
-        const R kg = R(md.k[0]) * zx1 * zy * zz + R(md.k[1]) * zx * zy1 * zz + R(md.k[2]) * zx * zy * zz1;
-        acc = cadd(acc, cscale(cmul(incident_at<R, C>(a, b, s, x, y, z), mk<C>(lap, R(2) * kg)), a.h2m));   // CW only
+        if ((a.aux_mask >> b) & 1ull) {
+            // hbar^2/2m [lap(zeta) psi_inc + 2 (khat . grad zeta) d psi_inc / d d] (Eq. pstd_dpsiinc)
+            const R kg = R(md.khat[0]) * zx1 * zy * zz + R(md.khat[1]) * zx * zy1 * zz + R(md.khat[2]) * zx * zy * zz1;
+            const long long e = aux_index(a, b, x, y, z);
+            acc = cadd(acc, cscale(cadd(cscale(a.aux_inc[e], lap), cscale(a.aux_dinc[e], R(2) * kg)), a.h2m));
+        } else {
+            const R kg = R(md.k[0]) * zx1 * zy * zz + R(md.k[1]) * zx * zy1 * zz + R(md.k[2]) * zx * zy * zz1;
+            acc = cadd(acc, cscale(cmul(incident_at<R, C>(a, b, s, x, y, z), mk<C>(lap, R(2) * kg)), a.h2m));   // CW
+        }
     }
     return acc;
 }
@@ -897,6 +914,111 @@ cudaError_t launch_xypass(const StepArgs<R>& a, const DftArgs<R>* dx, const DftA
     default: return cudaErrorInvalidValue;
     }
 }
+// ---------------------------------------------------------------------------------
+// the 1-D auxiliary incident wave (Section 2.2.3)
+// ---------------------------------------------------------------------------------
+// G_m^n = G0_m e^{-i theta_m n} for the steps of one call: the Fourier coefficients of the 1-D
+// leapfrog's solution, in which every mode advances by its root e^{-i theta_m} per step
+// (theta_m = asin(dt eta hbar q_m^2 / 2m)); phases and products in FP64, rounded once
+template <typename R>
+__global__ void __launch_bounds__(256) aux_table_kernel(const double2* G0, const double* theta, const double* q, int nslot,
+                                                        int nm, long long n0, long nsteps, int deriv,
+                                                        typename StepArgs<R>::C* G, typename StepArgs<R>::C* dG)
+{
+    step_kernel_entry();
+    using C = typename StepArgs<R>::C;
+    const long long total = (long long)nslot * nsteps * nm;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(e % nm);
+        const long long rest = e / nm;
+        const long long st = rest % nsteps;
+        const int slot = (int)(rest / nsteps);
+        const long long k = (long long)slot * nm + m;
+        double sn, cs;
+        sincos(-theta[k] * (double)(n0 + st), &sn, &cs);
+        const double gr = G0[k].x * cs - G0[k].y * sn, gi = G0[k].x * sn + G0[k].y * cs;
+        G[e] = mk<C>(R(gr), R(gi));
+        if (deriv) dG[e] = mk<C>(R(-q[k] * gi), R(q[k] * gr));
+    }
+}
+
+constexpr int kAuxChunk = 1024;   // modes staged in shared memory at a time (a multiple of 32)
+
+// psi_inc^n (and d psi_inc^n / d d) at every node of the box for every aux slot: the series of
+// Eqs. pstd_psiinc, pstd_dpsiinc, sum_m G_m e^{i (q_0 + m dq) d} = e^{i q_0 d} P(u), u = e^{i dq d},
+// P(u) = sum_m G_m u^m evaluated by Horner's rule in blocks of 32 modes (u within a block, u^32
+// from block to block): one complex multiply-add per mode, at most 32 + nm / 32 rounded steps
+template <typename R> __global__ void __launch_bounds__(256) aux_eval_kernel(const __grid_constant__ AuxEvalArgs<R> a)
+{
+    step_kernel_entry();
+    using C = typename StepArgs<R>::C;
+    __shared__ C sg[kAuxChunk];
+    __shared__ C sd[kAuxChunk];
+    const int slot = blockIdx.y;
+    const long long nb = (long long)a.bn[0] * a.bn[1] * a.bn[2];
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool act = e < nb;
+    const bool deriv = a.dG != nullptr;
+    const C zero = mk<C>(R(0), R(0));
+    C base = zero, u = zero, u32 = zero, acc = zero, dacc = zero;
+    if (act) {
+        const int x = a.lo[0] + (int)(e % a.bn[0]);
+        const int y = a.lo[1] + (int)((e / a.bn[0]) % a.bn[1]);
+        const int z = a.lo[2] + (int)(e / ((long long)a.bn[0] * a.bn[1]));
+        const long long ix = (long long)slot * a.n[0] + x, iy = (long long)slot * a.n[1] + y, iz = (long long)slot * a.n[2] + z;
+        base = cmul(cmul(a.t0[0][ix], a.t0[1][iy]), a.t0[2][iz]);
+        u = cmul(cmul(a.t1[0][ix], a.t1[1][iy]), a.t1[2][iz]);
+        u32 = cmul(cmul(a.t32[0][ix], a.t32[1][iy]), a.t32[2][iz]);
+    }
+    const C* G = a.G + slot * a.slot_stride + a.step_off * a.nm;
+    const C* dG = deriv ? a.dG + slot * a.slot_stride + a.step_off * a.nm : nullptr;
+    for (int c0 = ((a.nm - 1) / kAuxChunk) * kAuxChunk; c0 >= 0; c0 -= kAuxChunk) {
+        const int cn = min(kAuxChunk, a.nm - c0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < cn; i += blockDim.x) {
+            sg[i] = G[c0 + i];
+            if (deriv) sd[i] = dG[c0 + i];
+        }
+        __syncthreads();
+        if (!act) continue;
+        for (int b0 = cn - 32; b0 >= 0; b0 -= 32) {
+            C p = sg[b0 + 31];
+#pragma unroll
+            for (int j = 30; j >= 0; --j) p = cadd(cmul(p, u), sg[b0 + j]);
+            acc = cadd(cmul(acc, u32), p);
+            if (deriv) {
+                C dp = sd[b0 + 31];
+#pragma unroll
+                for (int j = 30; j >= 0; --j) dp = cadd(cmul(dp, u), sd[b0 + j]);
+                dacc = cadd(cmul(dacc, u32), dp);
+            }
+        }
+    }
+    if (act) {
+        a.out[slot * nb + e] = cmul(base, acc);
+        if (deriv) a.dout[slot * nb + e] = cmul(base, dacc);
+    }
+}
+
+template <typename R>
+cudaError_t launch_aux_table(const double2* G0, const double* theta, const double* q, int nslot, int nm, long long n0,
+                             long nsteps, bool deriv, typename std::conditional<sizeof(R) == 4, float2, double2>::type* G,
+                             typename std::conditional<sizeof(R) == 4, float2, double2>::type* dG, cudaStream_t s)
+{
+    const long long total = (long long)nslot * nsteps * nm;
+    if (total <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<long long>((total + 255) / 256, 152LL * 16);
+    return launch_step_kernel(aux_table_kernel<R>, dim3(blocks), dim3(256), 0, s, G0, theta, q, nslot, nm, n0, nsteps,
+                              deriv ? 1 : 0, G, dG);
+}
+
+template <typename R> cudaError_t launch_aux_eval(const AuxEvalArgs<R>& a, cudaStream_t s)
+{
+    const long long nb = (long long)a.bn[0] * a.bn[1] * a.bn[2];
+    if (nb <= 0 || a.nslot <= 0) return cudaSuccess;
+    return launch_step_kernel(aux_eval_kernel<R>, dim3((unsigned)((nb + 255) / 256), (unsigned)a.nslot), dim3(256), 0, s, a);
+}
+
 template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch, cudaStream_t s)
 {
     int lo[3], hi[3];

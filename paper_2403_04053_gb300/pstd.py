@@ -26,7 +26,8 @@ FIELD_CURRENT, FIELD_PREVIOUS, FIELD_SCATTERED = 0, 1, 2
 MAX_FREQ = 16
 
 STATUS = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EUNSTABLE", 5: "ESTATE", 6: "ENONFINITE", 7: "ETIMEOUT"}
-KERNELS = {"xpass": 0, "ypass": 1, "zpass": 2, "xypass": 3, "prepare": 4, "transform": 5, "far_field": 6, "source": 7}
+KERNELS = {"xpass": 0, "ypass": 1, "zpass": 2, "xypass": 3, "prepare": 4, "transform": 5, "far_field": 6, "source": 7,
+           "aux": 8}
 
 
 class PstdError(RuntimeError):
@@ -71,6 +72,8 @@ _SIGS = {
     "pstd_set_checkpointing": (c_int, [c_void_p, c_long, c_long]),
     "pstd_set_incidence_packet": (c_int, [c_void_p, c_int, POINTER(c_double), c_double, c_double, c_double]),
     "pstd_set_graphs": (c_int, [c_void_p, c_int]),
+    "pstd_set_incidence_aux": (c_int, [c_void_p, c_int, POINTER(c_double), c_double, c_double, c_double, c_long,
+                                        c_void_p]),
     "pstd_set_magnetic_field": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int, c_int]),
     "pstd_set_incidence_spinor": (c_int, [c_void_p, c_int, POINTER(c_double), c_double, c_double, POINTER(c_double)]),
     "pstd_graph_replays": (c_int, [c_void_p, POINTER(c_long)]),
@@ -205,6 +208,14 @@ class Grid:
     def set_incidence(self, b: int, khat, k: float, ramp_time: float, envelope: int = ENV_CW_RAMP):
         kh = (c_double * 3)(*[float(v) for v in khat])
         self._c(self.lib.pstd_set_incidence(self.h, b, kh, float(k), envelope, float(ramp_time)), "pstd_set_incidence")
+
+    def set_incidence_aux(self, b: int, khat, k: float, d_lo: float, dd: float, psi0):
+        """Incidence from the 1-D auxiliary wave (pstd_set_incidence_aux); psi0: n1 complex samples
+        of the profile at d_lo + m dd, t = 0."""
+        kh = (c_double * 3)(*[float(v) for v in khat])
+        p = np.ascontiguousarray(psi0, dtype=np.complex128)
+        self._c(self.lib.pstd_set_incidence_aux(self.h, b, kh, float(k), float(d_lo), float(dd), p.size,
+                                                p.ctypes.data_as(c_void_p)), "pstd_set_incidence_aux")
 
     def set_magnetic_field(self, B, gamma: float):
         """Spinor coupling gamma sigma . B (pstd_set_magnetic_field); B = (Bx, By, Bz) host arrays."""
