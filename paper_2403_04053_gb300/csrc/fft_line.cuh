@@ -187,18 +187,20 @@ template <int RAD, int DIR, typename C> __device__ __forceinline__ void dft(C* x
 // of every radix so each thread runs E / R butterflies per stage
 // ---------------------------------------------------------------------------------
 template <int N> struct Plan;
-template <> struct Plan<8>   { static constexpr int T = 1;  static constexpr int S = 1; static constexpr int R[3] = {8, 0, 0}; };
-template <> struct Plan<12>  { static constexpr int T = 1;  static constexpr int S = 1; static constexpr int R[3] = {12, 0, 0}; };
-template <> struct Plan<16>  { static constexpr int T = 1;  static constexpr int S = 1; static constexpr int R[3] = {16, 0, 0}; };
-template <> struct Plan<24>  { static constexpr int T = 2;  static constexpr int S = 2; static constexpr int R[3] = {12, 2, 0}; };
-template <> struct Plan<32>  { static constexpr int T = 4;  static constexpr int S = 2; static constexpr int R[3] = {8, 4, 0}; };
-template <> struct Plan<48>  { static constexpr int T = 4;  static constexpr int S = 2; static constexpr int R[3] = {12, 4, 0}; };
-template <> struct Plan<64>  { static constexpr int T = 8;  static constexpr int S = 2; static constexpr int R[3] = {8, 8, 0}; };
-template <> struct Plan<96>  { static constexpr int T = 4;  static constexpr int S = 2; static constexpr int R[3] = {12, 8, 0}; };
-template <> struct Plan<128> { static constexpr int T = 8;  static constexpr int S = 2; static constexpr int R[3] = {16, 8, 0}; };
-template <> struct Plan<192> { static constexpr int T = 16; static constexpr int S = 3; static constexpr int R[3] = {12, 4, 4}; };
-template <> struct Plan<256> { static constexpr int T = 16; static constexpr int S = 2; static constexpr int R[3] = {16, 16, 0}; };
-template <> struct Plan<384> { static constexpr int T = 16; static constexpr int S = 3; static constexpr int R[3] = {12, 8, 4}; };
+template <> struct Plan<8>   { static constexpr int T = 1;  static constexpr int S = 1; static constexpr int R[4] = {8, 0, 0, 0}; };
+template <> struct Plan<12>  { static constexpr int T = 1;  static constexpr int S = 1; static constexpr int R[4] = {12, 0, 0, 0}; };
+template <> struct Plan<16>  { static constexpr int T = 1;  static constexpr int S = 1; static constexpr int R[4] = {16, 0, 0, 0}; };
+template <> struct Plan<24>  { static constexpr int T = 2;  static constexpr int S = 2; static constexpr int R[4] = {12, 2, 0, 0}; };
+template <> struct Plan<32>  { static constexpr int T = 4;  static constexpr int S = 2; static constexpr int R[4] = {8, 4, 0, 0}; };
+template <> struct Plan<48>  { static constexpr int T = 4;  static constexpr int S = 2; static constexpr int R[4] = {12, 4, 0, 0}; };
+template <> struct Plan<64>  { static constexpr int T = 8;  static constexpr int S = 2; static constexpr int R[4] = {8, 8, 0, 0}; };
+template <> struct Plan<96>  { static constexpr int T = 4;  static constexpr int S = 2; static constexpr int R[4] = {12, 8, 0, 0}; };
+template <> struct Plan<128> { static constexpr int T = 8;  static constexpr int S = 2; static constexpr int R[4] = {16, 8, 0, 0}; };
+template <> struct Plan<192> { static constexpr int T = 16; static constexpr int S = 3; static constexpr int R[4] = {12, 4, 4, 0}; };
+template <> struct Plan<256> { static constexpr int T = 16; static constexpr int S = 2; static constexpr int R[4] = {16, 16, 0, 0}; };
+// 384: four stages with 32 threads a line, so that a thread holds 12 values (not 24) and a
+// 1024-thread CTA of 32 lines fits 64 registers a thread
+template <> struct Plan<384> { static constexpr int T = 32; static constexpr int S = 4; static constexpr int R[4] = {12, 4, 4, 2}; };
 
 #ifndef PSTD_LANES
 #define PSTD_LANES 32
@@ -274,7 +276,7 @@ __device__ __forceinline__ void kinetic_line(C (&v)[E], C* sm, int lane, int j, 
     using P = Plan<N>;
     constexpr int T = P::T;
     static_assert(E == N / T, "E");
-    constexpr int R0 = P::R[0], R1 = P::R[1], R2 = P::R[2];
+    constexpr int R0 = P::R[0], R1 = P::R[1], R2 = P::R[2], R3 = P::R[3];
     if constexpr (P::S == 1) {
         if constexpr (FIRST_FROM_SMEM) {
 #pragma unroll
@@ -292,6 +294,18 @@ __device__ __forceinline__ void kinetic_line(C (&v)[E], C* sm, int lane, int j, 
         __syncthreads();   // every thread has read the tile before it is rewritten
         stockham_stage<N, T, R1, 1, +1, false, true>(v, sm, lane, j, tw);
         stockham_stage<N, T, R0, R1, +1, true, false>(v, sm, lane, j, tw);
+    } else if constexpr (P::S == 4) {
+        stockham_stage<N, T, R0, 1, -1, FIRST_FROM_SMEM, true>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R1, R0, -1, true, true>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R2, R0 * R1, -1, true, true>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R3, R0 * R1 * R2, -1, true, false>(v, sm, lane, j, tw);
+#pragma unroll
+        for (int q = 0; q < E; ++q) v[q] = cscale(v[q], __ldg(&kin[spec_pos<N, T, R3>(q, j)]) * scale);
+        __syncthreads();
+        stockham_stage<N, T, R3, 1, +1, false, true>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R2, R3, +1, true, true>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R1, R3 * R2, +1, true, true>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R0, R3 * R2 * R1, +1, true, false>(v, sm, lane, j, tw);
     } else {
         stockham_stage<N, T, R0, 1, -1, FIRST_FROM_SMEM, true>(v, sm, lane, j, tw);
         stockham_stage<N, T, R1, R0, -1, true, true>(v, sm, lane, j, tw);
