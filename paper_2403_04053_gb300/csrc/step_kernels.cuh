@@ -446,10 +446,29 @@ __device__ __forceinline__ long long aux_index(const StepArgs<R>& a, int b, int 
     return slot * nb + ((long long)(z - a.abox_lo[2]) * a.abox_n[1] + (y - a.abox_lo[1])) * a.abox_n[0] + (x - a.abox_lo[0]);
 }
 
+// psi_inc of an aux member: the step's evaluated value
+template <typename R, typename C>
+__device__ __forceinline__ C aux_wave(const StepArgs<R>& a, int b, C s, int x, int y, int z)
+{
+    return cmul(s, a.aux_inc[aux_index(a, b, x, y, z)]);
+}
+
+// the PAPER form's taper source of an aux member
+template <typename R, typename C>
+__device__ __forceinline__ C aux_taper_source(const StepArgs<R>& a, int b, int x, int y, int z, R lap, R zx, R zy, R zz, R zx1,
+                                           R zy1, R zz1)
+{
+    const MemberDev& md = a.mem[b];
+    // hbar^2/2m [lap(zeta) psi_inc + 2 (khat . grad zeta) d psi_inc / d d] (Eq. pstd_dpsiinc)
+    const R kg = R(md.khat[0]) * zx1 * zy * zz + R(md.khat[1]) * zx * zy1 * zz + R(md.khat[2]) * zx * zy * zz1;
+    const long long e = aux_index(a, b, x, y, z);
+    return cscale(cadd(cscale(a.aux_inc[e], lap), cscale(a.aux_dinc[e], R(2) * kg)), a.h2m);
+}
+
 template <typename R, typename C>
 __device__ __forceinline__ C incident_wave(const StepArgs<R>& a, int b, C s, int x, int y, int z)
 {
-    if ((a.aux_mask >> b) & 1ull) return cmul(s, a.aux_inc[aux_index(a, b, x, y, z)]);
+    if ((a.aux_mask >> b) & 1ull) return aux_wave<R, C>(a, b, s, x, y, z);
     C w = incident_at<R, C>(a, b, s, x, y, z);
     if ((a.packet_mask >> b) & 1ull) w = cmul(w, packet_envelope<R, C>(a, b, x, y, z));
     return w;
@@ -485,18 +504,22 @@ __device__ __forceinline__ C spinor_acc(const StepArgs<R>& a, int b, C s, int x,
 }
 
 // V-term + source at node (x, y, z) of member b (before the factor -(2 i dt / hbar));
-// s = the member's incident time factor at step n, idx the node's state index
-template <typename R, typename C>
-__device__ __forceinline__ C source_acc(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
+// s = the member's incident time factor at step n, idx the node's state index.  PLAIN: a
+// scalar CW member (the common case, inlined into the pass epilogues); otherwise any member
+// (spinor pairs, wave packets, the 1-D auxiliary wave), reached through source_general.
+template <typename R, typename C, bool PLAIN>
+__device__ __forceinline__ C source_impl(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
 {
-    if (a.spinor) return spinor_acc<R, C>(a, b, s, x, y, z, idx);
+    if constexpr (!PLAIN) {
+        if (a.spinor) return spinor_acc<R, C>(a, b, s, x, y, z, idx);
+    }
     const bool paper = a.mode == PSTD_TFSF_PAPER;
     C acc = mk<C>(R(0), R(0));
     if (x >= a.vlo[0] && x < a.vhi[0] && y >= a.vlo[1] && y < a.vhi[1] && z >= a.vlo[2] && z < a.vhi[2]) {
         const int vnx = a.vhi[0] - a.vlo[0], vny = a.vhi[1] - a.vlo[1];
         const R Vv = a.V[((long long)(z - a.vlo[2]) * vny + (y - a.vlo[1])) * vnx + (x - a.vlo[0])];
         C src = a.cur[idx];
-        if (!paper) src = cadd(src, incident_wave<R, C>(a, b, s, x, y, z));
+        if (!paper) src = cadd(src, PLAIN ? incident_at<R, C>(a, b, s, x, y, z) : incident_wave<R, C>(a, b, s, x, y, z));
         acc = cscale(src, Vv);
     }
     if (paper && x > a.tf_lo[0] && x < a.tf_hi[0] && y > a.tf_lo[1] && y < a.tf_hi[1] && z > a.tf_lo[2] && z < a.tf_hi[2]) {
@@ -504,18 +527,34 @@ __device__ __forceinline__ C source_acc(const StepArgs<R>& a, int b, C s, int x,
         const R zy = a.zeta[1][y], zy1 = a.zeta1[1][y], zy2 = a.zeta2[1][y];
         const R zz = a.zeta[2][z], zz1 = a.zeta1[2][z], zz2 = a.zeta2[2][z];
         const R lap = zx2 * zy * zz + zx * zy2 * zz + zx * zy * zz2;
-        const MemberDev& md = a.mem[b];
-        if ((a.aux_mask >> b) & 1ull) {
-            // hbar^2/2m [lap(zeta) psi_inc + 2 (khat . grad zeta) d psi_inc / d d] (Eq. pstd_dpsiinc)
-            const R kg = R(md.khat[0]) * zx1 * zy * zz + R(md.khat[1]) * zx * zy1 * zz + R(md.khat[2]) * zx * zy * zz1;
-            const long long e = aux_index(a, b, x, y, z);
-            acc = cadd(acc, cscale(cadd(cscale(a.aux_inc[e], lap), cscale(a.aux_dinc[e], R(2) * kg)), a.h2m));
+        if (!PLAIN && ((a.aux_mask >> b) & 1ull)) {
+            acc = cadd(acc, aux_taper_source<R, C>(a, b, x, y, z, lap, zx, zy, zz, zx1, zy1, zz1));
         } else {
+            const MemberDev& md = a.mem[b];
             const R kg = R(md.k[0]) * zx1 * zy * zz + R(md.k[1]) * zx * zy1 * zz + R(md.k[2]) * zx * zy * zz1;
             acc = cadd(acc, cscale(cmul(incident_at<R, C>(a, b, s, x, y, z), mk<C>(lap, R(2) * kg)), a.h2m));   // CW
         }
     }
     return acc;
+}
+
+template <typename R, typename C>
+__device__ __noinline__ C source_general(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
+{
+    return source_impl<R, C, false>(a, b, s, x, y, z, idx);
+}
+
+// GEN = false: the grid has scalar CW members only (chosen on the host), so the general path
+// is not compiled in
+template <typename R, typename C, bool GEN = true>
+__device__ __forceinline__ C source_acc(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
+{
+    if constexpr (!GEN) {
+        return source_impl<R, C, true>(a, b, s, x, y, z, idx);
+    } else {
+        const bool plain = !a.spinor && !(((a.aux_mask | a.packet_mask) >> b) & 1ull);
+        return plain ? source_impl<R, C, true>(a, b, s, x, y, z, idx) : source_general<R, C>(a, b, s, x, y, z, idx);
+    }
 }
 
 // the box [lo, hi) on which the V-term or the source can be non-zero: the V box, or for the
@@ -563,7 +602,8 @@ __global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ Ste
 // ---------------------------------------------------------------------------------
 // z pass: lines along z, lane = x; completes psi^{n+1} with the mask
 // ---------------------------------------------------------------------------------
-template <typename R, int N, bool DFT, bool SRC>
+// SRC: 0 no V-term or source; 1 for grids of scalar CW members only; 2 for any members
+template <typename R, int N, bool DFT, int SRC>
 __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) zpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
 {
     step_kernel_entry();
@@ -600,7 +640,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     // with SRC the V-term and source of this column are added here instead of by source_kernel
     int slo[3] = {0, 0, 0}, shi[3] = {0, 0, 0};
     if constexpr (SRC) source_box<R>(a, slo, shi);
-    const bool src_col = SRC && x >= slo[0] && x < shi[0] && y >= slo[1] && y < shi[1];
+    const bool src_col = SRC != 0 && x >= slo[0] && x < shi[0] && y >= slo[1] && y < shi[1];
     const C s = src_col ? a.tfac[(a.step - a.tfac_base) * a.batch + b] : zero_c<R, C>();
 #pragma unroll
     for (int q = 0; q < E; ++q) {
@@ -613,7 +653,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 #endif
         if constexpr (SRC) {
             if (src_col && z >= slo[2] && z < shi[2]) {
-                const C sa = source_acc<R, C>(a, b, s, x, y, z, idx);
+                const C sa = source_acc<R, C, SRC == 2>(a, b, s, x, y, z, idx);
                 p = mk<C>(p.x + a.c2 * sa.y, p.y - a.c2 * sa.x);
             }
         }
@@ -826,19 +866,29 @@ template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const Dft
     if (d) return launch_step_kernel(ypass_kernel<R, N, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
     return launch_step_kernel(ypass_kernel<R, N, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
 }
-template <typename R, int N>
-cudaError_t zpass_n(const StepArgs<R>& a, const DftArgs<R>* d, bool src, int batch, cudaStream_t s)
+template <typename R, int N, bool DFT, int SRC>
+cudaError_t zpass_launch(const StepArgs<R>& a, const DftArgs<R>& d, int batch, cudaStream_t s)
 {
     const size_t sm = pass_smem<R, N>();
-    cudaError_t e = d ? (src ? set_smem_once<zpass_kernel<R, N, true, true>>(sm) : set_smem_once<zpass_kernel<R, N, true, false>>(sm))
-                      : src ? set_smem_once<zpass_kernel<R, N, false, true>>(sm) : set_smem_once<zpass_kernel<R, N, false, false>>(sm);
+    cudaError_t e = set_smem_once<zpass_kernel<R, N, DFT, SRC>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + kLanes - 1) / kLanes, a.ny, batch);
+    return launch_step_kernel(zpass_kernel<R, N, DFT, SRC>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, d);
+}
+
+template <typename R, int N>
+cudaError_t zpass_n(const StepArgs<R>& a, const DftArgs<R>* d, int src, int batch, cudaStream_t s)
+{
     const DftArgs<R> none{};
-    if (d && src) return launch_step_kernel(zpass_kernel<R, N, true, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
-    if (d) return launch_step_kernel(zpass_kernel<R, N, true, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
-    if (src) return launch_step_kernel(zpass_kernel<R, N, false, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
-    return launch_step_kernel(zpass_kernel<R, N, false, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
+    const DftArgs<R>& dd = d ? *d : none;
+    if (d) {
+        if (src == 2) return zpass_launch<R, N, true, 2>(a, dd, batch, s);
+        if (src == 1) return zpass_launch<R, N, true, 1>(a, dd, batch, s);
+        return zpass_launch<R, N, true, 0>(a, dd, batch, s);
+    }
+    if (src == 2) return zpass_launch<R, N, false, 2>(a, dd, batch, s);
+    if (src == 1) return zpass_launch<R, N, false, 1>(a, dd, batch, s);
+    return zpass_launch<R, N, false, 0>(a, dd, batch, s);
 }
 
 template <typename R, int N>
@@ -889,7 +939,7 @@ template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, const DftAr
     PSTD_SIZE_DISPATCH(ypass_n, a.ny, a, d, batch, s)
 }
 template <typename R>
-cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, bool src, int batch, cudaStream_t s)
+cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, int src, int batch, cudaStream_t s)
 {
     PSTD_SIZE_DISPATCH(zpass_n, a.nz, a, d, src, batch, s)
 }
