@@ -994,6 +994,16 @@ __global__ void __launch_bounds__(256) aux_table_kernel(const double2* G0, const
 
 constexpr int kAuxChunk = 1024;   // modes staged in shared memory at a time (a multiple of 32)
 
+// one Horner step p u + g as four fused multiply-adds
+template <typename C> __device__ __forceinline__ C horner_step(C p, C u, C g)
+{
+    if constexpr (sizeof(C) == 8) {
+        return mk<C>(__fmaf_rn(p.x, u.x, __fmaf_rn(-p.y, u.y, g.x)), __fmaf_rn(p.x, u.y, __fmaf_rn(p.y, u.x, g.y)));
+    } else {
+        return mk<C>(__fma_rn(p.x, u.x, __fma_rn(-p.y, u.y, g.x)), __fma_rn(p.x, u.y, __fma_rn(p.y, u.x, g.y)));
+    }
+}
+
 // psi_inc^n (and d psi_inc^n / d d) at every node of the box for every aux slot: the series of
 // Eqs. pstd_psiinc, pstd_dpsiinc, sum_m G_m e^{i (q_0 + m dq) d} = e^{i q_0 d} P(u), u = e^{i dq d},
 // P(u) = sum_m G_m u^m evaluated by Horner's rule in blocks of 32 modes (u within a block, u^32
@@ -1034,13 +1044,13 @@ template <typename R> __global__ void __launch_bounds__(256) aux_eval_kernel(con
         for (int b0 = cn - 32; b0 >= 0; b0 -= 32) {
             C p = sg[b0 + 31];
 #pragma unroll
-            for (int j = 30; j >= 0; --j) p = cadd(cmul(p, u), sg[b0 + j]);
-            acc = cadd(cmul(acc, u32), p);
+            for (int j = 30; j >= 0; --j) p = horner_step(p, u, sg[b0 + j]);
+            acc = horner_step(acc, u32, p);
             if (deriv) {
                 C dp = sd[b0 + 31];
 #pragma unroll
-                for (int j = 30; j >= 0; --j) dp = cadd(cmul(dp, u), sd[b0 + j]);
-                dacc = cadd(cmul(dacc, u32), dp);
+                for (int j = 30; j >= 0; --j) dp = horner_step(dp, u, sd[b0 + j]);
+                dacc = horner_step(dacc, u32, dp);
             }
         }
     }
