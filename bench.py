@@ -31,7 +31,7 @@ METRIC = "PSTD cell-updates/s, FP32 vs FP64 at stated error (1 GB300); adjoint/f
 
 # DRAM bytes (read + write) of one cold launch at 128^3, from an ncu --set full capture of
 # that kernel (dram__bytes_read.sum + dram__bytes_write.sum); drop an entry when its kernel changes
-DRAM_TRAFFIC = {"xypass": 34.05e6}
+DRAM_TRAFFIC = {"xypass": 34.05e6, "zpass": 34.63e6}
 # the same for the 256^3 passes of the batched leg: captured with 4 members, scaled by the
 # units processed (x4) to a 16-member launch
 BATCHED_TRAFFIC = {"xpass": 4 * 1.576e9, "ypass": 4 * 1.621e9}
@@ -419,11 +419,13 @@ def aux_leg(pstd, inputs, stream, dev, flush, nsteps=300):
     prof = np.exp(-x * x / (4 * sigma * sigma) + 1j * inc.k * x)
     ncell = int(np.prod(spec.n))
     out = {}
-    for kind in ("cw", "aux"):
+    for kind in ("cw", "packet", "aux"):
         g = pstd.Grid(spec, precision=pstd.F32, stream=stream.cuda_stream)
         g.set_potential(torch.from_numpy(wl.V).to(dev))
         if kind == "aux":
             g.set_incidence_aux(0, inc.khat, inc.k, d_lo, dd, prof)
+        elif kind == "packet":
+            g.set_incidence_packet(0, inc.khat, inc.k, sigma, d0)   # the same packet in closed form
         else:
             g.set_incidence(0, inc.khat, inc.k, inc.ramp_time)
         g.huygens_dft(0, [w0], nsteps - 60, 60)
@@ -450,9 +452,11 @@ def aux_leg(pstd, inputs, stream, dev, flush, nsteps=300):
             out[kind]["aux_kernel_us_per_step"] = round(ms_aux / nsteps * 1e3, 2)
             out[kind]["aux_launches"] = n_aux
     return {"workload": f"gaussian-sum-128^3, {nsteps} steps (60 in the DFT window), incident wave from the 1-D "
-                        f"auxiliary axis ({n1} points, dd = {dd}, Gaussian profile sigma = {sigma}) vs the CW wave",
-            "unit": "cell-updates/s", "aux": out["aux"], "cw": out["cw"],
-            "aux_overhead": round(out["aux"]["ms_per_step"] / out["cw"]["ms_per_step"] - 1.0, 4)}
+                        f"auxiliary axis ({n1} points, dd = {dd}, Gaussian profile sigma = {sigma}), the same packet "
+                        f"in closed form, and the CW wave",
+            "unit": "cell-updates/s", "aux": out["aux"], "packet": out["packet"], "cw": out["cw"],
+            "aux_overhead": round(out["aux"]["ms_per_step"] / out["cw"]["ms_per_step"] - 1.0, 4),
+            "packet_overhead": round(out["packet"]["ms_per_step"] / out["cw"]["ms_per_step"] - 1.0, 4)}
 
 
 def adjoint_leg(pstd, inputs, stream, dev):

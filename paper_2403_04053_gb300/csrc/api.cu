@@ -710,8 +710,8 @@ pstd_status enqueue_step(pstd_grid* g, const StepArgs<R>& a, unsigned long long 
     }
     {
         Timer t(g, 2);
-        const bool general = g->spinor || g->aux_mask || g->packet_mask;
-        CK(g, launch_zpass<R>(a, mask ? dz : nullptr, src_in_z ? (general ? 2 : 1) : 0, g->batch, g->stream));
+        const int kind = (g->spinor || (g->aux_mask && g->packet_mask)) ? 2 : g->packet_mask ? 3 : g->aux_mask ? 4 : 1;
+        CK(g, launch_zpass<R>(a, mask ? dz : nullptr, src_in_z ? kind : 0, g->batch, g->stream));
     }
     return PSTD_OK;
 }

@@ -128,8 +128,9 @@ template <typename R> struct DftArgs {
 // virtual planes normal to its axis (d->axis must match the pass)
 template <typename R> cudaError_t launch_xpass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s);
-// src: 0 plain z pass; 1 also add the V-term and source in the epilogue (scalar CW members
-// only); 2 the same for any members (spinor pairs, wave packets, the 1-D auxiliary wave)
+// src: 0 plain z pass; otherwise also add the V-term and source in the epilogue: 1 for
+// scalar CW members only, 3 for CW and wave-packet members, 4 for CW and auxiliary-wave
+// members, 2 for any members (spinor pairs as well)
 template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, int src, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch, cudaStream_t s);
 // fused x + y pass (one CTA per z plane); available for FP32 square planes of 64, 96, 128

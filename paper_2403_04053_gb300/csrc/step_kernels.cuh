@@ -504,13 +504,15 @@ __device__ __forceinline__ C spinor_acc(const StepArgs<R>& a, int b, C s, int x,
 }
 
 // V-term + source at node (x, y, z) of member b (before the factor -(2 i dt / hbar));
-// s = the member's incident time factor at step n, idx the node's state index.  PLAIN: a
-// scalar CW member (the common case, inlined into the pass epilogues); otherwise any member
-// (spinor pairs, wave packets, the 1-D auxiliary wave), reached through source_general.
-template <typename R, typename C, bool PLAIN>
+// s = the member's incident time factor at step n, idx the node's state index.  KIND 1: a
+// scalar CW member (the common case, inlined into the pass epilogues); 3: a CW or wave-packet
+// member; 4: a CW or 1-D auxiliary-wave member (both also inlined); 2: any member (spinor
+// pairs as well), reached through source_general.
+template <typename R, typename C, int KIND>
 __device__ __forceinline__ C source_impl(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
 {
-    if constexpr (!PLAIN) {
+    constexpr bool PLAIN = KIND == 1;
+    if constexpr (KIND == 2) {
         if (a.spinor) return spinor_acc<R, C>(a, b, s, x, y, z, idx);
     }
     const bool paper = a.mode == PSTD_TFSF_PAPER;
@@ -519,7 +521,20 @@ __device__ __forceinline__ C source_impl(const StepArgs<R>& a, int b, C s, int x
         const int vnx = a.vhi[0] - a.vlo[0], vny = a.vhi[1] - a.vlo[1];
         const R Vv = a.V[((long long)(z - a.vlo[2]) * vny + (y - a.vlo[1])) * vnx + (x - a.vlo[0])];
         C src = a.cur[idx];
-        if (!paper) src = cadd(src, PLAIN ? incident_at<R, C>(a, b, s, x, y, z) : incident_wave<R, C>(a, b, s, x, y, z));
+        if (!paper) {
+            C w;
+            if constexpr (KIND == 1) {
+                w = incident_at<R, C>(a, b, s, x, y, z);
+            } else if constexpr (KIND == 3) {
+                w = incident_at<R, C>(a, b, s, x, y, z);
+                if ((a.packet_mask >> b) & 1ull) w = cmul(w, packet_envelope<R, C>(a, b, x, y, z));
+            } else if constexpr (KIND == 4) {
+                w = ((a.aux_mask >> b) & 1ull) ? aux_wave<R, C>(a, b, s, x, y, z) : incident_at<R, C>(a, b, s, x, y, z);
+            } else {
+                w = incident_wave<R, C>(a, b, s, x, y, z);
+            }
+            src = cadd(src, w);
+        }
         acc = cscale(src, Vv);
     }
     if (paper && x > a.tf_lo[0] && x < a.tf_hi[0] && y > a.tf_lo[1] && y < a.tf_hi[1] && z > a.tf_lo[2] && z < a.tf_hi[2]) {
@@ -527,7 +542,7 @@ __device__ __forceinline__ C source_impl(const StepArgs<R>& a, int b, C s, int x
         const R zy = a.zeta[1][y], zy1 = a.zeta1[1][y], zy2 = a.zeta2[1][y];
         const R zz = a.zeta[2][z], zz1 = a.zeta1[2][z], zz2 = a.zeta2[2][z];
         const R lap = zx2 * zy * zz + zx * zy2 * zz + zx * zy * zz2;
-        if (!PLAIN && ((a.aux_mask >> b) & 1ull)) {
+        if ((KIND == 2 || KIND == 4) && ((a.aux_mask >> b) & 1ull)) {
             acc = cadd(acc, aux_taper_source<R, C>(a, b, x, y, z, lap, zx, zy, zz, zx1, zy1, zz1));
         } else {
             const MemberDev& md = a.mem[b];
@@ -541,19 +556,19 @@ __device__ __forceinline__ C source_impl(const StepArgs<R>& a, int b, C s, int x
 template <typename R, typename C>
 __device__ __noinline__ C source_general(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
 {
-    return source_impl<R, C, false>(a, b, s, x, y, z, idx);
+    return source_impl<R, C, 2>(a, b, s, x, y, z, idx);
 }
 
-// GEN = false: the grid has scalar CW members only (chosen on the host), so the general path
-// is not compiled in
-template <typename R, typename C, bool GEN = true>
+// KIND (chosen per grid on the host): 1 scalar CW members only; 3 CW and wave-packet members;
+// 4 CW and auxiliary-wave members; 2 any members, with the uncommon paths out of line
+template <typename R, typename C, int KIND = 2>
 __device__ __forceinline__ C source_acc(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
 {
-    if constexpr (!GEN) {
-        return source_impl<R, C, true>(a, b, s, x, y, z, idx);
+    if constexpr (KIND != 2) {
+        return source_impl<R, C, KIND>(a, b, s, x, y, z, idx);
     } else {
         const bool plain = !a.spinor && !(((a.aux_mask | a.packet_mask) >> b) & 1ull);
-        return plain ? source_impl<R, C, true>(a, b, s, x, y, z, idx) : source_general<R, C>(a, b, s, x, y, z, idx);
+        return plain ? source_impl<R, C, 1>(a, b, s, x, y, z, idx) : source_general<R, C>(a, b, s, x, y, z, idx);
     }
 }
 
@@ -602,7 +617,8 @@ __global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ Ste
 // ---------------------------------------------------------------------------------
 // z pass: lines along z, lane = x; completes psi^{n+1} with the mask
 // ---------------------------------------------------------------------------------
-// SRC: 0 no V-term or source; 1 for grids of scalar CW members only; 2 for any members
+// SRC: 0 no V-term or source; otherwise the source form (source_acc's KIND: 1 scalar CW
+// members only, 3 CW and wave packets, 4 CW and the auxiliary wave, 2 any members)
 template <typename R, int N, bool DFT, int SRC>
 __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) zpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
 {
@@ -653,7 +669,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 #endif
         if constexpr (SRC) {
             if (src_col && z >= slo[2] && z < shi[2]) {
-                const C sa = source_acc<R, C, SRC == 2>(a, b, s, x, y, z, idx);
+                const C sa = source_acc<R, C, SRC>(a, b, s, x, y, z, idx);
                 p = mk<C>(p.x + a.c2 * sa.y, p.y - a.c2 * sa.x);
             }
         }
@@ -882,10 +898,14 @@ cudaError_t zpass_n(const StepArgs<R>& a, const DftArgs<R>* d, int src, int batc
     const DftArgs<R> none{};
     const DftArgs<R>& dd = d ? *d : none;
     if (d) {
+        if (src == 4) return zpass_launch<R, N, true, 4>(a, dd, batch, s);
+        if (src == 3) return zpass_launch<R, N, true, 3>(a, dd, batch, s);
         if (src == 2) return zpass_launch<R, N, true, 2>(a, dd, batch, s);
         if (src == 1) return zpass_launch<R, N, true, 1>(a, dd, batch, s);
         return zpass_launch<R, N, true, 0>(a, dd, batch, s);
     }
+    if (src == 4) return zpass_launch<R, N, false, 4>(a, dd, batch, s);
+    if (src == 3) return zpass_launch<R, N, false, 3>(a, dd, batch, s);
     if (src == 2) return zpass_launch<R, N, false, 2>(a, dd, batch, s);
     if (src == 1) return zpass_launch<R, N, false, 1>(a, dd, batch, s);
     return zpass_launch<R, N, false, 0>(a, dd, batch, s);
