@@ -560,6 +560,8 @@ template <typename R> StepArgs<R> step_args(pstd_grid* g)
     a.flag = g->flag;
     a.packet_mask = g->packet_mask;
     a.pipe_y = g->pipe_y ? 1 : 0;
+    // two levels of the whole batch against the 129 MB L2 (with room for the tables and the DFT)
+    a.pf_l1 = 2.0 * (double)g->batch * (double)g->ncell * (double)g->csize > 96e6 ? 1 : 0;
     a.spinor = g->spinor ? 1 : 0;
     for (int ax = 0; ax < 3; ++ax) {
         a.B[ax] = static_cast<const R*>(g->B[ax]);

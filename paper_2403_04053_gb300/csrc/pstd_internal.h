@@ -48,6 +48,7 @@ template <typename R> struct StepArgs {
     R h2m;                   // hbar^2 / 2m
     int mode;                // PSTD_TFSF_EXACT / PSTD_TFSF_PAPER
     int pipe_y;              // pipelined y pass where available (chosen by the autotuner)
+    int pf_l1;               // the state exceeds L2: the z pass prefetches its update operand to L1
     int* flag;               // bit 0: non-finite value written
     const C* tfac;           // a(t_n) e^{-i w0 t_n}: [(n - tfac_base) * batch + member], evaluated in FP64 on the host
     long long tfac_base;
