@@ -200,6 +200,12 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     const int row0 = blockIdx.x * kLanes;
     const int nrows = min(kLanes, rows - row0);
     const long long tile0 = (long long)b * a.ncell + (long long)row0 * N;
+    if constexpr (N >= 192) {   // the tile's update operand, one 128-byte line a thread (see prefetch_l1)
+        if (a.pf_l1) {
+            constexpr int per = 128 / (int)sizeof(C);
+            for (int e = threadIdx.x * per; e < nrows * N; e += blockDim.x * per) prefetch_l1(a.prev + tile0 + e);
+        }
+    }
     for (int e = threadIdx.x; e < kLanes * N; e += blockDim.x) {
         const int r = e / N, x = e - r * N;
         sm[x * kPitch + r] = r < nrows ? a.cur[tile0 + e] : zero_c<R, C>();
@@ -247,6 +253,14 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     C v[E];
 #pragma unroll
     for (int q = 0; q < E; ++q) v[q] = act ? a.cur[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
+#if !PSTD_PREFETCH_PREV
+    if constexpr (N >= 192) {
+        if (a.pf_l1 && act) {
+#pragma unroll
+            for (int q = 0; q < E; ++q) prefetch_l1(a.prev + base + slot_pos<N, T, R0>(q, j) * stride);
+        }
+    }
+#endif
 #if PSTD_PREFETCH_PREV
     C pv[E];
 #pragma unroll
