@@ -206,9 +206,21 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
             for (int e = threadIdx.x * per; e < nrows * N; e += blockDim.x * per) prefetch_l1(a.prev + tile0 + e);
         }
     }
-    for (int e = threadIdx.x; e < kLanes * N; e += blockDim.x) {
-        const int r = e / N, x = e - r * N;
-        sm[x * kPitch + r] = r < nrows ? a.cur[tile0 + e] : zero_c<R, C>();
+    // the tile's kLanes * N values, E a thread: every load of a thread in flight before its
+    // first shared-memory store
+    constexpr int NT = kLanes * T;
+    {
+        C t[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int e = threadIdx.x + i * NT;
+            t[i] = e / N < nrows ? a.cur[tile0 + e] : zero_c<R, C>();
+        }
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int e = threadIdx.x + i * NT, r = e / N;
+            sm[(e - r * N) * kPitch + r] = t[i];
+        }
     }
     __syncthreads();
     C v[E];
@@ -225,11 +237,21 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 #pragma unroll
     for (int q = 0; q < E; ++q) sm[slot_pos<N, T, R0>(q, j) * kPitch + lane] = v[q];
     __syncthreads();
-    for (int e = threadIdx.x; e < nrows * N; e += blockDim.x) {
-        const int r = e / N, x = e - r * N;
-        const C w = sm[x * kPitch + r];
-        const C p = a.prev[tile0 + e];
-        a.prev[tile0 + e] = mk<C>(p.x + w.y, p.y - w.x);   // p - i w
+    {
+        C p[E];
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int e = threadIdx.x + i * NT;
+            if (e / N < nrows) p[i] = a.prev[tile0 + e];
+        }
+#pragma unroll
+        for (int i = 0; i < E; ++i) {
+            const int e = threadIdx.x + i * NT, r = e / N;
+            if (r < nrows) {
+                const C w = sm[(e - r * N) * kPitch + r];
+                a.prev[tile0 + e] = mk<C>(p[i].x + w.y, p[i].y - w.x);   // p - i w
+            }
+        }
     }
 }
 
