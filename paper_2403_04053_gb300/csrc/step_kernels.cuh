@@ -299,15 +299,24 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
         __syncthreads();
     }
     if (!act) return;
+    constexpr int GR = N >= 192 ? 4 : 1;   // update operands read GR at a time (see the z pass)
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
-        const long long idx = base + slot_pos<N, T, R0>(q, j) * stride;
-#if PSTD_PREFETCH_PREV
-        const C p = pv[q];
-#else
-        const C p = a.prev[idx];
+    for (int q0 = 0; q0 < E; q0 += GR) {
+#if !PSTD_PREFETCH_PREV
+        C pg[GR];
+#pragma unroll
+        for (int i = 0; i < GR; ++i) pg[i] = a.prev[base + slot_pos<N, T, R0>(q0 + i, j) * stride];
 #endif
-        a.prev[idx] = mk<C>(p.x + v[q].y, p.y - v[q].x);
+#pragma unroll
+        for (int q = q0; q < q0 + GR; ++q) {
+            const long long idx = base + slot_pos<N, T, R0>(q, j) * stride;
+#if PSTD_PREFETCH_PREV
+            const C p = pv[q];
+#else
+            const C p = pg[q - q0];
+#endif
+            a.prev[idx] = mk<C>(p.x + v[q].y, p.y - v[q].x);
+        }
     }
     if (dft && j == 0) dft_commit<R, T>(sm, lane, d, b, (long long)z * a.nx + x);   // plane [z][x]
 }
@@ -710,14 +719,25 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     if constexpr (SRC) source_box<R>(a, slo, shi);
     const bool src_col = SRC != 0 && x >= slo[0] && x < shi[0] && y >= slo[1] && y < shi[1];
     const C s = src_col ? a.tfac[(a.step - a.tfac_base) * a.batch + b] : zero_c<R, C>();
+    // on long lines the update operand is read four values at a time, so that its loads do
+    // not wait on the stores before them (at 128 points the extra registers cost more)
+    constexpr int GR = N >= 192 ? 4 : 1;
+    static_assert(E % GR == 0, "E");
 #pragma unroll
-    for (int q = 0; q < E; ++q) {
+    for (int q0 = 0; q0 < E; q0 += GR) {
+#if !PSTD_PREFETCH_PREV
+    C pg[GR];
+#pragma unroll
+    for (int i = 0; i < GR; ++i) pg[i] = a.prev[base + slot_pos<N, T, R0>(q0 + i, j) * stride];
+#endif
+#pragma unroll
+    for (int q = q0; q < q0 + GR; ++q) {
         const int z = slot_pos<N, T, R0>(q, j);
         const long long idx = base + z * stride;
 #if PSTD_PREFETCH_PREV
         C p = pv[q];
 #else
-        C p = a.prev[idx];
+        C p = pg[q - q0];
 #endif
         if constexpr (SRC) {
             if (src_col && z >= slo[2] && z < shi[2]) {
@@ -729,6 +749,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
         const C acc = mk<C>(g * (p.x + v[q].y), g * (p.y - v[q].x));
         ok = ok && finite_c<R>(acc.x, acc.y);
         a.prev[idx] = acc;
+    }
     }
     if (!ok) atomicOr(a.flag, 1);
     if (dft && j == 0) dft_commit<R, T>(sm, lane, d, b, (long long)y * a.nx + x);   // plane [y][x]
