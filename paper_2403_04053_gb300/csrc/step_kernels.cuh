@@ -200,12 +200,6 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     const int row0 = blockIdx.x * kLanes;
     const int nrows = min(kLanes, rows - row0);
     const long long tile0 = (long long)b * a.ncell + (long long)row0 * N;
-    if constexpr (N >= 192) {   // the tile's update operand, one 128-byte line a thread (see prefetch_l1)
-        if (a.pf_l1) {
-            constexpr int per = 128 / (int)sizeof(C);
-            for (int e = threadIdx.x * per; e < nrows * N; e += blockDim.x * per) prefetch_l1(a.prev + tile0 + e);
-        }
-    }
     // the tile's kLanes * N values, E a thread: every load of a thread in flight before its
     // first shared-memory store
     constexpr int NT = kLanes * T;
@@ -220,6 +214,12 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
         for (int i = 0; i < E; ++i) {
             const int e = threadIdx.x + i * NT, r = e / N;
             sm[(e - r * N) * kPitch + r] = t[i];
+        }
+    }
+    if constexpr (N >= 192) {   // the tile's update operand, one 128-byte line a thread (see prefetch_l1)
+        if (a.pf_l1) {
+            constexpr int per = 128 / (int)sizeof(C);
+            for (int e = threadIdx.x * per; e < nrows * N; e += blockDim.x * per) prefetch_l1(a.prev + tile0 + e);
         }
     }
     __syncthreads();
