@@ -1745,10 +1745,11 @@ pstd_status rebuild_aux(pstd_grid* g)
     g->aux_mask = 0;
     g->aux_nslot = g->aux_nm = 0;
     std::vector<int> slots;
+    unsigned long long mask = 0;
     size_t nm = 0;
     for (int b = 0; b < g->batch; ++b)
         if (g->mem[b].aux) {
-            g->aux_mask |= 1ull << b;
+            mask |= 1ull << b;
             slots.push_back(b);
             nm = std::max(nm, g->mem[b].aux_G0.size());
         }
@@ -1796,6 +1797,7 @@ pstd_status rebuild_aux(pstd_grid* g)
     CK(g, cudaMemcpy(g->aux_q, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice));
     g->aux_nslot = ns;
     g->aux_nm = (int)nm;
+    g->aux_mask = mask;   // only now: a failure above leaves no member marked for the kernels
     return PSTD_OK;
 }
 
@@ -1804,7 +1806,11 @@ pstd_status drop_aux(pstd_grid* g, int b)
 {
     if (!g->mem[b].aux) return PSTD_OK;
     g->mem[b].aux = false;
-    return rebuild_aux(g);
+    const pstd_status st = rebuild_aux(g);
+    if (st != PSTD_OK)   // no tables for the others: they are left without an incidence
+        for (auto& m : g->mem)
+            if (m.aux) { m.aux = false; m.has_inc = false; }
+    return st;
 }
 }  // namespace
 
@@ -1873,7 +1879,12 @@ pstd_status pstd_set_incidence_aux(pstd_grid* g, int b, const double khat[3], do
     m.chi = cd(1.0, 0.0);
     g->packet_mask &= ~(1ull << b);
     st = rebuild_aux(g);
-    if (st != PSTD_OK) return st;
+    if (st != PSTD_OK) {
+        // no tables: every aux member is left without an incidence (pstd_step reports ESTATE)
+        for (auto& mm : g->mem)
+            if (mm.aux) { mm.aux = false; mm.has_inc = false; }
+        return st;
+    }
     return upload_members(g);
 }
 
@@ -2501,6 +2512,7 @@ pstd_status pstd_set_magnetic_field(pstd_grid* g, const void* Bx, const void* By
     if (d.dt > dt_bound(d, g->vmax + std::fabs(gamma) * bmax))
         return fail(g, PSTD_EUNSTABLE, "dt above the stability bound with |V|max + |gamma| |B|max (Eq. PSTDstability)");
     CK(g, cudaStreamSynchronize(g->stream));
+    g->spinor = false;   // until the new field is in place (a failed upload leaves a scalar grid)
     for (int a = 0; a < 3; ++a) {
         if (g->B[a]) cudaFree(g->B[a]);
         g->B[a] = nullptr;
