@@ -131,6 +131,19 @@ __device__ __forceinline__ void dft_accumulate(const DftArgs<R>& a, int b, long 
     }
 }
 
+// the accumulator entries that dft_accumulate will read-modify-write for pixel `pix` (first
+// frequency), requested into L1 early so that the commit at the end of the pass finds them
+template <typename R>
+__device__ __forceinline__ void dft_prefetch_acc(const DftArgs<R>& a, int b, long long pix)
+{
+    const double2* accf = a.acc + (long long)b * a.acc_member_stride;
+    const int f0 = 2 * a.axis, f1 = 2 * a.axis + 1;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(accf + a.face_off[f0] + pix));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(accf + a.face_off[f0] + a.face_size[f0] + pix));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(accf + a.face_off[f1] + pix));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(accf + a.face_off[f1] + a.face_size[f1] + pix));
+}
+
 // partial sums of this thread's raw line values: [0] d/da at h0, [1] d/da at h1, [2] psi(h0), [3] psi(h1)
 template <int N, int T, int R0, typename C, int E>
 __device__ __forceinline__ void dft_partials(const C (&v)[E], int j, const C* __restrict__ dw, int h0, int h1, C (&part)[4])
@@ -384,6 +397,10 @@ __global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid
     // DFT scratch after the plane: y-plane partials [group][4][T][32], then x-plane sums [N][4]
     C* red_y = sm + (size_t)N * P;
     C* sum_x = red_y + (size_t)4 * T * N;
+    if (dft && threadIdx.x < N) {
+        dft_prefetch_acc<R>(dx, b, (long long)z * N + threadIdx.x);   // plane [z][y]
+        dft_prefetch_acc<R>(dy, b, (long long)z * N + threadIdx.x);   // plane [z][x]
+    }
     if (dft) {
         // x planes: row y of this z plane, lanes over x
         const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -695,6 +712,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     for (int q = 0; q < E; ++q) pv[q] = act ? a.prev[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
 #endif
     const bool dft = DFT && ((d.member_mask >> b) & 1ull);
+    if (dft && j == 0 && act) dft_prefetch_acc<R>(d, b, (long long)y * a.nx + x);   // plane [y][x]
 #if !PSTD_PREFETCH_PREV
     if constexpr (N >= 192) {   // compiled in for long lines only: its mere presence slows the 128-point pass
         if (a.pf_l1 && act) {
