@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 // One read of psi^n and one read-modify-write of the partial per cell, instead of two
 // of each for separate x and y passes.
 // ---------------------------------------------------------------------------------
-template <int N> constexpr int xy_threads() { return (N / 32) * Plan<N>::T * 32; }
+template <int N> __host__ __device__ constexpr int xy_threads() { return (N / 32) * Plan<N>::T * 32; }
 template <typename R, int N> constexpr bool xy_supported()
 {
     return sizeof(R) == 4 && Plan<N>::S == 2 && N % 32 == 0 && xy_threads<N>() <= 1024 &&
@@ -402,8 +402,12 @@ __global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid
         dft_prefetch_acc<R>(dy, b, (long long)z * N + threadIdx.x);   // plane [z][x]
     }
     if (dft) {
-        // x planes: row y of this z plane, lanes over x
-        const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+        // x planes: row y of this z plane, lanes over x (the warp count is the launch's, known
+        // at compile time, so a warp's rows are unrolled and their loads overlap)
+        constexpr int nwarps = xy_threads<N>() / 32;
+        static_assert(N % nwarps == 0, "rows per warp");
+        const int warp = threadIdx.x >> 5;
+#pragma unroll
         for (int y = warp; y < N; y += nwarps) {
             const C* row = a.cur + pbase + (long long)y * N;
             C d0 = zero_c<R, C>(), d1 = zero_c<R, C>(), p0 = zero_c<R, C>(), p1 = zero_c<R, C>();
