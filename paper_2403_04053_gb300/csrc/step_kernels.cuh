@@ -1127,8 +1127,8 @@ template <typename R> __global__ void __launch_bounds__(256) aux_eval_kernel(con
 {
     step_kernel_entry();
     using C = typename StepArgs<R>::C;
-    __shared__ C sg[kAuxChunk];
-    __shared__ C sd[kAuxChunk];
+    __shared__ __align__(16) C sg[kAuxChunk];
+    __shared__ __align__(16) C sd[kAuxChunk];
     const int slot = blockIdx.y;
     const long long nb = (long long)a.bn[0] * a.bn[1] * a.bn[2];
     const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -1157,9 +1157,24 @@ template <typename R> __global__ void __launch_bounds__(256) aux_eval_kernel(con
         __syncthreads();
         if (!act) continue;
         for (int b0 = cn - 32; b0 >= 0; b0 -= 32) {
-            C p = sg[b0 + 31];
+            C p;
+            if constexpr (sizeof(C) == 8) {
+                // FP32: two modes per 16-byte shared-memory read (b0 is a multiple of 32)
+                const float4* g4 = reinterpret_cast<const float4*>(sg + b0);
+                float4 q = g4[15];
+                p = mk<C>(q.z, q.w);
+                p = horner_step(p, u, mk<C>(q.x, q.y));
 #pragma unroll
-            for (int j = 30; j >= 0; --j) p = horner_step(p, u, sg[b0 + j]);
+                for (int t = 14; t >= 0; --t) {
+                    q = g4[t];
+                    p = horner_step(p, u, mk<C>(q.z, q.w));
+                    p = horner_step(p, u, mk<C>(q.x, q.y));
+                }
+            } else {
+                p = sg[b0 + 31];
+#pragma unroll
+                for (int j = 30; j >= 0; --j) p = horner_step(p, u, sg[b0 + j]);
+            }
             acc = horner_step(acc, u32, p);
             if (deriv) {
                 C dp = sd[b0 + 31];
