@@ -5,7 +5,6 @@
 namespace pstd {
 template cudaError_t launch_xpass<float>(const StepArgs<float>&, const DftArgs<float>*, int, cudaStream_t);
 template cudaError_t launch_ypass<float>(const StepArgs<float>&, const DftArgs<float>*, int, cudaStream_t);
-template cudaError_t launch_zpass<float>(const StepArgs<float>&, const DftArgs<float>*, int, int, cudaStream_t);
 template cudaError_t launch_source<float>(const StepArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_aux_table<float>(const double2*, const double*, const double*, int, int, long long, long, bool,
                                            float2*, float2*, cudaStream_t);

@@ -5,7 +5,6 @@
 namespace pstd {
 template cudaError_t launch_xpass<double>(const StepArgs<double>&, const DftArgs<double>*, int, cudaStream_t);
 template cudaError_t launch_ypass<double>(const StepArgs<double>&, const DftArgs<double>*, int, cudaStream_t);
-template cudaError_t launch_zpass<double>(const StepArgs<double>&, const DftArgs<double>*, int, int, cudaStream_t);
 template cudaError_t launch_source<double>(const StepArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_aux_table<double>(const double2*, const double*, const double*, int, int, long long, long, bool,
                                            double2*, double2*, cudaStream_t);

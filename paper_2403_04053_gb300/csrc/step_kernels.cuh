@@ -585,7 +585,6 @@ __device__ __forceinline__ C spinor_acc(const StepArgs<R>& a, int b, C s, int x,
 template <typename R, typename C, int KIND>
 __device__ __forceinline__ C source_impl(const StepArgs<R>& a, int b, C s, int x, int y, int z, long long idx)
 {
-    constexpr bool PLAIN = KIND == 1;
     if constexpr (KIND == 2) {
         if (a.spinor) return spinor_acc<R, C>(a, b, s, x, y, z, idx);
     }
@@ -992,6 +991,19 @@ cudaError_t zpass_n(const StepArgs<R>& a, const DftArgs<R>* d, int src, int batc
 {
     const DftArgs<R> none{};
     const DftArgs<R>& dd = d ? *d : none;
+    // FP64 keeps the plain and the general epilogue only (packets and the auxiliary wave take
+    // the general one): half the FP64 z-pass variants to compile
+    if (sizeof(R) == 8 && (src == 3 || src == 4)) src = 2;
+    if constexpr (sizeof(R) == 8) {
+        if (d) {
+            if (src == 2) return zpass_launch<R, N, true, 2>(a, dd, batch, s);
+            if (src == 1) return zpass_launch<R, N, true, 1>(a, dd, batch, s);
+            return zpass_launch<R, N, true, 0>(a, dd, batch, s);
+        }
+        if (src == 2) return zpass_launch<R, N, false, 2>(a, dd, batch, s);
+        if (src == 1) return zpass_launch<R, N, false, 1>(a, dd, batch, s);
+        return zpass_launch<R, N, false, 0>(a, dd, batch, s);
+    }
     if (d) {
         if (src == 4) return zpass_launch<R, N, true, 4>(a, dd, batch, s);
         if (src == 3) return zpass_launch<R, N, true, 3>(a, dd, batch, s);
