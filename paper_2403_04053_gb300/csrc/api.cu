@@ -78,12 +78,12 @@ struct GraphKey {
     long long version = 0;
     const void* tfac = nullptr;
     const void* tenv = nullptr;
-    const void* aux_tab = nullptr;
-    const void* aux_inc = nullptr;
+    const void* aux[4] = {};                // auxiliary-wave table, derivative table, value and derivative buffers
     bool operator==(const GraphKey& o) const
     {
         return valid && o.valid && n0 == o.n0 && nsteps == o.nsteps && cur == o.cur && version == o.version &&
-               tfac == o.tfac && tenv == o.tenv && aux_tab == o.aux_tab && aux_inc == o.aux_inc;
+               tfac == o.tfac && tenv == o.tenv && aux[0] == o.aux[0] && aux[1] == o.aux[1] && aux[2] == o.aux[2] &&
+               aux[3] == o.aux[3];
     }
 };
 
@@ -839,8 +839,10 @@ template <typename R> pstd_status run_steps(pstd_grid* g, long nsteps, bool dft 
     key.version = g->config_version;
     key.tfac = g->tfac;
     key.tenv = g->tenv;
-    key.aux_tab = g->aux_tab;
-    key.aux_inc = g->aux_inc;
+    key.aux[0] = g->aux_tab;
+    key.aux[1] = g->aux_dtab;
+    key.aux[2] = g->aux_inc;
+    key.aux[3] = g->aux_dinc;
     const bool graphable = g->graphs && dft && !save && !record && !g->timing && nsteps >= 2;
     if (graphable && g->graph_exec && g->graph_key == key) {
         plan_steps<R>(g, nsteps, dft, n0, nullptr);
