@@ -85,9 +85,10 @@ _lib = None
 
 
 def load_library(path: str = LIB_PATH):
-    """Load libpstd.so (raises if it is missing: there is no fallback)."""
+    """Load libpstd.so (raises if it is missing: there is no fallback).  The in-tree library
+    is loaded once and cached; another path is loaded as asked."""
     global _lib
-    if _lib is not None:
+    if path == LIB_PATH and _lib is not None:
         return _lib
     if not os.path.exists(path):
         raise ImportError(f"{path} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'`")
@@ -96,7 +97,8 @@ def load_library(path: str = LIB_PATH):
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
-    _lib = lib
+    if path == LIB_PATH:
+        _lib = lib
     return lib
 
 

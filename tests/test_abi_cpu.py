@@ -59,3 +59,10 @@ def test_bad_geometry_is_rejected(lib, kw):
 
 def test_stability_bound_matches_the_formula(lib):
     assert pstd.stability_dt_max(_spec(), 0.3 * 2 * math.pi ** 2) == pytest.approx(0.0041188, rel=1e-4)
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    # the product path has no fallback: a missing library is an ImportError, not a CPU path
+    from paper_2403_04053_gb300 import pstd
+    with pytest.raises(ImportError):
+        pstd.load_library(str(tmp_path / "libpstd.so"))
