@@ -32,9 +32,9 @@ METRIC = "PSTD cell-updates/s, FP32 vs FP64 at stated error (1 GB300); adjoint/f
 # DRAM bytes (read + write) of one cold launch at 128^3, from an ncu --set full capture of
 # that kernel (dram__bytes_read.sum + dram__bytes_write.sum); drop an entry when its kernel changes
 DRAM_TRAFFIC = {"xypass": 34.05e6, "zpass": 34.65e6}
-# the same for the 256^3 passes of the batched leg: captured with 4 members, scaled by the
-# units processed (x4) to a 16-member launch
-BATCHED_TRAFFIC = {"xpass": 4 * 2.029e9, "zpass": 4 * 1.658e9}
+# the same for the 256^3 passes of the batched leg, captured with 4 members (the leg scales
+# them by the units processed to its own member count)
+BATCHED_TRAFFIC = {"xpass": 2.029e9, "zpass": 1.658e9}
 WORKLOAD = "gaussian-sum-128^3"
 
 
@@ -134,6 +134,62 @@ def barrier(world: int):
 
 
 # ----------------------------------------------------------------------------------
+# roofline of the leapfrog step
+# ----------------------------------------------------------------------------------
+STEP_KERNELS = ("xpass", "ypass", "zpass", "xypass", "source", "aux")
+
+
+def step_roofline(kstats, ncell, members, nsteps, t_steps, traffic_per_launch, l2_resident=False):
+    """HBM roofline of the whole leapfrog step.
+
+    Algorithmic bytes: one step must read psi^n and psi^{n-1} and write psi^{n+1}, 3 complex64
+    = 24 B per cell and member.  `achieved` divides them by the live stepping time per step
+    (CUDA events around the steps alone, on the library's stream) and `frac` by the measured
+    copy bandwidth.  The step's passes each read psi^n and read-modify-write the partial level
+    (24 B a cell per pass); `passes` gives each pass kernel's mean live launch time and its own
+    achieved rate on those 24 B, and `traffic_per_step` the DRAM bytes the ncu captures measured
+    for the step's launches (null when a kernel changed since its capture)."""
+    pk = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    alg = 24.0 * ncell * members
+    per_step = t_steps / nsteps
+    achieved = alg / per_step / 1e9
+    passes = {}
+    traffic = 0.0
+    traffic_known = True
+    launches_per_step = 0.0
+    for name in STEP_KERNELS:
+        n, ms = kstats.get(name, (0, 0.0))
+        if not n:
+            continue
+        launches_per_step += n / nsteps
+        if name in ("source", "aux"):
+            passes[name] = {"launches": n, "avg_us": round(ms / n * 1e3, 2)}
+            continue
+        avg = ms / n / 1e3
+        passes[name] = {"launches": n, "avg_us": round(avg * 1e6, 2), "achieved_GBs": round(alg / avg / 1e9, 1),
+                        "frac": round(alg / avg / 1e9 / hbm, 4)}
+        t = traffic_per_launch.get(name)
+        if t is None:
+            traffic_known = False
+        else:
+            traffic += t * n / nsteps
+    out = {"kernel": "leapfrog step (" + " + ".join(k for k in passes if k not in ("source", "aux")) + ")",
+           "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+           "traffic": round(traffic) if traffic_known else None,
+           "traffic_per_step": round(traffic) if traffic_known else None,
+           "traffic_over_algorithmic": round(traffic / alg, 3) if traffic_known else None,
+           "algorithmic_bytes_per_step": int(alg), "step_us": round(per_step * 1e6, 2),
+           "launches_per_step": round(launches_per_step, 2), "passes": passes,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback"}
+    if l2_resident:
+        out["l2_resident"] = True
+        out["note"] = ("two levels of the state fit in the 129 MB L2 and stay there between steps: "
+                       "an HBM-equivalent rate, not a DRAM measurement")
+    return out
+
+
+# ----------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------
 def run_gpu(args):
@@ -158,11 +214,15 @@ def run_gpu(args):
     ph_dev = torch.from_numpy(wl.far_phi).to(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
 
-    def one_pass(g, host=False):
+    def one_pass(g, host=False, step_events=None):
         g.reset()
         g.set_incidence(0, inc.khat, inc.k, inc.ramp_time)
         g.huygens_dft(0, [w0], wl.window_first, wl.window_len)
+        if step_events:
+            step_events[0].record(stream)
         g.step(wl.nsteps)
+        if step_events:
+            step_events[1].record(stream)
         if host:
             psi = g.transform_to_points(0, 0, wl.fresnel_points)
             ds, fa = g.cross_section(0, 0, wl.far_theta, wl.far_phi)
@@ -176,7 +236,7 @@ def run_gpu(args):
     for _ in range(args.warmup):
         one_pass(g)
     torch.cuda.synchronize()
-    times = []
+    times, step_times = [], []
     launches0 = g.launch_count()
     barrier(world)
     torch.cuda.synchronize()
@@ -185,11 +245,13 @@ def run_gpu(args):
             flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            se = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             e0.record(stream)
-            psi, ds, fa = one_pass(g)
+            psi, ds, fa = one_pass(g, step_events=se)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
+            step_times.append(se[0].elapsed_time(se[1]) / 1e3)   # the leapfrog steps of the pass alone
     barrier(world)
     launches = g.launch_count() - launches0
     # per-kernel CUDA-event durations on the library's stream, from one more pass with the
@@ -216,17 +278,8 @@ def run_gpu(args):
     d2h = 0 if args.skip_e2e else psi_h.nbytes + ds_h.nbytes + fa_h.nbytes
     t_e2e, v_e2e = aggregate(sum(e2e_times) / len(e2e_times), world, ncell * wl.nsteps) if e2e_times else (0.0, None)
 
-    # roofline of the dominant kernel: every pass launch (x, y, z or the fused x+y) reads
-    # psi^n and the partial level and writes it back: 3 complex64 = 24 B per cell
-    pk = peaks()
-    hbm = pk.get("hbm_gbs", 6800.0)
-    top = max(("xpass", "ypass", "zpass", "xypass"), key=lambda n: kstats[n][1])
-    nl, ms = kstats[top]
-    achieved = 24.0 * ncell / (ms / nl / 1e3) / 1e9
-    roofline = {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": DRAM_TRAFFIC.get(top),
-                "avg_launch_us": round(ms / nl * 1e3, 2), "algorithmic_bytes_per_launch": 24 * ncell,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in pk else "fallback"}
+    roofline = step_roofline(kstats, ncell, 1, wl.nsteps, statistics.median(step_times),
+                             DRAM_TRAFFIC, l2_resident=True)
     kernel_ms = {n: {"launches": c, "total_ms": round(t, 3)} for n, (c, t) in kstats.items()}
 
     # FP64 path once (outside the timed region): throughput and the FP32-vs-FP64 error
@@ -324,22 +377,16 @@ def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80):
     g.reset()
     g.set_timing(True)
     g.step(nsteps)
-    ks = {name: g.kernel_stats(name) for name in ("xpass", "ypass", "zpass", "source")}
+    ks = {name: g.kernel_stats(name) for name in STEP_KERNELS}
     g.set_timing(False)
     g.close()
-    top = max(("xpass", "ypass", "zpass"), key=lambda n: ks[n][1])
-    nl, ms = ks[top]
-    pk = peaks()
-    hbm = pk.get("hbm_gbs", 6800.0)
-    achieved = 24.0 * ncell * B / (ms / nl / 1e3) / 1e9
+    traffic = {k: v * B / 4 for k, v in BATCHED_TRAFFIC.items()}   # captured at 4 members
     return {"workload": f"batched-256^3: {B} incidences (8 Fibonacci directions x k in {{2pi, pi}}) on one "
                         f"Gaussian-sum potential, FP32, {nsteps} steps ({nsteps - nsteps // 2} in the DFT window)",
             "value": B * ncell * nsteps / t, "unit": "cell-updates/s", "ms_per_step": t / nsteps * 1e3,
             "state_bytes": 2 * B * ncell * 8,
-            "kernels_us": {n: round(v[1] / max(1, v[0]) * 1e3, 1) for n, v in ks.items()},
-            "roofline": {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(achieved / hbm, 4), "algorithmic_bytes_per_launch": 24 * ncell * B,
-                         "traffic": BATCHED_TRAFFIC.get(top) if B == 16 else None}}
+            "kernels_us": {n: round(v[1] / max(1, v[0]) * 1e3, 1) for n, v in ks.items() if v[0]},
+            "roofline": step_roofline(ks, ncell, B, nsteps, t, traffic)}
 
 
 def spinor_leg(pstd, inputs, stream, dev, flush, nsteps=80):
@@ -379,29 +426,22 @@ def spinor_leg(pstd, inputs, stream, dev, flush, nsteps=80):
     g.reset()
     g.set_timing(True)
     g.step(nsteps)
-    ks = {name: g.kernel_stats(name) for name in ("xpass", "ypass", "zpass", "source")}
+    ks = {name: g.kernel_stats(name) for name in STEP_KERNELS}
     g.set_timing(False)
     pts = torch.from_numpy(wl.fresnel_points).to(dev)
     th, ph = torch.from_numpy(wl.far_theta).to(dev), torch.from_numpy(wl.far_phi).to(dev)
     t_tr = sum(timed(lambda: g.transform_to_points(b, 0, pts))[0] for b in range(B))
     t_ff = sum(timed(lambda: g.cross_section(b, 0, th, ph))[0] for b in range(B))
     g.close()
-    top = max(("xpass", "ypass", "zpass"), key=lambda n: ks[n][1])
-    nl, ms = ks[top]
-    pk = peaks()
-    hbm = pk.get("hbm_gbs", 6800.0)
-    achieved = 24.0 * ncell * B / (ms / nl / 1e3) / 1e9
     return {"workload": f"spinor-384^3: gamma sigma . B of a point dipole (cut off inside r = 1 and outside r = 12), "
                         f"unpolarised incidence as 2 spinors = {B} members, FP32, {nsteps} steps "
                         f"({nsteps - nsteps // 2} in the DFT window)",
             "value": B * ncell * nsteps / t, "unit": "cell-updates/s", "ms_per_step": t / nsteps * 1e3,
             "state_bytes": 2 * B * ncell * 8,
-            "kernels_us": {n: round(v[1] / max(1, v[0]) * 1e3, 1) for n, v in ks.items()},
+            "kernels_us": {n: round(v[1] / max(1, v[0]) * 1e3, 1) for n, v in ks.items() if v[0]},
             "fresnel_transform_ms": round(t_tr * 1e3, 2), "fresnel_points_per_member": len(wl.fresnel_points),
             "far_field_ms": round(t_ff * 1e3, 2), "far_field_directions": len(wl.far_theta),
-            "roofline": {"kernel": top, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                         "frac": round(achieved / hbm, 4), "algorithmic_bytes_per_launch": 24 * ncell * B,
-                         "traffic": None}}
+            "roofline": step_roofline(ks, ncell, B, nsteps, t, {})}
 
 
 def aux_leg(pstd, inputs, stream, dev, flush, nsteps=300):
@@ -510,28 +550,74 @@ def adjoint_leg(pstd, inputs, stream, dev):
 # ----------------------------------------------------------------------------------
 # CPU oracle (baseline leg and the reference arm)
 # ----------------------------------------------------------------------------------
-def oracle_sample(wl, seconds: float):
-    """Time the FP64 oracle's leapfrog steps on the full 128^3 grid for about `seconds`."""
+def _oracle_worker(nsteps_total, cmd, barrier, out):
+    """One host process: build the 128^3 workload and the FP64 oracle once, then for every
+    command (a duration in seconds) wait at the barrier with the other workers and step the
+    oracle for that long, putting (steps, elapsed seconds) on `out`; None ends it."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import pstd_oracle as po
+    from paper_2403_04053_gb300 import inputs
+    wl = inputs.gaussian_sum_workload(nsteps=nsteps_total, with_outputs=False)
     inc = wl.incidences[0]
     sim = po.Simulation(wl.spec, wl.V, inc.khat, inc.k, inc.ramp_time)
     sim.n = 500
     sim.cur = np.full(wl.spec.shape, 1e-3 + 0j)
-    t0 = time.perf_counter()
-    steps = 0
+    sim.step(1)                         # first-touch of every array outside the timing
     while True:
-        sim.step(1)
-        steps += 1
-        if time.perf_counter() - t0 > seconds:
+        seconds = cmd.get()
+        if seconds is None:
             break
-    dt = time.perf_counter() - t0
-    return int(np.prod(wl.spec.n)) * steps / dt, steps, dt
+        barrier.wait()
+        t0 = time.perf_counter()
+        steps = 0
+        while True:
+            sim.step(1)
+            steps += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        out.put((steps, time.perf_counter() - t0))
+
+
+class OraclePool:
+    """The FP64 oracle on the host cores: one process per core (started with spawn), each
+    stepping its own copy of the 128^3 workload; sample() times all of them together."""
+
+    def __init__(self, nsteps_total: int, workers: int = 0):
+        import multiprocessing as mp
+        self.workers = workers or (os.cpu_count() or 1)
+        ctx = mp.get_context("spawn")
+        self.cmd = [ctx.Queue() for _ in range(self.workers)]
+        self.out = ctx.Queue()
+        self.barrier = ctx.Barrier(self.workers)
+        self.procs = [ctx.Process(target=_oracle_worker, args=(nsteps_total, q, self.barrier, self.out))
+                      for q in self.cmd]
+        for p in self.procs:
+            p.start()
+
+    def sample(self, seconds: float):
+        """(whole-host cell-updates/s, total steps, wall seconds) over about `seconds`."""
+        for q in self.cmd:
+            q.put(seconds)
+        res = [self.out.get() for _ in self.procs]
+        ncell = 128 ** 3
+        return sum(ncell * s / t for s, t in res), sum(s for s, _ in res), max(t for _, t in res)
+
+    def close(self):
+        for q in self.cmd:
+            q.put(None)
+        for p in self.procs:
+            p.join()
 
 
 def cpu_baseline(wl, seconds: float):
-    value, steps, dt = oracle_sample(wl, seconds)
-    return {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} FP64 leapfrog steps of the 128^3 workload (numpy FFT, one thread), {dt:.1f} s"}
+    pool = OraclePool(wl.nsteps)
+    try:
+        value, steps, dt = pool.sample(seconds)
+    finally:
+        pool.close()
+    return {"value": value, "unit": "cell-updates/s", "cores": pool.workers, "kind": "oracle",
+            "sample": f"{steps} FP64 leapfrog steps of the 128^3 workload in total, {pool.workers} processes (one "
+                      f"per host core, numpy FFT) stepping their own copy for {dt:.1f} s"}
 
 
 def run_reference(args):
@@ -541,14 +627,18 @@ def run_reference(args):
     from paper_2403_04053_gb300 import inputs
     wl = inputs.gaussian_sum_workload(nsteps=args.nsteps, with_outputs=False)
     per = max(2.0, args.cpu_seconds / 4)
-    for _ in range(args.warmup):
-        oracle_sample(wl, 0.1)
     vals, tot_steps, tot_t = [], 0, 0.0
-    for _ in range(args.steps):
-        v, s, t = oracle_sample(wl, per)
-        vals.append(v)
-        tot_steps += s
-        tot_t += t
+    pool = OraclePool(args.nsteps)
+    workers = pool.workers
+    try:
+        for i in range(args.warmup + args.steps):
+            v, s, t = pool.sample(0.2 if i < args.warmup else per)
+            if i >= args.warmup:
+                vals.append(v)
+                tot_steps += s
+                tot_t += t
+    finally:
+        pool.close()
     value = sum(vals) / len(vals)
     ncell = int(np.prod(wl.spec.n))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
@@ -556,8 +646,9 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
            "data": "synthetic (seeded Gaussian-sum potential)",
            "config": {"workload": WORKLOAD, "grid": list(wl.spec.n), "sample": "leapfrog steps only, FP64 oracle"},
-           "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                            "sample": f"{tot_steps} FP64 oracle steps of the 128^3 grid in {tot_t:.1f} s"},
+           "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": workers, "kind": "oracle",
+                            "sample": f"{tot_steps} FP64 oracle steps of the 128^3 grid over {workers} processes "
+                                      f"(one per host core), {args.steps} samples of {per:.1f} s"},
            "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "cells_per_step": ncell}
     print(json.dumps(out), flush=True)

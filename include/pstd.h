@@ -199,13 +199,17 @@ pstd_status pstd_cross_section(pstd_grid* g, int b, int f, const double* theta, 
  * memory once running (a fixed, fully reserved memory budget, or a latency-critical loop
  * that cannot afford an allocation or the synchronisation a free implies).  The paper has
  * no counterpart: this is a deployment convenience.  theta, phi, out_dsdo and out_f (may be
- * NULL) are DEVICE pointers; M <= 1048576, else PSTD_EINVAL.  The only scratch, the
- * transform's partial sums, sits in a 16 MiB file-scope device array that every device
- * loading the library holds until exit; the first call on a device looks up its address
- * (make that first call before any stream capture).  All calls on a device share the
- * array and it keeps the last call's contents; calls whose kernels overlap on the GPU race
- * on it and must be serialised.  The grid's surface records must exist: PSTD_ESTATE until
- * pstd_cross_section or pstd_transform_to_points has run once on the grid. */
+ * NULL) are DEVICE pointers on the grid's device (PSTD_EINVAL for host or other-device
+ * memory, checked before any launch); M <= 1048576, else PSTD_EINVAL.  The only scratch,
+ * the transform's partial sums, sits in a 16 MiB file-scope device array held until exit.
+ * With CUDA's lazy module loading (the default) the array is committed on a device when
+ * the first call there looks up its address: that first call can fail with PSTD_ECUDA
+ * (out of memory) under a fully reserved budget, so make it at start-up, before memory is
+ * reserved and before any stream capture.  Later calls allocate nothing.  All calls on a
+ * device share the array and it keeps the last call's contents; calls whose kernels
+ * overlap on the GPU race on it and must be serialised.  The grid's surface records must
+ * exist: PSTD_ESTATE until pstd_cross_section or pstd_transform_to_points has run once on
+ * the grid. */
 pstd_status pstd_cross_section_noalloc(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M,
                                        double* out_dsdo, void* out_f);
 
@@ -230,6 +234,9 @@ pstd_status pstd_synchronize(pstd_grid* g);
 
 /* Step index n of the current state. */
 pstd_status pstd_get_step(pstd_grid* g, long* n);
+
+/* CUDA device ordinal the grid was created on (its buffers live there). */
+pstd_status pstd_get_device(pstd_grid* g, int* device);
 
 /* Sufficient stability bound of Eq. PSTDstability for the descriptor's spacing and units. */
 pstd_status pstd_stability_dt_max(const pstd_grid_desc* desc, double vmax, double* out_dt);
@@ -296,15 +303,21 @@ pstd_status pstd_set_graphs(pstd_grid* g, int enable);
 /* Number of pstd_step calls of g that ran as one CUDA-graph launch. */
 pstd_status pstd_graph_replays(pstd_grid* g, long* count);
 
-/* Step-kernel variants: the tile shape of the x and y transforms (fused: one CTA applies
- * K_x + K_y to a whole z plane in shared memory; separate: 1-D line passes) and, for 192- and
- * 256-point y lines, the pipelined y pass (the next tile staged with cp.async while the current
- * one is transformed).  All variants compute the same step.  pstd_set_variants forces them
- * (EINVAL where a variant does not exist for the grid: fused needs FP32 square 64/96/128
- * planes, pipelined FP32 192/256-point y lines); pstd_autotune times trial_steps steps of
- * every available combination from the grid's current state, keeps the fastest and puts the
- * state back (step counter included; the running DFT is not touched).  out_variants (may be
- * NULL): {fused_xy, pipelined_y} chosen.  Both synchronise. */
+/* Step-kernel variants.  fused_xy selects how the x and y transforms run:
+ *   PSTD_XY_SEPARATE  1-D line passes along x, then along y (two launches);
+ *   PSTD_XY_PLANE     one CTA applies K_x + K_y to a whole z plane held in shared memory
+ *                     (FP32 square 64/96/128 planes);
+ *   PSTD_XY_CLUSTER   a thread-block cluster of N/32 CTAs per z plane: each CTA transforms 32
+ *                     rows, then, after a cluster barrier, 32 columns, the plane's second
+ *                     visit served from L2 (FP32 square 128/192/256 planes).
+ * pipelined_y: for 192- and 256-point y lines of the separate passes, the pipelined y pass
+ * (the next tile staged with cp.async while the current one is transformed).  All variants
+ * compute the same step.  pstd_set_variants forces them (EINVAL where a variant does not
+ * exist for the grid); pstd_autotune times trial_steps steps of every available combination
+ * from the grid's current state, keeps the fastest and puts the state back (step counter
+ * included; the running DFT is not touched).  out_variants (may be NULL): {fused_xy,
+ * pipelined_y} chosen.  Both synchronise. */
+enum { PSTD_XY_SEPARATE = 0, PSTD_XY_PLANE = 1, PSTD_XY_CLUSTER = 2 };
 pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int pipelined_y);
 pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants);
 

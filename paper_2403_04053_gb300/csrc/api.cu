@@ -223,7 +223,7 @@ struct pstd_grid {
     size_t dsdo_cap = 0;
     // instrumentation
     bool timing = false;
-    bool use_xy = false;                    // fused x + y pass (every step; with the plane DFT on window steps)
+    int xy_mode = PSTD_XY_SEPARATE;         // fused x + y pass (every step; with the plane DFT on window steps)
     bool pipe_y = false;                    // pipelined y pass (192/256-point lines)
     // CUDA-graph replay of repeated runs (see run_steps)
     bool graphs = true;
@@ -666,7 +666,7 @@ pstd_status enqueue_step(pstd_grid* g, const StepArgs<R>& a, unsigned long long 
 {
     // the V-term and source: folded into the z pass when x and y run fused; their own kernel
     // ahead of the separate x and y passes otherwise (where the DFT variants are heavier)
-    const bool src_in_z = need_src && (g->use_xy || !mask);
+    const bool src_in_z = need_src && (g->xy_mode != PSTD_XY_SEPARATE || !mask);
     if (g->aux_mask && need_src) {
         // psi_inc of the aux members on the source box for this step (Eqs. pstd_psiinc, pstd_dpsiinc)
         AuxEvalArgs<R> x;
@@ -696,10 +696,10 @@ pstd_status enqueue_step(pstd_grid* g, const StepArgs<R>& a, unsigned long long 
         Timer t(g, 7);
         CK(g, launch_source<R>(a, g->batch, g->stream));
     }
-    if (g->use_xy) {
+    if (g->xy_mode != PSTD_XY_SEPARATE) {
         // x and y together, one CTA per z plane (with the x and y plane DFT on window steps)
         Timer t(g, 3);
-        CK(g, launch_xypass<R>(a, mask ? dx : nullptr, mask ? dy : nullptr, g->batch, g->stream));
+        CK(g, launch_xypass<R>(a, mask ? dx : nullptr, mask ? dy : nullptr, g->batch, g->stream, g->xy_mode));
     } else {
         {
             Timer t(g, 0);
@@ -1449,7 +1449,10 @@ pstd_status pstd_create_grid(const pstd_grid_desc* desc, pstd_grid** out)
     }
     g->stream = static_cast<cudaStream_t>(desc->stream);
     g->prec = desc->precision;
-    g->use_xy = g->prec == PSTD_F32 ? xypass_available<float>(desc->n[0], desc->n[1]) : false;
+    // the fused x + y pass by default: one CTA per plane up to 128 points, a cluster per plane above
+    if (g->prec == PSTD_F32 && xypass_available<float>(desc->n[0], desc->n[1], PSTD_XY_PLANE)) g->xy_mode = PSTD_XY_PLANE;
+    else if (g->prec == PSTD_F32 && xypass_available<float>(desc->n[0], desc->n[1], PSTD_XY_CLUSTER)) g->xy_mode = PSTD_XY_CLUSTER;
+    else g->xy_mode = PSTD_XY_SEPARATE;
     g->pipe_y = g->prec == PSTD_F32 ? pipe_y_available<float>(desc->n[1]) : false;
     g->rsize = g->prec == PSTD_F64 ? 8 : 4;
     g->csize = 2 * g->rsize;
@@ -2202,6 +2205,13 @@ pstd_status pstd_get_step(pstd_grid* g, long* n)
     return PSTD_OK;
 }
 
+pstd_status pstd_get_device(pstd_grid* g, int* device)
+{
+    if (!g || !device) return fail(g, PSTD_EINVAL, "null argument");
+    *device = g->dev;
+    return PSTD_OK;
+}
+
 pstd_status pstd_stability_dt_max(const pstd_grid_desc* desc, double vmax, double* out_dt)
 {
     if (!desc || !out_dt) return fail(nullptr, PSTD_EINVAL, "null argument");
@@ -2361,18 +2371,21 @@ pstd_status pstd_set_graphs(pstd_grid* g, int enable)
 }
 
 namespace {
-bool xy_possible(const pstd_grid* g) { return g->prec == PSTD_F32 && xypass_available<float>(g->desc.n[0], g->desc.n[1]); }
+bool xy_possible(const pstd_grid* g, int mode)
+{
+    return mode == PSTD_XY_SEPARATE || (g->prec == PSTD_F32 && xypass_available<float>(g->desc.n[0], g->desc.n[1], mode));
+}
 bool pipe_possible(const pstd_grid* g) { return g->prec == PSTD_F32 && pipe_y_available<float>(g->desc.n[1]); }
 }  // namespace
 
 pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int pipelined_y)
 {
     if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
-    if ((fused_xy && !xy_possible(g)) || (pipelined_y && !pipe_possible(g)))
+    if (fused_xy < PSTD_XY_SEPARATE || fused_xy > PSTD_XY_CLUSTER || !xy_possible(g, fused_xy) || (pipelined_y && !pipe_possible(g)))
         return fail(g, PSTD_EINVAL, "variant not available for this grid");
     DeviceGuard dg(g->dev);
     ++g->config_version;
-    g->use_xy = fused_xy != 0;
+    g->xy_mode = fused_xy;
     g->pipe_y = pipelined_y != 0;
     return PSTD_OK;
 }
@@ -2395,7 +2408,7 @@ pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     pstd_status st = PSTD_OK;
     float best = -1;
-    int best_xy = g->use_xy, best_pipe = g->pipe_y;
+    int best_xy = g->xy_mode, best_pipe = g->pipe_y;
     auto restore = [&]() -> pstd_status {
         CK(g, cudaMemcpyAsync(g->buf[0], saved, sbytes, cudaMemcpyDeviceToDevice, g->stream));
         CK(g, cudaMemcpyAsync(g->buf[1], static_cast<char*>(saved) + sbytes, sbytes, cudaMemcpyDeviceToDevice, g->stream));
@@ -2408,9 +2421,10 @@ pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants)
         cudaMemcpyAsync(saved, g->buf[0], sbytes, cudaMemcpyDeviceToDevice, g->stream);
         cudaMemcpyAsync(static_cast<char*>(saved) + sbytes, g->buf[1], sbytes, cudaMemcpyDeviceToDevice, g->stream);
     }
-    for (int xy = xy_possible(g) ? 1 : 0; xy >= 0 && st == PSTD_OK; --xy)
+    for (int xy = PSTD_XY_CLUSTER; xy >= PSTD_XY_SEPARATE && st == PSTD_OK; --xy)
         for (int pp = pipe_possible(g) ? 1 : 0; pp >= 0 && st == PSTD_OK; --pp) {
-            g->use_xy = xy;
+            if (!xy_possible(g, xy)) continue;
+            g->xy_mode = xy;
             g->pipe_y = pp;
             st = restore();
             if (st != PSTD_OK) break;
@@ -2432,11 +2446,11 @@ pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants)
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     g->timing = timing_saved;
-    g->use_xy = best_xy;
+    g->xy_mode = best_xy;
     g->pipe_y = best_pipe;
     ++g->config_version;
     if (out_variants) {
-        out_variants[0] = g->use_xy ? 1 : 0;
+        out_variants[0] = g->xy_mode;
         out_variants[1] = g->pipe_y ? 1 : 0;
     }
     return st;

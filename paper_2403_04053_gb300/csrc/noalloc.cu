@@ -8,11 +8,13 @@
 // surface transform -- lives in the file-scope device array below instead of a buffer
 // the grid allocates on demand.
 //
-// The array is kNoAllocScratchElems double2 entries (16 MiB) on every device that loads
-// the library, held until the process exits.  Host code cannot use its name as a device
-// address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it; every later call on the
-// device reuses it.  Every call on a device shares the array and it keeps the last
+// The array is kNoAllocScratchElems double2 entries (16 MiB) per device, held until the
+// process exits.  Host code cannot use its name as a device address, so the first call on
+// each device looks the address up with cudaGetSymbolAddress (with that device current)
+// and caches it; every later call on the device reuses it.  Under CUDA's lazy module
+// loading (the default) that lookup is also what loads the module on the device and
+// commits the array, so the first call can fail for lack of memory: callers make it once
+// at start-up, before their memory budget is reserved and before any stream capture.  Every call on a device shares the array and it keeps the last
 // call's contents; nothing in it needs clearing, because the transform writes every
 // entry it later reads.  Calls whose kernels overlap on the GPU (different streams, or
 // different grids on one device) race on the array and must be serialised by the caller.
@@ -58,6 +60,20 @@ extern "C" pstd_status pstd_cross_section_noalloc(pstd_grid* g, int b, int f, co
         scratch = g_scratch_addr[dev];
     }
     if (M == 0) return PSTD_OK;
+    // every caller pointer must be device (or managed) memory of the grid's device: a host or
+    // other-device pointer would reach the kernels unchecked
+    const void* ptrs[4] = {theta, phi, out_dsdo, out_f};
+    for (const void* p : ptrs) {
+        if (!p) continue;
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+            cudaGetLastError();
+            return pstd::grid_error(g, PSTD_EINVAL, "pstd_cross_section_noalloc: argument is not a CUDA pointer");
+        }
+        const bool on_dev = (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+        if (!on_dev)
+            return pstd::grid_error(g, PSTD_EINVAL, "pstd_cross_section_noalloc: arguments must be device memory of the grid's device");
+    }
     return pstd::far_field_into_scratch(g, b, f, theta, phi, M, out_dsdo, static_cast<double2*>(out_f), scratch,
                                         kNoAllocScratchElems);
 }

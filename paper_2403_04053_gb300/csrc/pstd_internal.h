@@ -135,10 +135,11 @@ template <typename R> cudaError_t launch_ypass(const StepArgs<R>& a, const DftAr
 template <typename R> cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, int src, int batch, cudaStream_t s);
 template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch, cudaStream_t s);
 // fused x + y pass (one CTA per z plane); available for FP32 square planes of 64, 96, 128
-template <typename R> bool xypass_available(int nx, int ny);
+template <typename R> bool xypass_available(int nx, int ny, int mode);
 template <typename R> bool pipe_y_available(int ny);
 template <typename R>
-cudaError_t launch_xypass(const StepArgs<R>& a, const DftArgs<R>* dx, const DftArgs<R>* dy, int batch, cudaStream_t s);
+cudaError_t launch_xypass(const StepArgs<R>& a, const DftArgs<R>* dx, const DftArgs<R>* dy, int batch, cudaStream_t s,
+                          int mode);
 
 // ---------------------------------------------------------------------------------
 // surface-equivalence transform

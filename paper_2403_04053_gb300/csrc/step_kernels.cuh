@@ -199,18 +199,15 @@ __device__ __forceinline__ void dft_finish(const C (&part)[4], C* red, int lane,
 // x pass: 32 consecutive rows per CTA, staged through shared memory (rows are
 // contiguous, so the tile is one contiguous block of 32 * nx values)
 // ---------------------------------------------------------------------------------
+// The x-line work of one CTA: rows [row0, row0 + kLanes) of member b (row = z * ny + y).
 template <typename R, int N, bool DFT>
-__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) xpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+__device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R>& d, int b, int row0,
+                                           typename StepArgs<R>::C* sm)
 {
-    step_kernel_entry();
     using C = typename StepArgs<R>::C;
     constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
     const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
-    const int b = blockIdx.y;
     const int rows = a.ny * a.nz;
-    const int row0 = blockIdx.x * kLanes;
     const int nrows = min(kLanes, rows - row0);
     const long long tile0 = (long long)b * a.ncell + (long long)row0 * N;
     // the tile's kLanes * N values, E a thread: every load of a thread in flight before its
@@ -268,20 +265,34 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     }
 }
 
+template <typename R, int N, bool DFT>
+__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) xpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+{
+    step_kernel_entry();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    xpass_tile<R, N, DFT>(a, d, blockIdx.y, blockIdx.x * kLanes, reinterpret_cast<typename StepArgs<R>::C*>(smraw));
+}
+
 // ---------------------------------------------------------------------------------
 // y pass: lines along y, 32 consecutive x per CTA (lane = x), coalesced in place
 // ---------------------------------------------------------------------------------
-template <typename R, int N, bool DFT>
-__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) ypass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+// load of the y pass's read-modify-write operand: CG = true reads it at L2 (the fused
+// cluster pass, whose other CTAs have just written it), bypassing L1
+template <bool CG, typename C> __device__ __forceinline__ C load_prev(const C* p)
 {
-    step_kernel_entry();
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+// The y-line work of one CTA: columns [x0, x0 + kLanes) of z plane z, member b.
+template <typename R, int N, bool DFT, bool CG = false>
+__device__ __forceinline__ void ypass_tile(const StepArgs<R>& a, const DftArgs<R>& d, int x0, int z, int b,
+                                           typename StepArgs<R>::C* sm)
+{
     using C = typename StepArgs<R>::C;
     constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
     const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
-    const int x = blockIdx.x * kLanes + lane;
-    const int z = blockIdx.y, b = blockIdx.z;
+    const int x = x0 + lane;
     const bool act = x < a.nx;
     const long long stride = a.nx;
     const long long base = (long long)b * a.ncell + (long long)z * a.nx * a.ny + x;
@@ -289,7 +300,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 #pragma unroll
     for (int q = 0; q < E; ++q) v[q] = act ? a.cur[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
 #if !PSTD_PREFETCH_PREV
-    if constexpr (N >= 192) {
+    if constexpr (N >= 192 && !CG) {
         if (a.pf_l1 && act) {
 #pragma unroll
             for (int q = 0; q < E; ++q) prefetch_l1(a.prev + base + slot_pos<N, T, R0>(q, j) * stride);
@@ -299,7 +310,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 #if PSTD_PREFETCH_PREV
     C pv[E];
 #pragma unroll
-    for (int q = 0; q < E; ++q) pv[q] = act ? a.prev[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
+    for (int q = 0; q < E; ++q) pv[q] = act ? load_prev<CG>(a.prev + base + slot_pos<N, T, R0>(q, j) * stride) : zero_c<R, C>();
 #endif
     const bool dft = DFT && ((d.member_mask >> b) & 1ull);
     C part[4];
@@ -318,7 +329,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 #if !PSTD_PREFETCH_PREV
         C pg[GR];
 #pragma unroll
-        for (int i = 0; i < GR; ++i) pg[i] = a.prev[base + slot_pos<N, T, R0>(q0 + i, j) * stride];
+        for (int i = 0; i < GR; ++i) pg[i] = load_prev<CG>(a.prev + base + slot_pos<N, T, R0>(q0 + i, j) * stride);
 #endif
 #pragma unroll
         for (int q = q0; q < q0 + GR; ++q) {
@@ -332,6 +343,54 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
         }
     }
     if (dft && j == 0) dft_commit<R, T>(sm, lane, d, b, (long long)z * a.nx + x);   // plane [z][x]
+}
+
+template <typename R, int N, bool DFT>
+__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) ypass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+{
+    step_kernel_entry();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    ypass_tile<R, N, DFT>(a, d, blockIdx.x * kLanes, blockIdx.y, blockIdx.z, reinterpret_cast<typename StepArgs<R>::C*>(smraw));
+}
+
+// ---------------------------------------------------------------------------------
+// fused x + y pass for large square planes (FP32, N = 192 or 256): a thread-block
+// cluster of N / 32 CTAs per (z plane, member).  CTA r of the cluster first applies K_x
+// to rows [32 r, 32 r + 32) of the plane and read-modify-writes them (the x pass's
+// work), then, after a cluster barrier with release/acquire semantics (which orders the
+// other CTAs' stores of the plane before this CTA's loads), applies K_y to columns
+// [32 r, 32 r + 32) and read-modify-writes those (the y pass's work).  The plane's two
+// levels (2 x 512 KB at N = 256) were touched by the cluster a few microseconds before,
+// so the column phase reads psi^n and the partial level from L2: DRAM sees one read of
+// psi^n and one read-modify-write of the partial per cell for both axes -- 24 B a cell
+// instead of the 48 B of separate x and y passes.  The cluster is what bounds the set of
+// planes in flight (and so the L2 footprint) while keeping every SM busy.
+// ---------------------------------------------------------------------------------
+template <typename R, int N> constexpr bool xycl_supported()
+{
+    return sizeof(R) == 4 && (N == 128 || N == 192 || N == 256) && N % kLanes == 0 && N / kLanes <= 8;
+}
+
+__device__ __forceinline__ void cluster_sync_acq_rel()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+template <typename R, int N, bool DFT>
+__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) xycl_kernel(const __grid_constant__ StepArgs<R> a,
+                                                                                           const __grid_constant__ DftArgs<R> dx,
+                                                                                           const __grid_constant__ DftArgs<R> dy)
+{
+    step_kernel_entry();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    using C = typename StepArgs<R>::C;
+    C* sm = reinterpret_cast<C*>(smraw);
+    const int r = blockIdx.x;                  // rank in the cluster (the grid's x extent is the cluster)
+    const int z = blockIdx.y, b = blockIdx.z;
+    xpass_tile<R, N, DFT>(a, dx, b, z * N + r * kLanes, sm);
+    cluster_sync_acq_rel();
+    ypass_tile<R, N, DFT, true>(a, dy, r * kLanes, z, b, sm);
 }
 
 // ---------------------------------------------------------------------------------
@@ -1075,19 +1134,71 @@ template <typename R> bool pipe_y_available(int ny)
 {
     return (ny == 192 && pipe_supported<R, 192>()) || (ny == 256 && pipe_supported<R, 256>());
 }
-// fused xy pass: FP32, square planes of 64, 96 or 128 (one CTA per plane)
-template <typename R> bool xypass_available(int nx, int ny)
+// fused xy pass, FP32 square planes: PSTD_XY_PLANE (one CTA per plane) for 64, 96 or 128;
+// PSTD_XY_CLUSTER (a cluster of N / 32 CTAs per plane) for 128, 192 or 256
+template <typename R> bool xypass_available(int nx, int ny, int mode)
 {
-    return sizeof(R) == 4 && nx == ny && (nx == 64 || nx == 96 || nx == 128);
+    if (sizeof(R) != 4 || nx != ny) return false;
+    if (mode == PSTD_XY_PLANE) return nx == 64 || nx == 96 || nx == 128;
+    if (mode == PSTD_XY_CLUSTER) return nx == 128 || nx == 192 || nx == 256;
+    return false;
 }
-template <typename R>
-cudaError_t launch_xypass(const StepArgs<R>& a, const DftArgs<R>* dx, const DftArgs<R>* dy, int batch, cudaStream_t s)
+template <typename R, int N, bool DFT>
+cudaError_t xycl_launch(const StepArgs<R>& a, const DftArgs<R>& dx, const DftArgs<R>& dy, int batch, cudaStream_t s)
 {
-    if (!xypass_available<R>(a.nx, a.ny)) return cudaErrorInvalidValue;
+    const size_t sm = pass_smem<R, N>();
+    cudaError_t e = set_smem_once<xycl_kernel<R, N, DFT>>(sm);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(N / kLanes, a.nz, batch);
+    cfg.blockDim = dim3(kLanes * Plan<N>::T);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = N / kLanes;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    int na = 1;
+#if PSTD_PDL
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    na = 2;
+#endif
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    return cudaLaunchKernelEx(&cfg, xycl_kernel<R, N, DFT>, a, dx, dy);
+}
+
+template <typename R, int N>
+cudaError_t xycl_n(const StepArgs<R>& a, const DftArgs<R>* dx, const DftArgs<R>* dy, int batch, cudaStream_t s)
+{
+    if constexpr (xycl_supported<R, N>()) {
+        if (dx && dy) return xycl_launch<R, N, true>(a, *dx, *dy, batch, s);
+        const DftArgs<R> none{};
+        return xycl_launch<R, N, false>(a, none, none, batch, s);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R>
+cudaError_t launch_xypass(const StepArgs<R>& a, const DftArgs<R>* dx, const DftArgs<R>* dy, int batch, cudaStream_t s,
+                          int mode)
+{
+    if (!xypass_available<R>(a.nx, a.ny, mode)) return cudaErrorInvalidValue;
+    if (mode == PSTD_XY_PLANE) {
+        switch (a.nx) {
+        case 64: return xypass_n<R, 64>(a, dx, dy, batch, s);
+        case 96: return xypass_n<R, 96>(a, dx, dy, batch, s);
+        case 128: return xypass_n<R, 128>(a, dx, dy, batch, s);
+        default: return cudaErrorInvalidValue;
+        }
+    }
     switch (a.nx) {
-    case 64: return xypass_n<R, 64>(a, dx, dy, batch, s);
-    case 96: return xypass_n<R, 96>(a, dx, dy, batch, s);
-    case 128: return xypass_n<R, 128>(a, dx, dy, batch, s);
+    case 128: return xycl_n<R, 128>(a, dx, dy, batch, s);
+    case 192: return xycl_n<R, 192>(a, dx, dy, batch, s);
+    case 256: return xycl_n<R, 256>(a, dx, dy, batch, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -20,6 +20,7 @@ F32, F64 = 0, 1
 MEM_HOST, MEM_DEVICE = 0, 1
 DTYPE_F32, DTYPE_F64 = 0, 1
 ABC_POLY, ABC_POSCHL_TELLER = 0, 1
+XY_SEPARATE, XY_PLANE, XY_CLUSTER = 0, 1, 2
 TFSF_EXACT, TFSF_PAPER = 0, 1
 ENV_CW_RAMP = 0
 FIELD_CURRENT, FIELD_PREVIOUS, FIELD_SCATTERED = 0, 1, 2
@@ -62,6 +63,7 @@ _SIGS = {
     "pstd_get_phasors": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
     "pstd_synchronize": (c_int, [c_void_p]),
     "pstd_get_step": (c_int, [c_void_p, POINTER(c_long)]),
+    "pstd_get_device": (c_int, [c_void_p, POINTER(c_int)]),
     "pstd_stability_dt_max": (c_int, [POINTER(GridDesc), c_double, POINTER(c_double)]),
     "pstd_set_timing": (c_int, [c_void_p, c_int]),
     "pstd_kernel_stats": (c_int, [c_void_p, c_int, POINTER(c_long), POINTER(c_double)]),
@@ -318,16 +320,17 @@ class Grid:
                 "pstd_transform_adjoint")
         return self.split_phasors(out)
 
-    def set_variants(self, fused_xy: bool, pipelined_y: bool):
-        """Force the step-kernel variants (pstd_set_variants)."""
-        self._c(self.lib.pstd_set_variants(self.h, int(bool(fused_xy)), int(bool(pipelined_y))), "pstd_set_variants")
+    def set_variants(self, fused_xy, pipelined_y: bool):
+        """Force the step-kernel variants (pstd_set_variants): fused_xy is XY_SEPARATE,
+        XY_PLANE or XY_CLUSTER (True means XY_PLANE)."""
+        self._c(self.lib.pstd_set_variants(self.h, int(fused_xy), int(bool(pipelined_y))), "pstd_set_variants")
 
     def autotune(self, trial_steps: int = 20):
         """Time the available step-kernel variants and keep the fastest (pstd_autotune);
-        returns {"fused_xy": bool, "pipelined_y": bool}."""
+        returns {"fused_xy": XY_SEPARATE | XY_PLANE | XY_CLUSTER, "pipelined_y": bool}."""
         out = (c_int * 2)()
         self._c(self.lib.pstd_autotune(self.h, int(trial_steps), out), "pstd_autotune")
-        return {"fused_xy": bool(out[0]), "pipelined_y": bool(out[1])}
+        return {"fused_xy": int(out[0]), "pipelined_y": bool(out[1])}
 
     def graph_replays(self) -> int:
         n = c_long()
@@ -399,12 +402,36 @@ class Grid:
         return ds, fa
 
     def cross_section_noalloc(self, b: int, f: int, theta, phi, out_dsdo, out_f=None):
-        """pstd_cross_section_noalloc: device tensors in and out, no device allocation."""
+        """pstd_cross_section_noalloc: device tensors in and out, no device allocation.
+
+        theta, phi and out_dsdo are float64 CUDA tensors and out_f (optional) a complex128 one,
+        all contiguous, on the grid's device, with at least M = theta.shape[0] elements."""
+        M = int(theta.shape[0]) if hasattr(theta, "shape") and len(theta.shape) else -1
+        dev = self._device_index()
+        for name, t, dt in (("theta", theta, "float64"), ("phi", phi, "float64"), ("out_dsdo", out_dsdo, "float64"),
+                            ("out_f", out_f, "complex128")):
+            if t is None and name == "out_f":
+                continue
+            if not _is_cuda_tensor(t):
+                raise ValueError(f"cross_section_noalloc: {name} must be a CUDA tensor")
+            if t.device.index != dev:
+                raise ValueError(f"cross_section_noalloc: {name} is on cuda:{t.device.index}, the grid on cuda:{dev}")
+            if not str(t.dtype).endswith(dt):
+                raise ValueError(f"cross_section_noalloc: {name} must be {dt}, not {t.dtype}")
+            if not t.is_contiguous():
+                raise ValueError(f"cross_section_noalloc: {name} must be contiguous")
+            if t.numel() < M:
+                raise ValueError(f"cross_section_noalloc: {name} holds {t.numel()} elements, fewer than M = {M}")
         self._c(self.lib.pstd_cross_section_noalloc(self.h, b, f, c_void_p(theta.data_ptr()), c_void_p(phi.data_ptr()),
-                                                    int(theta.shape[0]), c_void_p(out_dsdo.data_ptr()),
+                                                    M, c_void_p(out_dsdo.data_ptr()),
                                                     c_void_p(out_f.data_ptr()) if out_f is not None else None),
                 "pstd_cross_section_noalloc")
         return out_dsdo, out_f
+
+    def _device_index(self) -> int:
+        d = c_int()
+        self._c(self.lib.pstd_get_device(self.h, byref(d)), "pstd_get_device")
+        return d.value
 
     # -- instrumentation ------------------------------------------------------------
     def set_timing(self, enable: bool):

@@ -201,44 +201,90 @@ def test_adjoint_call_errors():
         assert not g.adjoint_gradient(20, [z], (0, 0, 0), (4, 4, 4)).any()
 
 
+@pytest.fixture(scope="module")
+def oracle_48():
+    """The adjoint workload's construction on a 48^3 grid (V on the central 12^3 block of
+    seeded smoothed noise, 400 steps, an 8 x 8 Fresnel plane): the FP64 oracle's loss and its
+    discrete-adjoint gradient."""
+    wl, V_target = inputs.adjoint_workload(n=48, nsteps=400, block=12, fresnel_count=8, abc=8, tf=(14, 34), taper=4,
+                                           hb=(11, 37))
+    inc = wl.incidences[0]
+    win = (wl.window_first, wl.window_len)
+    from oracle import ntdf_oracle as no
+    from oracle import pstd_oracle as po
+    sim = po.Simulation(wl.spec, V_target, inc.khat, inc.k, inc.ramp_time, window=win)
+    sim.step(wl.nsteps)
+    target = np.abs(no.transform_to_points(wl.spec, inc.k, sim.scaled_phasors(0), wl.fresnel_points))
+    L, grad, psi = ao.fresnel_loss_and_gradient(wl.spec, wl.V, inc.khat, inc.k, inc.ramp_time, win, wl.nsteps,
+                                                wl.fresnel_points, target)
+    return wl, target, L, grad, psi
+
+
+@pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-9), (pstd.F32, 2e-3)])
+def test_adjoint_gradient_matches_oracle_at_48_cubed(oracle_48, prec, tol):
+    wl, target, L_ref, grad_ref, psi_ref = oracle_48
+    inc = wl.incidences[0]
+    lo, hi = (18, 18, 18), (30, 30, 30)          # the 12^3 block of V
+    with pstd.Grid(wl.spec, precision=prec) as g:
+        g.set_potential(wl.V)
+        g.set_incidence(0, inc.khat, inc.k, inc.ramp_time)
+        g.huygens_dft(0, [E0], wl.window_first, wl.window_len)
+        g.step(wl.nsteps)
+        psi = g.transform_to_points(0, 0, wl.fresnel_points)
+        L, gpts = ao.magnitude_misfit(psi, target)
+        grad = g.adjoint_gradient(wl.nsteps, [g.transform_adjoint(0, 0, wl.fresnel_points, gpts)], lo, hi)
+    assert rel(psi, psi_ref) < (1e-10 if prec == pstd.F64 else 2e-4)
+    assert abs(L - L_ref) < (1e-9 if prec == pstd.F64 else 1e-3) * L_ref
+    assert rel(grad, sub(grad_ref, lo, hi)) < tol
+
+
 def test_full_size_adjoint_against_finite_differences():
-    # 128^3 Gaussian-sum grid, FP64, a 400-step run (window the last 120 steps), 64 points of
-    # a Fresnel plane; central differences at four voxels of the central 48^3 block, and
-    # the FP32 adjoint against the FP64 one on the whole block
-    wl = inputs.gaussian_sum_workload(nsteps=400, with_outputs=False)
+    # the adjoint workload as stated: 128^3, 2000 steps, V on the central 48^3 block, the |Psi|
+    # misfit on a 128 x 128 Fresnel plane against the field of a second seeded potential.
+    # Central differences (h = 1e-4, FP64 runs) at 32 seeded voxels of the block against the
+    # FP64 adjoint, and the FP32 adjoint against the FP64 one on the whole block
+    wl, V_target = inputs.adjoint_workload()
     spec = wl.spec
     inc = wl.incidences[0]
-    rng = np.random.default_rng(4)
-    pts = inputs.plane_points(inc.khat, 20.0, 18.0, 8)
-    target = np.abs(rng.standard_normal(len(pts))) * 1e-3
+    pts = wl.fresnel_points
     lo, hi = (40, 40, 40), (88, 88, 88)
+    win = (wl.window_first, wl.window_len)
 
-    def run(V, prec):
+    def run(V, prec, target=None):
         g = pstd.Grid(spec, precision=prec)
         g.set_potential(V)
         g.set_incidence(0, inc.khat, inc.k, inc.ramp_time)
-        g.huygens_dft(0, [E0], 280, 120)
-        g.step(400)
+        g.huygens_dft(0, [E0], *win)
+        g.step(wl.nsteps)
         psi = g.transform_to_points(0, 0, pts)
+        if target is None:
+            g.close()
+            return np.abs(psi)
         L, gpts = ao.magnitude_misfit(psi, target)
         return g, L, gpts
 
-    g, L, gpts = run(wl.V, pstd.F64)
+    target = run(V_target, pstd.F64)
+    g, L, gpts = run(wl.V, pstd.F64, target)
     with g:
-        grad64 = g.adjoint_gradient(400, [g.transform_adjoint(0, 0, pts, gpts)], lo, hi)
-    g, L32, gpts32 = run(wl.V, pstd.F32)
+        grad64 = g.adjoint_gradient(wl.nsteps, [g.transform_adjoint(0, 0, pts, gpts)], lo, hi)
+    g, L32, gpts32 = run(wl.V, pstd.F32, target)
     with g:
-        grad32 = g.adjoint_gradient(400, [g.transform_adjoint(0, 0, pts, gpts32)], lo, hi)
+        grad32 = g.adjoint_gradient(wl.nsteps, [g.transform_adjoint(0, 0, pts, gpts32)], lo, hi)
     assert rel(grad32, grad64) < 2e-3
     h = 1e-4
-    errs = []
-    for (z, y, x) in [(64, 64, 64), (60, 70, 55), (50, 45, 80), (75, 66, 61)]:
+    rng = np.random.default_rng(2407)
+    voxels = rng.integers(lo[0], hi[0], size=(32, 3))
+    fd, ad = [], []
+    for (z, y, x) in voxels:
         Lpm = []
         for sgn in (1, -1):
             V = wl.V.copy()
             V[z, y, x] += sgn * h
-            gp, Lp, _ = run(V, pstd.F64)
+            gp, Lp, _ = run(V, pstd.F64, target)
             gp.close()
             Lpm.append(Lp)
-        errs.append(abs((Lpm[0] - Lpm[1]) / (2 * h) - grad64[z - lo[2], y - lo[1], x - lo[0]]))
-    assert max(errs) / np.abs(grad64).max() < 1e-6
+        fd.append((Lpm[0] - Lpm[1]) / (2 * h))
+        ad.append(grad64[z - lo[2], y - lo[1], x - lo[0]])
+    fd, ad = np.array(fd), np.array(ad)
+    assert np.max(np.abs(fd - ad)) < 1e-6 * np.abs(grad64).max()
+    assert rel(ad, fd) < 1e-5
