@@ -134,6 +134,37 @@ def barrier(world: int):
 
 
 # ----------------------------------------------------------------------------------
+# error against the FP64 oracle
+# ----------------------------------------------------------------------------------
+ORACLE_SAMPLES = os.path.join(ROOT, "tests", "golden", "gaussian_sum_128_fp64_oracle.npz")
+
+
+def oracle_error(state, psi, ds, fa):
+    """Relative L2 errors of the benchmarked pass's results against the FP64 oracle's results
+    for the same seeded 128^3 run, over the stored samples (tests/golden, written by a script
+    that runs only the oracle): the final state at 8192 nodes, the Fresnel field at 48 plane
+    points and the far field at 1066 directions."""
+    try:
+        gd = np.load(ORACLE_SAMPLES)
+    except OSError:
+        return None
+
+    def host(x):
+        return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+
+    def r(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+    state, psi, ds, fa = host(state).ravel(), host(psi), host(ds), host(fa)
+    return {"psi_rel_l2": r(state[gd["nodes"]], gd["psi_nodes"]),
+            "fresnel_psi_rel_l2": r(psi[gd["fresnel_idx"]], gd["fresnel_psi"]),
+            "f_rel_l2": r(fa[gd["far_idx"]], gd["far_f"]),
+            "dsdo_rel_l2": r(ds[gd["far_idx"]], gd["far_dsdo"]),
+            "samples": "8192 state nodes, 48 Fresnel points, 1066 far-field directions of the full 3000-step run",
+            "targets": {"psi": 2e-4, "cross_sections": 1e-3}}
+
+
+# ----------------------------------------------------------------------------------
 # roofline of the leapfrog step
 # ----------------------------------------------------------------------------------
 STEP_KERNELS = ("xpass", "ypass", "zpass", "xypass", "source", "aux")
@@ -262,6 +293,8 @@ def run_gpu(args):
     one_pass(g)
     kstats = {name: g.kernel_stats(name) for name in pstd.KERNELS}
     g.set_timing(False)
+    # the pass's FP32 results against the FP64 oracle's (stored samples of the same seeded run)
+    err_oracle = oracle_error(g.get_field(0), psi, ds, fa)
     t_step, value = aggregate(sum(times) / len(times), world, ncell * wl.nsteps)
 
     # end to end through host buffers: V, points and angles in, psi and dsigma out
@@ -303,9 +336,30 @@ def run_gpu(args):
                 "stepping_only_value": ncell * wl.nsteps / (step_ms / 1e3),
                 "fp32_speedup": round(t64 / t_step, 2),
                 "err_fp32_vs_fp64": {"dsdo_rel_l2": float(np.linalg.norm(ds32 - ds64c) / np.linalg.norm(ds64c)),
-                                     "fresnel_psi_rel_l2": float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64))}}
+                                     "fresnel_psi_rel_l2": float(np.linalg.norm(p32 - p64) / np.linalg.norm(p64))},
+                "err_vs_fp64_oracle": oracle_error(g64.get_field(0), psi64, ds64, fa64)}
         g64.close()
+        # the FP64 passes are ALU-bound on GB300: their rate against the measured FP64 FMA peak,
+        # on the nominal 5 N log2 N flops of each forward and inverse line FFT (six a cell and
+        # step) plus the update's ~30
+        f64_peak = pstd.measure_fma_peak(pstd.F64)
+        flops_cell = 6 * 5 * math.log2(spec.n[0]) + 30
+        ach = flops_cell * fp64["stepping_only_value"] / 1e12
+        fp64["roofline"] = {"kernel": "FP64 leapfrog step (x, y, z passes)", "bound": "alu", "achieved": round(ach, 4),
+                            "peak": round(f64_peak, 4), "unit": "TFLOP/s", "frac": round(ach / f64_peak, 4),
+                            "flops_per_cell_update": flops_cell,
+                            "peak_source": "pstd_measure_fma_peak (FP64 FMA chains on every SM, measured here)"}
     g.close()
+    fma_peaks = {"fp32_tflops": round(pstd.measure_fma_peak(pstd.F32), 2),
+                 "fp64_tflops": round(pstd.measure_fma_peak(pstd.F64), 3),
+                 "how": "independent FMA chains, 8 per thread, 8 CTAs of 256 threads per SM, best of 5 launches"}
+    # the near transform: (point, cell) pairs per second of the benchmarked pass
+    n_tr, ms_tr = kstats["transform"]
+    ncells_surface = sum(2 * (spec.huygens_hi[b] - spec.huygens_lo[b]) * (spec.huygens_hi[c] - spec.huygens_lo[c])
+                         for (b, c) in ((1, 2), (0, 2), (0, 1)))
+    transform = {"points": len(wl.fresnel_points), "surface_cells": ncells_surface, "ms": round(ms_tr, 3),
+                 "pairs_per_s": len(wl.fresnel_points) * ncells_surface / (ms_tr / 1e3),
+                 "points_per_s": len(wl.fresnel_points) / (ms_tr / 1e3)}
 
     # adjoint leg: gradient of the Fresnel-plane |Psi| misfit with respect to V on the central
     # 48^3 block (128^3, FP32, 2000 steps, 128^2 points), timed against its forward run
@@ -328,6 +382,9 @@ def run_gpu(args):
         "e2e": {"value": v_e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "roofline": roofline,
+        "err_vs_fp64_oracle": err_oracle,
+        "fma_peaks": fma_peaks,
+        "transform": transform,
         "gpu_launches": int(launches),
         "kernels": kernel_ms,
         "fp64": fp64,

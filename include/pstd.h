@@ -310,16 +310,29 @@ pstd_status pstd_graph_replays(pstd_grid* g, long* count);
  *   PSTD_XY_CLUSTER   a thread-block cluster of N/32 CTAs per z plane: each CTA transforms 32
  *                     rows, then, after a cluster barrier, 32 columns, the plane's second
  *                     visit served from L2 (FP32 square 128/192/256 planes).
- * pipelined_y: for 192- and 256-point y lines of the separate passes, the pipelined y pass
- * (the next tile staged with cp.async while the current one is transformed).  All variants
- * compute the same step.  pstd_set_variants forces them (EINVAL where a variant does not
- * exist for the grid); pstd_autotune times trial_steps steps of every available combination
- * from the grid's current state, keeps the fastest and puts the state back (step counter
- * included; the running DFT is not touched).  out_variants (may be NULL): {fused_xy,
- * pipelined_y} chosen.  Both synchronise. */
+ * y_pass (the separate y pass) and z_pass select how their lines reach the SMs on steps
+ * without the running DFT:
+ *   PSTD_LINE_PLAIN      each CTA loads its tile into registers (any size and precision);
+ *   PSTD_LINE_PIPELINED  y only, FP32 192/256-point lines: a persistent CTA stages the next
+ *                        tile with cp.async while it transforms the current one;
+ *   PSTD_LINE_TMA        FP32 128/192/256-point lines: a persistent CTA streams its tiles with
+ *                        tensor copies into a ring of shared-memory slots (mbarrier-completed),
+ *                        several tiles in flight while one is transformed.
+ * All variants compute the same step.  pstd_set_variants forces them (EINVAL where a variant
+ * does not exist for the grid); pstd_autotune times trial_steps steps of every available
+ * combination from the grid's current state, keeps the fastest and puts the state back (step
+ * counter included; the running DFT is not touched).  out_variants (may be NULL): {fused_xy,
+ * y_pass, z_pass} chosen.  Both synchronise. */
 enum { PSTD_XY_SEPARATE = 0, PSTD_XY_PLANE = 1, PSTD_XY_CLUSTER = 2 };
-pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int pipelined_y);
+enum { PSTD_LINE_PLAIN = 0, PSTD_LINE_PIPELINED = 1, PSTD_LINE_TMA = 2 };
+pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int y_pass, int z_pass);
 pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants);
+
+/* Measured fused multiply-add peak of the current device in TFLOP/s (2 flops per FMA) for
+ * PSTD_F32 or PSTD_F64: independent FMA chains over every SM, best of five timed launches.
+ * The roofline denominator of the library's ALU-bound kernels (the surface transform, the
+ * auxiliary-wave evaluation, the FP64 passes).  Not part of the paper's method; synchronises. */
+pstd_status pstd_measure_fma_peak(int precision, double* tflops);
 
 /* Message of the last failure on g (or of the last failed pstd_create_grid when g is NULL). */
 const char* pstd_last_error(const pstd_grid* g);

@@ -18,7 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpstd.so")
 SOURCES = ["api.cu", "common.cu", "kernels_f32.cu", "kernels_f32_z.cu", "kernels_f32_z2.cu", "kernels_f32_z3.cu",
-           "kernels_f64.cu", "kernels_f64_z.cu", "kernels_f64_z2.cu", "kernels_f64_z3.cu", "noalloc.cu", "adjoint.cu"]
+           "kernels_f64.cu", "kernels_f64_z.cu", "kernels_f64_z2.cu", "kernels_f64_z3.cu", "noalloc.cu", "adjoint.cu",
+           "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -9,6 +9,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+
 #include "pstd_internal.h"
 
 using namespace pstd;
@@ -224,7 +226,10 @@ struct pstd_grid {
     // instrumentation
     bool timing = false;
     int xy_mode = PSTD_XY_SEPARATE;         // fused x + y pass (every step; with the plane DFT on window steps)
-    bool pipe_y = false;                    // pipelined y pass (192/256-point lines)
+    int y_mode = PSTD_LINE_PLAIN;           // y pass form (192/256-point lines: pipelined; 128-256: TMA-fed)
+    bool tma_z = false;                     // TMA-fed z pass (128/192/256-point lines, steps without the DFT)
+    void* tmaps = nullptr;                  // tensor maps [level buffer][y, z] (device memory, 4 x 128 B)
+    bool tma_y_ok = false, tma_z_ok = false;
     // CUDA-graph replay of repeated runs (see run_steps)
     bool graphs = true;
     long long config_version = 0;           // bumped by every call that changes kernel arguments
@@ -528,6 +533,51 @@ void aux_box(const pstd_grid* g, int lo[3], int n[3])
     if (n[0] <= 0 || n[1] <= 0 || n[2] <= 0) n[0] = n[1] = n[2] = 0;
 }
 
+// Tensor maps for the TMA-fed y and z passes: the state buffer as a 3-D tensor of 8-byte
+// elements [member * nz + z][y][x] (x innermost), one map per level buffer and axis, with
+// boxes of 32 x ny x 1 (y lines) and 32 x 1 x nz (z lines).  Built once per grid (the buffers
+// never move) and kept in device memory; FP32 grids whose y or z lines have 128, 192 or 256
+// points only.  The driver's encoder is reached through the runtime's entry-point query, so
+// the library links no driver library.
+pstd_status make_tensor_maps(pstd_grid* g)
+{
+    const int nx = g->desc.n[0], ny = g->desc.n[1], nz = g->desc.n[2];
+    const bool ty = g->prec == PSTD_F32 && tma_pass_available<float>(ny);
+    const bool tz = g->prec == PSTD_F32 && tma_pass_available<float>(nz);
+    if (!ty && !tz) return PSTD_OK;
+    using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                                const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static Encode encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return PSTD_OK;   // no encoder: the grid keeps the register-fed passes
+        encode = reinterpret_cast<Encode>(fn);
+    }
+    CUtensorMap maps[4];
+    std::memset(maps, 0, sizeof(maps));
+    const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz * g->batch};
+    const cuuint64_t strides[2] = {(cuuint64_t)nx * 8, (cuuint64_t)nx * ny * 8};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    for (int lvl = 0; lvl < 2; ++lvl)
+        for (int ax = 1; ax <= 2; ++ax) {
+            if ((ax == 1 && !ty) || (ax == 2 && !tz)) continue;
+            const cuuint32_t box[3] = {32, ax == 1 ? (cuuint32_t)ny : 1u, ax == 1 ? 1u : (cuuint32_t)nz};
+            const CUresult r = encode(&maps[2 * lvl + ax - 1], CU_TENSOR_MAP_DATA_TYPE_INT64, 3, g->buf[lvl], dims, strides, box,
+                                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return PSTD_OK;   // the grid keeps the register-fed passes
+        }
+    CK(g, dalloc(&g->tmaps, sizeof(maps)));
+    CK(g, cudaMemcpy(g->tmaps, maps, sizeof(maps), cudaMemcpyHostToDevice));
+    g->tma_y_ok = ty;
+    g->tma_z_ok = tz;
+    return PSTD_OK;
+}
+
 template <typename R> StepArgs<R> step_args(pstd_grid* g)
 {
     using C = typename StepArgs<R>::C;
@@ -559,7 +609,12 @@ template <typename R> StepArgs<R> step_args(pstd_grid* g)
     a.mode = g->desc.tfsf_mode;
     a.flag = g->flag;
     a.packet_mask = g->packet_mask;
-    a.pipe_y = g->pipe_y ? 1 : 0;
+    a.pipe_y = g->y_mode;
+    a.tma_z = g->tma_z ? 1 : 0;
+    if (g->tmaps) {
+        a.tmap_y = static_cast<const char*>(g->tmaps) + (size_t)(2 * g->cur + 0) * sizeof(CUtensorMap);
+        a.tmap_z = static_cast<const char*>(g->tmaps) + (size_t)(2 * g->cur + 1) * sizeof(CUtensorMap);
+    }
     // two levels of the whole batch against the 129 MB L2 (with room for the tables and the DFT)
     a.pf_l1 = 2.0 * (double)g->batch * (double)g->ncell * (double)g->csize > 96e6 ? 1 : 0;
     a.spinor = g->spinor ? 1 : 0;
@@ -1453,7 +1508,7 @@ pstd_status pstd_create_grid(const pstd_grid_desc* desc, pstd_grid** out)
     if (g->prec == PSTD_F32 && xypass_available<float>(desc->n[0], desc->n[1], PSTD_XY_PLANE)) g->xy_mode = PSTD_XY_PLANE;
     else if (g->prec == PSTD_F32 && xypass_available<float>(desc->n[0], desc->n[1], PSTD_XY_CLUSTER)) g->xy_mode = PSTD_XY_CLUSTER;
     else g->xy_mode = PSTD_XY_SEPARATE;
-    g->pipe_y = g->prec == PSTD_F32 ? pipe_y_available<float>(desc->n[1]) : false;
+    g->y_mode = g->prec == PSTD_F32 && pipe_y_available<float>(desc->n[1]) ? PSTD_LINE_PIPELINED : PSTD_LINE_PLAIN;
     g->rsize = g->prec == PSTD_F64 ? 8 : 4;
     g->csize = 2 * g->rsize;
     g->ncell = (long long)desc->n[0] * desc->n[1] * desc->n[2];
@@ -1469,6 +1524,10 @@ pstd_status pstd_create_grid(const pstd_grid_desc* desc, pstd_grid** out)
         if (dalloc(&g->buf[i], sbytes) != cudaSuccess) return cleanup_fail(PSTD_ENOMEM, "state allocation failed");
     if (dalloc(&g->flag, sizeof(int)) != cudaSuccess || dalloc(&g->mem_dev, sizeof(MemberDev) * g->batch) != cudaSuccess)
         return cleanup_fail(PSTD_ENOMEM, "allocation failed");
+    {
+        const pstd_status ts = make_tensor_maps(g);
+        if (ts != PSTD_OK) return cleanup_fail(ts, "tensor maps");
+    }
     // 1-D tables (double precision on the host, rounded once to the grid precision)
     for (int a = 0; a < 3; ++a) {
         const int n = desc->n[a];
@@ -1526,7 +1585,7 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     for (void* p : {g->buf[0], g->buf[1], g->V, (void*)g->mem_dev, (void*)g->acc, (void*)g->flag, (void*)g->gl_w_dev,
                     (void*)g->dft_phase, (void*)g->window_first_dev, g->tfac,
                     g->T1, g->OutP, g->OutD, g->Pw, g->rec, (void*)g->partial, (void*)g->pts_dev,
-                    (void*)g->out_dev, (void*)g->dsdo_dev})
+                    (void*)g->out_dev, (void*)g->dsdo_dev, g->tmaps})
         if (p) cudaFree(p);
     for (int a = 0; a < 3; ++a)
         for (void* p : {g->tw[a], g->kin[a], g->mask[a], g->zeta[a], g->zeta1[a], g->zeta2[a], g->phase[a], g->dw[a]})
@@ -2191,6 +2250,10 @@ pstd_status pstd_synchronize(pstd_grid* g)
     CK(g, cudaStreamSynchronize(g->stream));
     int flag = 0;
     CK(g, cudaMemcpy(&flag, g->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag & 2) {
+        CK(g, cudaMemset(g->flag, 0, sizeof(int)));
+        return fail(g, PSTD_ETIMEOUT, "a step kernel gave up waiting for its tensor copies");
+    }
     if (flag & 1) {
         CK(g, cudaMemset(g->flag, 0, sizeof(int)));
         return fail(g, PSTD_ENONFINITE, "the state became non-finite");
@@ -2375,18 +2438,30 @@ bool xy_possible(const pstd_grid* g, int mode)
 {
     return mode == PSTD_XY_SEPARATE || (g->prec == PSTD_F32 && xypass_available<float>(g->desc.n[0], g->desc.n[1], mode));
 }
-bool pipe_possible(const pstd_grid* g) { return g->prec == PSTD_F32 && pipe_y_available<float>(g->desc.n[1]); }
+bool ymode_possible(const pstd_grid* g, int mode)
+{
+    if (mode == PSTD_LINE_PLAIN) return true;
+    if (mode == PSTD_LINE_PIPELINED) return g->prec == PSTD_F32 && pipe_y_available<float>(g->desc.n[1]);
+    if (mode == PSTD_LINE_TMA) return g->tma_y_ok;
+    return false;
+}
+bool zmode_possible(const pstd_grid* g, int mode)
+{
+    return mode == PSTD_LINE_PLAIN || (mode == PSTD_LINE_TMA && g->tma_z_ok);
+}
 }  // namespace
 
-pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int pipelined_y)
+pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int y_pass, int z_pass)
 {
     if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
-    if (fused_xy < PSTD_XY_SEPARATE || fused_xy > PSTD_XY_CLUSTER || !xy_possible(g, fused_xy) || (pipelined_y && !pipe_possible(g)))
+    if (fused_xy < PSTD_XY_SEPARATE || fused_xy > PSTD_XY_CLUSTER || !xy_possible(g, fused_xy) || !ymode_possible(g, y_pass) ||
+        !zmode_possible(g, z_pass))
         return fail(g, PSTD_EINVAL, "variant not available for this grid");
     DeviceGuard dg(g->dev);
     ++g->config_version;
     g->xy_mode = fused_xy;
-    g->pipe_y = pipelined_y != 0;
+    g->y_mode = y_pass;
+    g->tma_z = z_pass == PSTD_LINE_TMA;
     return PSTD_OK;
 }
 
@@ -2408,7 +2483,8 @@ pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     pstd_status st = PSTD_OK;
     float best = -1;
-    int best_xy = g->xy_mode, best_pipe = g->pipe_y;
+    int best_xy = g->xy_mode, best_y = g->y_mode;
+    bool best_z = g->tma_z;
     auto restore = [&]() -> pstd_status {
         CK(g, cudaMemcpyAsync(g->buf[0], saved, sbytes, cudaMemcpyDeviceToDevice, g->stream));
         CK(g, cudaMemcpyAsync(g->buf[1], static_cast<char*>(saved) + sbytes, sbytes, cudaMemcpyDeviceToDevice, g->stream));
@@ -2422,10 +2498,13 @@ pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants)
         cudaMemcpyAsync(static_cast<char*>(saved) + sbytes, g->buf[1], sbytes, cudaMemcpyDeviceToDevice, g->stream);
     }
     for (int xy = PSTD_XY_CLUSTER; xy >= PSTD_XY_SEPARATE && st == PSTD_OK; --xy)
-        for (int pp = pipe_possible(g) ? 1 : 0; pp >= 0 && st == PSTD_OK; --pp) {
-            if (!xy_possible(g, xy)) continue;
+        for (int ym = PSTD_LINE_TMA; ym >= PSTD_LINE_PLAIN && st == PSTD_OK; --ym)
+        for (int zm = PSTD_LINE_TMA; zm >= PSTD_LINE_PLAIN && st == PSTD_OK; zm -= 2) {
+            if (!xy_possible(g, xy) || !ymode_possible(g, ym) || !zmode_possible(g, zm)) continue;
+            if (xy != PSTD_XY_SEPARATE && ym != PSTD_LINE_PLAIN) continue;   // no separate y pass to vary
             g->xy_mode = xy;
-            g->pipe_y = pp;
+            g->y_mode = ym;
+            g->tma_z = zm == PSTD_LINE_TMA;
             st = restore();
             if (st != PSTD_OK) break;
             st = g->prec == PSTD_F64 ? run_steps<double>(g, 2, false) : run_steps<float>(g, 2, false);   // warm-up
@@ -2437,7 +2516,7 @@ pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants)
             if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(g, PSTD_ECUDA, "tuning events"); break; }
             float ms = 0;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (best < 0 || ms < best) { best = ms; best_xy = xy; best_pipe = pp; }
+            if (best < 0 || ms < best) { best = ms; best_xy = xy; best_y = ym; best_z = zm == PSTD_LINE_TMA; }
         }
     const pstd_status rs = restore();
     if (st == PSTD_OK) st = rs;
@@ -2447,11 +2526,13 @@ pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants)
     if (e1) cudaEventDestroy(e1);
     g->timing = timing_saved;
     g->xy_mode = best_xy;
-    g->pipe_y = best_pipe;
+    g->y_mode = best_y;
+    g->tma_z = best_z;
     ++g->config_version;
     if (out_variants) {
         out_variants[0] = g->xy_mode;
-        out_variants[1] = g->pipe_y ? 1 : 0;
+        out_variants[1] = g->y_mode;
+        out_variants[2] = g->tma_z ? PSTD_LINE_TMA : PSTD_LINE_PLAIN;
     }
     return st;
 }

@@ -268,8 +268,10 @@ template <int N, int T, int RADL> __device__ __forceinline__ int spec_pos(int q,
 
 // F^-1[ mult * F[v] ] for one line held as described above.  `kin` is the real
 // multiplier in FFT index order (already including 1/N).  FIRST_FROM_SMEM: the
-// inputs sit in the tile (x-lines loaded by a transposing copy) instead of v.
-template <int N, bool FIRST_FROM_SMEM, typename C, int E>
+// inputs sit in the tile (x-lines loaded by a transposing copy) instead of v.  PS: the
+// exchange tile's row pitch (kLanes itself is conflict-free for the column passes, whose
+// lanes are consecutive; the transposing x-line copy needs kLanes + 1).
+template <int N, bool FIRST_FROM_SMEM, int PS = kPitch, typename C, int E>
 __device__ __forceinline__ void kinetic_line(C (&v)[E], C* sm, int lane, int j, const C* __restrict__ tw,
                                              const decltype(C::x)* __restrict__ kin, decltype(C::x) scale)
 {
@@ -280,42 +282,42 @@ __device__ __forceinline__ void kinetic_line(C (&v)[E], C* sm, int lane, int j, 
     if constexpr (P::S == 1) {
         if constexpr (FIRST_FROM_SMEM) {
 #pragma unroll
-            for (int q = 0; q < E; ++q) v[q] = sm[slot_pos<N, T, R0>(q, j) * kPitch + lane];
+            for (int q = 0; q < E; ++q) v[q] = sm[slot_pos<N, T, R0>(q, j) * PS + lane];
         }
-        stockham_stage<N, T, R0, 1, -1, false, false>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R0, 1, -1, false, false, PS>(v, sm, lane, j, tw);
 #pragma unroll
         for (int q = 0; q < E; ++q) v[q] = cscale(v[q], __ldg(&kin[spec_pos<N, T, R0>(q, j)]) * scale);
-        stockham_stage<N, T, R0, 1, +1, false, false>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R0, 1, +1, false, false, PS>(v, sm, lane, j, tw);
     } else if constexpr (P::S == 2) {
-        stockham_stage<N, T, R0, 1, -1, FIRST_FROM_SMEM, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R1, R0, -1, true, false>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R0, 1, -1, FIRST_FROM_SMEM, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R1, R0, -1, true, false, PS>(v, sm, lane, j, tw);
 #pragma unroll
         for (int q = 0; q < E; ++q) v[q] = cscale(v[q], __ldg(&kin[spec_pos<N, T, R1>(q, j)]) * scale);
         __syncthreads();   // every thread has read the tile before it is rewritten
-        stockham_stage<N, T, R1, 1, +1, false, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R0, R1, +1, true, false>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R1, 1, +1, false, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R0, R1, +1, true, false, PS>(v, sm, lane, j, tw);
     } else if constexpr (P::S == 4) {
-        stockham_stage<N, T, R0, 1, -1, FIRST_FROM_SMEM, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R1, R0, -1, true, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R2, R0 * R1, -1, true, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R3, R0 * R1 * R2, -1, true, false>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R0, 1, -1, FIRST_FROM_SMEM, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R1, R0, -1, true, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R2, R0 * R1, -1, true, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R3, R0 * R1 * R2, -1, true, false, PS>(v, sm, lane, j, tw);
 #pragma unroll
         for (int q = 0; q < E; ++q) v[q] = cscale(v[q], __ldg(&kin[spec_pos<N, T, R3>(q, j)]) * scale);
         __syncthreads();
-        stockham_stage<N, T, R3, 1, +1, false, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R2, R3, +1, true, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R1, R3 * R2, +1, true, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R0, R3 * R2 * R1, +1, true, false>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R3, 1, +1, false, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R2, R3, +1, true, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R1, R3 * R2, +1, true, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R0, R3 * R2 * R1, +1, true, false, PS>(v, sm, lane, j, tw);
     } else {
-        stockham_stage<N, T, R0, 1, -1, FIRST_FROM_SMEM, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R1, R0, -1, true, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R2, R0 * R1, -1, true, false>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R0, 1, -1, FIRST_FROM_SMEM, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R1, R0, -1, true, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R2, R0 * R1, -1, true, false, PS>(v, sm, lane, j, tw);
 #pragma unroll
         for (int q = 0; q < E; ++q) v[q] = cscale(v[q], __ldg(&kin[spec_pos<N, T, R2>(q, j)]) * scale);
         __syncthreads();
-        stockham_stage<N, T, R2, 1, +1, false, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R1, R2, +1, true, true>(v, sm, lane, j, tw);
-        stockham_stage<N, T, R0, R2 * R1, +1, true, false>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R2, 1, +1, false, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R1, R2, +1, true, true, PS>(v, sm, lane, j, tw);
+        stockham_stage<N, T, R0, R2 * R1, +1, true, false, PS>(v, sm, lane, j, tw);
     }
 }
 

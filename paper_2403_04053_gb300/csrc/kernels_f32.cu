@@ -11,6 +11,7 @@ template cudaError_t launch_aux_table<float>(const double2*, const double*, cons
 template cudaError_t launch_aux_eval<float>(const AuxEvalArgs<float>&, cudaStream_t);
 template bool xypass_available<float>(int, int, int);
 template bool pipe_y_available<float>(int);
+template bool tma_pass_available<float>(int);
 template cudaError_t launch_xypass<float>(const StepArgs<float>&, const DftArgs<float>*, const DftArgs<float>*, int, cudaStream_t,
                                            int);
 template cudaError_t launch_transform<float>(const TransformArgs<float>&, int, int, cudaStream_t);

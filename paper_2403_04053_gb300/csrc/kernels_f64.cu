@@ -11,6 +11,7 @@ template cudaError_t launch_aux_table<double>(const double2*, const double*, con
 template cudaError_t launch_aux_eval<double>(const AuxEvalArgs<double>&, cudaStream_t);
 template bool xypass_available<double>(int, int, int);
 template bool pipe_y_available<double>(int);
+template bool tma_pass_available<double>(int);
 template cudaError_t launch_xypass<double>(const StepArgs<double>&, const DftArgs<double>*, const DftArgs<double>*, int, cudaStream_t,
                                            int);
 template cudaError_t launch_transform<double>(const TransformArgs<double>&, int, int, cudaStream_t);

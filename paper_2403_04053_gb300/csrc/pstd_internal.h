@@ -47,7 +47,10 @@ template <typename R> struct StepArgs {
     R c2;                    // 2 dt / hbar, rounded once on the host
     R h2m;                   // hbar^2 / 2m
     int mode;                // PSTD_TFSF_EXACT / PSTD_TFSF_PAPER
-    int pipe_y;              // pipelined y pass where available (chosen by the autotuner)
+    int pipe_y;              // y pass form where available: PSTD_LINE_PIPELINED or PSTD_LINE_TMA (autotuner)
+    int tma_z;               // z pass fed by tensor copies where available (autotuner)
+    const void* tmap_y;      // tensor maps of the current level (device memory): boxes of 32 y lines
+    const void* tmap_z;      //   and of 32 z lines (see colpass_tma_kernel)
     int pf_l1;               // the state exceeds L2: the z pass prefetches its update operand to L1
     int* flag;               // bit 0: non-finite value written
     const C* tfac;           // a(t_n) e^{-i w0 t_n}: [(n - tfac_base) * batch + member], evaluated in FP64 on the host
@@ -137,6 +140,8 @@ template <typename R> cudaError_t launch_source(const StepArgs<R>& a, int batch,
 // fused x + y pass (one CTA per z plane); available for FP32 square planes of 64, 96, 128
 template <typename R> bool xypass_available(int nx, int ny, int mode);
 template <typename R> bool pipe_y_available(int ny);
+// tensor-copy-fed y or z pass: FP32 lines of 128, 192 or 256 points
+template <typename R> bool tma_pass_available(int n);
 template <typename R>
 cudaError_t launch_xypass(const StepArgs<R>& a, const DftArgs<R>* dx, const DftArgs<R>* dy, int batch, cudaStream_t s,
                           int mode);

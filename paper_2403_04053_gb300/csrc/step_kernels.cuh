@@ -968,6 +968,211 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, 1) colpass_pipe_kernel(co
 }
 
 // ---------------------------------------------------------------------------------
+// TMA-fed y and z passes (FP32, lines of 128, 192 or 256 points, steps without the DFT).
+// A persistent CTA per SM walks its tiles of kLanes lines.  Each tile's psi^n arrives by one
+// tensor copy (cp.async.bulk.tensor, box 32 x N) into a ring of S shared-memory slots laid
+// out [position][lane], completing on the slot's mbarrier.  The CTA reads its tile from the
+// slot, issues the loads of the tile's read-modify-write operand into registers, and runs
+// the line transform using the slot itself as the exchange tile (pitch kLanes: the lanes of
+// a warp are consecutive, so every exchange is conflict-free).  Once every thread is done
+// with the slot, thread 0 refills it with the tile S steps ahead, so S - 1 tiles of psi^n
+// stream in from HBM while one is transformed; the operand's latency is covered by the
+// transform.  Waits on the mbarriers are bounded in time: past the limit the kernel sets
+// bit 1 of the grid's flag (reported as PSTD_ETIMEOUT), waits (bounded again) for its own
+// copies in flight and returns.
+// ---------------------------------------------------------------------------------
+template <typename R, int N> constexpr bool tma_pass_supported()
+{
+    return sizeof(R) == 4 && (N == 128 || N == 192 || N == 256) && Plan<N>::S == 2 + (N == 192);
+}
+// ring depth: about 192 KB of slots per SM (two CTAs an SM share it at N = 128), at most 6
+template <int N> __host__ __device__ constexpr int tma_ctas_sm() { return N == 128 ? 2 : 1; }
+template <int N> __host__ __device__ constexpr int tma_slots()
+{
+    return (192 * 1024 / tma_ctas_sm<N>()) / (N * kLanes * 8) > 6 ? 6 : (192 * 1024 / tma_ctas_sm<N>()) / (N * kLanes * 8);
+}
+// dynamic shared memory: the slots (1024-byte aligned at run time, hence the pad), then the
+// slots' mbarriers and the CTA's wait verdict
+template <int N> constexpr size_t tma_smem() { return (size_t)tma_slots<N>() * N * kLanes * 8 + 1024 + 8 * 8 + 16; }
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait for phase `parity` of the mbarrier, for at most `limit_ns`; false when the limit passed
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned long long limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+// 3-D tiled tensor copy global -> shared, completing `bytes` on the mbarrier
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2, unsigned long long* bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_u32(dst)), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;   // 2 s: a tile normally lands in microseconds
+
+template <typename R, int N, int AXIS, int SRC>
+__global__ void __launch_bounds__(kLanes * Plan<N>::T, tma_ctas_sm<N>()) colpass_tma_kernel(const __grid_constant__ StepArgs<R> a)
+{
+    step_kernel_entry();
+    using C = typename StepArgs<R>::C;
+    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
+    constexpr int S = tma_slots<N>();
+    constexpr unsigned SLOT = (unsigned)N * kLanes;            // complex values per slot
+    extern __shared__ __align__(16) unsigned char smraw[];
+    // tensor copies land on 1024-byte-aligned slots: round the window's start up
+    unsigned char* base_sm = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);
+    C* slots = reinterpret_cast<C*>(base_sm);
+    unsigned long long* full = reinterpret_cast<unsigned long long*>(base_sm + (size_t)S * SLOT * sizeof(C));
+    int& ok_s = *reinterpret_cast<int*>(full + S);
+    const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
+    const int xtiles = (a.nx + kLanes - 1) / kLanes;
+    const int other = AXIS == 1 ? a.nz : a.ny;
+    const long long ntiles = (long long)xtiles * other * a.batch;
+    const long long stride = AXIS == 1 ? (long long)a.nx : (long long)a.nx * a.ny;
+    const void* tmap = AXIS == 1 ? a.tmap_y : a.tmap_z;
+    const C* __restrict__ tw = a.tw[AXIS];
+    const R* __restrict__ kin = a.kin[AXIS];
+    // tile t -> member b, in-plane index o (z for y lines, y for z lines), first column x0
+    auto decode = [&](long long t, int& b, int& o, int& x0) {
+        x0 = (int)(t % xtiles) * kLanes;
+        const long long r = t / xtiles;
+        o = (int)(r % other);
+        b = (int)(r / other);
+    };
+    auto issue = [&](long long t, int s) {
+        int b, o, x0;
+        decode(t, b, o, x0);
+        mbar_expect_tx(&full[s], SLOT * (unsigned)sizeof(C));
+        if constexpr (AXIS == 1) tma_load_3d(slots + (size_t)s * SLOT, tmap, x0, 0, b * a.nz + o, &full[s]);
+        else tma_load_3d(slots + (size_t)s * SLOT, tmap, x0, o, b * a.nz, &full[s]);
+    };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int s = 0; s < S; ++s) {
+            const long long t = blockIdx.x + (long long)s * gridDim.x;
+            if (t < ntiles) issue(t, s);
+        }
+    }
+    __syncthreads();
+    int it = 0;
+    bool timed_out = false;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+        const int s = it % S;
+        const unsigned parity = (unsigned)(it / S) & 1u;
+        // one thread decides (so that every thread leaves together), then all observe the phase
+        if (threadIdx.x == 0) ok_s = mbar_wait_bounded(&full[s], parity, kWaitLimitNs) ? 1 : 0;
+        __syncthreads();
+        if (!ok_s) { timed_out = true; break; }
+        mbar_wait_bounded(&full[s], parity, kWaitLimitNs);
+        C* slot = slots + (size_t)s * SLOT;
+        int b, o, x0;
+        decode(t, b, o, x0);
+        const int x = x0 + lane;
+        const bool act = x < a.nx;
+        const long long base = (long long)b * a.ncell + (AXIS == 1 ? (long long)o * a.nx * a.ny : (long long)o * a.nx) + x;
+        C v[E], pv[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) v[q] = slot[slot_pos<N, T, R0>(q, j) * kLanes + lane];
+#pragma unroll
+        for (int q = 0; q < E; ++q) pv[q] = act ? a.prev[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
+        __syncthreads();                 // every value read before the slot becomes the exchange tile
+        kinetic_line<N, false, kLanes>(v, slot, lane, j, tw, kin, R(a.mem[b].eta));
+        // the slot is free: order this thread's accesses before the tensor copy that refills it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const long long tn = t + (long long)S * gridDim.x;
+            if (tn < ntiles) issue(tn, s);
+        }
+        if (!act) continue;
+        if constexpr (AXIS == 1) {
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                const C p = pv[q];
+                a.prev[base + slot_pos<N, T, R0>(q, j) * stride] = mk<C>(p.x + v[q].y, p.y - v[q].x);
+            }
+        } else {
+            const int y = o;
+            const R gxy = a.mask[0][x] * a.mask[1][y];
+            bool ok = true;
+            int slo[3] = {0, 0, 0}, shi[3] = {0, 0, 0};
+            if constexpr (SRC) source_box<R>(a, slo, shi);
+            const bool src_col = SRC != 0 && x >= slo[0] && x < shi[0] && y >= slo[1] && y < shi[1];
+            const C sf = src_col ? a.tfac[(a.step - a.tfac_base) * a.batch + b] : zero_c<R, C>();
+#pragma unroll
+            for (int q = 0; q < E; ++q) {
+                const int z = slot_pos<N, T, R0>(q, j);
+                const long long idx = base + z * stride;
+                C p = pv[q];
+                if constexpr (SRC) {
+                    if (src_col && z >= slo[2] && z < shi[2]) {
+                        const C sa = source_acc<R, C, SRC>(a, b, sf, x, y, z, idx);
+                        p = mk<C>(p.x + a.c2 * sa.y, p.y - a.c2 * sa.x);
+                    }
+                }
+                const R g = gxy * a.mask[2][z];
+                const C acc = mk<C>(g * (p.x + v[q].y), g * (p.y - v[q].x));
+                ok = ok && finite_c<R>(acc.x, acc.y);
+                a.prev[idx] = acc;
+            }
+            if (!ok) atomicOr(a.flag, 1);
+        }
+    }
+    if (timed_out) {
+        if (threadIdx.x == 0) {
+            atomicOr(a.flag, 2);
+            // the copies this CTA still has in flight land in its own shared memory: wait for
+            // them (bounded) before the CTA exits
+            for (int k = 0; k < S; ++k) {
+                const int itk = it + k;
+                const long long tk = blockIdx.x + (long long)itk * gridDim.x;
+                if (tk >= ntiles) break;
+                mbar_wait_bounded(&full[itk % S], (unsigned)(itk / S) & 1u, kWaitLimitNs);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------
 template <typename R, int N> size_t pass_smem() { return sizeof(typename StepArgs<R>::C) * (size_t)N * kPitch; }
@@ -1023,10 +1228,26 @@ template <typename R, int N, int AXIS, bool SRC> cudaError_t colpass_pipe_n(cons
     }
 }
 
+template <typename R, int N, int AXIS, int SRC> cudaError_t colpass_tma_n(const StepArgs<R>& a, int batch, cudaStream_t s)
+{
+    if constexpr (tma_pass_supported<R, N>()) {
+        const size_t sm = tma_smem<N>();
+        cudaError_t e = set_smem_once<colpass_tma_kernel<R, N, AXIS, SRC>>(sm);
+        if (e != cudaSuccess) return e;
+        const long long ntiles = (long long)((a.nx + kLanes - 1) / kLanes) * (AXIS == 1 ? a.nz : a.ny) * batch;
+        const dim3 grid((unsigned)std::min<long long>(ntiles, (long long)sm_count() * tma_ctas_sm<N>()));
+        return launch_step_kernel(colpass_tma_kernel<R, N, AXIS, SRC>, grid, dim3(kLanes * Plan<N>::T), sm, s, a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
+    if constexpr (tma_pass_supported<R, N>())
+        if (!d && a.pipe_y == PSTD_LINE_TMA) return colpass_tma_n<R, N, 1, 0>(a, batch, s);
     if constexpr (pipe_supported<R, N>())
-        if (!d && a.pipe_y) return colpass_pipe_n<R, N, 1, false>(a, batch, s);
+        if (!d && a.pipe_y == PSTD_LINE_PIPELINED) return colpass_pipe_n<R, N, 1, false>(a, batch, s);
     const size_t sm = pass_smem<R, N>();
     cudaError_t e = d ? set_smem_once<ypass_kernel<R, N, true>>(sm) : set_smem_once<ypass_kernel<R, N, false>>(sm);
     if (e != cudaSuccess) return e;
@@ -1038,6 +1259,8 @@ template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const Dft
 template <typename R, int N, bool DFT, int SRC>
 cudaError_t zpass_launch(const StepArgs<R>& a, const DftArgs<R>& d, int batch, cudaStream_t s)
 {
+    if constexpr (!DFT && tma_pass_supported<R, N>())
+        if (a.tma_z) return colpass_tma_n<R, N, 2, SRC>(a, batch, s);
     const size_t sm = pass_smem<R, N>();
     cudaError_t e = set_smem_once<zpass_kernel<R, N, DFT, SRC>>(sm);
     if (e != cudaSuccess) return e;
@@ -1133,6 +1356,11 @@ cudaError_t launch_zpass(const StepArgs<R>& a, const DftArgs<R>* d, int src, int
 template <typename R> bool pipe_y_available(int ny)
 {
     return (ny == 192 && pipe_supported<R, 192>()) || (ny == 256 && pipe_supported<R, 256>());
+}
+template <typename R> bool tma_pass_available(int n)
+{
+    return (n == 128 && tma_pass_supported<R, 128>()) || (n == 192 && tma_pass_supported<R, 192>()) ||
+           (n == 256 && tma_pass_supported<R, 256>());
 }
 // fused xy pass, FP32 square planes: PSTD_XY_PLANE (one CTA per plane) for 64, 96 or 128;
 // PSTD_XY_CLUSTER (a cluster of N / 32 CTAs per plane) for 128, 192 or 256

@@ -21,6 +21,7 @@ MEM_HOST, MEM_DEVICE = 0, 1
 DTYPE_F32, DTYPE_F64 = 0, 1
 ABC_POLY, ABC_POSCHL_TELLER = 0, 1
 XY_SEPARATE, XY_PLANE, XY_CLUSTER = 0, 1, 2
+LINE_PLAIN, LINE_PIPELINED, LINE_TMA = 0, 1, 2
 TFSF_EXACT, TFSF_PAPER = 0, 1
 ENV_CW_RAMP = 0
 FIELD_CURRENT, FIELD_PREVIOUS, FIELD_SCATTERED = 0, 1, 2
@@ -64,6 +65,7 @@ _SIGS = {
     "pstd_synchronize": (c_int, [c_void_p]),
     "pstd_get_step": (c_int, [c_void_p, POINTER(c_long)]),
     "pstd_get_device": (c_int, [c_void_p, POINTER(c_int)]),
+    "pstd_measure_fma_peak": (c_int, [c_int, POINTER(c_double)]),
     "pstd_stability_dt_max": (c_int, [POINTER(GridDesc), c_double, POINTER(c_double)]),
     "pstd_set_timing": (c_int, [c_void_p, c_int]),
     "pstd_kernel_stats": (c_int, [c_void_p, c_int, POINTER(c_long), POINTER(c_double)]),
@@ -79,7 +81,7 @@ _SIGS = {
     "pstd_set_magnetic_field": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int, c_int]),
     "pstd_set_incidence_spinor": (c_int, [c_void_p, c_int, POINTER(c_double), c_double, c_double, POINTER(c_double)]),
     "pstd_graph_replays": (c_int, [c_void_p, POINTER(c_long)]),
-    "pstd_set_variants": (c_int, [c_void_p, c_int, c_int]),
+    "pstd_set_variants": (c_int, [c_void_p, c_int, c_int, c_int]),
     "pstd_autotune": (c_int, [c_void_p, c_long, POINTER(c_int)]),
 }
 
@@ -153,6 +155,13 @@ def make_desc(spec, precision: int = F32, batch: int = 1, stream=None) -> GridDe
     d.huygens_hi[:] = list(spec.huygens_hi)
     d.stream = stream
     return d
+
+
+def measure_fma_peak(precision: int) -> float:
+    """Measured FMA peak of the current device in TFLOP/s (pstd_measure_fma_peak)."""
+    out = c_double()
+    _check(load_library().pstd_measure_fma_peak(int(precision), byref(out)), "pstd_measure_fma_peak")
+    return out.value
 
 
 def stability_dt_max(spec, vmax: float) -> float:
@@ -320,17 +329,17 @@ class Grid:
                 "pstd_transform_adjoint")
         return self.split_phasors(out)
 
-    def set_variants(self, fused_xy, pipelined_y: bool):
-        """Force the step-kernel variants (pstd_set_variants): fused_xy is XY_SEPARATE,
-        XY_PLANE or XY_CLUSTER (True means XY_PLANE)."""
-        self._c(self.lib.pstd_set_variants(self.h, int(fused_xy), int(bool(pipelined_y))), "pstd_set_variants")
+    def set_variants(self, fused_xy: int, y_pass: int = 0, z_pass: int = 0):
+        """Force the step-kernel variants (pstd_set_variants): fused_xy is XY_SEPARATE, XY_PLANE
+        or XY_CLUSTER; y_pass and z_pass are LINE_PLAIN, LINE_PIPELINED (y only) or LINE_TMA."""
+        self._c(self.lib.pstd_set_variants(self.h, int(fused_xy), int(y_pass), int(z_pass)), "pstd_set_variants")
 
     def autotune(self, trial_steps: int = 20):
         """Time the available step-kernel variants and keep the fastest (pstd_autotune);
-        returns {"fused_xy": XY_SEPARATE | XY_PLANE | XY_CLUSTER, "pipelined_y": bool}."""
-        out = (c_int * 2)()
+        returns {"fused_xy": XY_*, "y_pass": LINE_*, "z_pass": LINE_*}."""
+        out = (c_int * 3)()
         self._c(self.lib.pstd_autotune(self.h, int(trial_steps), out), "pstd_autotune")
-        return {"fused_xy": int(out[0]), "pipelined_y": bool(out[1])}
+        return {"fused_xy": int(out[0]), "y_pass": int(out[1]), "z_pass": int(out[2])}
 
     def graph_replays(self) -> int:
         n = c_long()

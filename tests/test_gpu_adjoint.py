@@ -203,11 +203,11 @@ def test_adjoint_call_errors():
 
 @pytest.fixture(scope="module")
 def oracle_48():
-    """The adjoint workload's construction on a 48^3 grid (V on the central 12^3 block of
+    """The adjoint workload's construction on a 48^3 grid (V on the central 18^3 block of
     seeded smoothed noise, 400 steps, an 8 x 8 Fresnel plane): the FP64 oracle's loss and its
     discrete-adjoint gradient."""
-    wl, V_target = inputs.adjoint_workload(n=48, nsteps=400, block=12, fresnel_count=8, abc=8, tf=(14, 34), taper=4,
-                                           hb=(11, 37))
+    wl, V_target = inputs.adjoint_workload(n=48, nsteps=400, block=18, fresnel_count=8, abc=4, tf=(8, 40), taper=4,
+                                           hb=(5, 43))
     inc = wl.incidences[0]
     win = (wl.window_first, wl.window_len)
     from oracle import ntdf_oracle as no
@@ -224,7 +224,7 @@ def oracle_48():
 def test_adjoint_gradient_matches_oracle_at_48_cubed(oracle_48, prec, tol):
     wl, target, L_ref, grad_ref, psi_ref = oracle_48
     inc = wl.incidences[0]
-    lo, hi = (18, 18, 18), (30, 30, 30)          # the 12^3 block of V
+    lo, hi = (15, 15, 15), (33, 33, 33)          # the 18^3 block of V
     with pstd.Grid(wl.spec, precision=prec) as g:
         g.set_potential(wl.V)
         g.set_incidence(0, inc.khat, inc.k, inc.ramp_time)

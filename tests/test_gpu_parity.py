@@ -101,6 +101,16 @@ ONE_STEP_SPECS = {
                                                       abc_cells=(10, 10, 2), tfsf_lo=(44, 44, 5), tfsf_hi=(84, 84, 11),
                                                       taper_cells=2, huygens_lo=(36, 36, 3), huygens_hi=(92, 92, 13),
                                                       tfsf_mode=mode),
+    # z lines of 128, 192 and 256 points: the tensor-copy-fed z pass (FP32)
+    "line256-z": lambda mode: inputs.GridSpec(n=(48, 12, 256), d=(0.3, 0.4, 0.1), dt=0.0015, abc_cells=(3, 1, 20),
+                                              tfsf_lo=(12, 4, 80), tfsf_hi=(28, 8, 176), taper_cells=1,
+                                              huygens_lo=(8, 2, 60), huygens_hi=(32, 10, 196), tfsf_mode=mode),
+    "line128-z": lambda mode: inputs.GridSpec(n=(24, 16, 128), d=(0.3, 0.3, 0.15), dt=0.002, abc_cells=(2, 2, 10),
+                                              tfsf_lo=(8, 5, 40), tfsf_hi=(16, 11, 88), taper_cells=1,
+                                              huygens_lo=(5, 3, 30), huygens_hi=(19, 13, 98), tfsf_mode=mode),
+    "line192-z": lambda mode: inputs.GridSpec(n=(32, 8, 192), d=(0.3, 0.4, 0.12), dt=0.002, abc_cells=(3, 1, 16),
+                                              tfsf_lo=(9, 3, 60), tfsf_hi=(23, 5, 132), taper_cells=1,
+                                              huygens_lo=(5, 2, 40), huygens_hi=(27, 6, 150), tfsf_mode=mode),
     # the paper's own absorber profile (Eq. Poshcl-Teller) on the ragged grid
     "ragged-poschl-teller": lambda mode: dataclasses.replace(ragged_spec(mode), abc_profile="poschl_teller",
                                                              abc_param=(5.0, 0.3)),
@@ -713,18 +723,30 @@ def test_graph_is_not_replayed_after_a_new_potential():
 # ----------------------------------------------------------------------------------
 # step-kernel variants and the autotuner
 # ----------------------------------------------------------------------------------
-@pytest.mark.parametrize("name,variants", [("square-64x64x48", (pstd.XY_PLANE, False)),
-                                           ("square-64x64x48", (pstd.XY_SEPARATE, False)),
-                                           ("pipe-16x192x256", (pstd.XY_SEPARATE, True)),
-                                           ("pipe-16x192x256", (pstd.XY_SEPARATE, False)),
-                                           ("line256-y", (pstd.XY_SEPARATE, True)), ("line256-y", (pstd.XY_SEPARATE, False)),
-                                           ("square-256x256x12", (pstd.XY_CLUSTER, False)),
-                                           ("square-256x256x12", (pstd.XY_SEPARATE, True)),
-                                           ("square-256x256x12", (pstd.XY_SEPARATE, False)),
-                                           ("square-192x192x12", (pstd.XY_CLUSTER, False)),
-                                           ("square-128x128x16", (pstd.XY_PLANE, False)),
-                                           ("square-128x128x16", (pstd.XY_CLUSTER, False)),
-                                           ("square-128x128x16", (pstd.XY_SEPARATE, False))])
+X, L = pstd, pstd
+VARIANTS = [("square-64x64x48", (X.XY_PLANE, L.LINE_PLAIN, L.LINE_PLAIN)),
+            ("square-64x64x48", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN)),
+            ("pipe-16x192x256", (X.XY_SEPARATE, L.LINE_PIPELINED, L.LINE_PLAIN)),
+            ("pipe-16x192x256", (X.XY_SEPARATE, L.LINE_TMA, L.LINE_TMA)),
+            ("pipe-16x192x256", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN)),
+            ("line256-y", (X.XY_SEPARATE, L.LINE_PIPELINED, L.LINE_PLAIN)),
+            ("line256-y", (X.XY_SEPARATE, L.LINE_TMA, L.LINE_PLAIN)),
+            ("line256-y", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN)),
+            ("square-256x256x12", (X.XY_CLUSTER, L.LINE_PLAIN, L.LINE_PLAIN)),
+            ("square-256x256x12", (X.XY_SEPARATE, L.LINE_PIPELINED, L.LINE_PLAIN)),
+            ("square-256x256x12", (X.XY_SEPARATE, L.LINE_TMA, L.LINE_PLAIN)),
+            ("square-256x256x12", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN)),
+            ("square-192x192x12", (X.XY_CLUSTER, L.LINE_PLAIN, L.LINE_PLAIN)),
+            ("square-128x128x16", (X.XY_PLANE, L.LINE_PLAIN, L.LINE_PLAIN)),
+            ("square-128x128x16", (X.XY_CLUSTER, L.LINE_PLAIN, L.LINE_PLAIN)),
+            ("square-128x128x16", (X.XY_SEPARATE, L.LINE_TMA, L.LINE_PLAIN)),
+            ("line256-z", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_TMA)),
+            ("line256-z", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN)),
+            ("line128-z", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_TMA)),
+            ("line192-z", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_TMA))]
+
+
+@pytest.mark.parametrize("name,variants", VARIANTS)
 def test_every_variant_matches_oracle(name, variants):
     spec = ONE_STEP_SPECS[name]("exact")
     V = random_core_V(spec, 3)
@@ -752,10 +774,11 @@ def test_autotune_keeps_the_state_and_picks_available_variants():
         g.step(7)
         before, n = g.get_field(0), g.get_step()
         chosen = g.autotune(10)
-        assert chosen["pipelined_y"] is False            # not available for 64-point y lines
+        assert chosen["y_pass"] == pstd.LINE_PLAIN      # 64-point y lines: only the plain y pass
         assert chosen["fused_xy"] in (pstd.XY_SEPARATE, pstd.XY_PLANE)
         assert g.get_step() == n and np.array_equal(g.get_field(0), before)
-        for bad in ((pstd.XY_SEPARATE, True), (pstd.XY_CLUSTER, False), (3, False)):
+        for bad in ((pstd.XY_SEPARATE, pstd.LINE_PIPELINED, 0), (pstd.XY_CLUSTER, 0, 0), (3, 0, 0),
+                    (pstd.XY_SEPARATE, pstd.LINE_TMA, 0), (pstd.XY_SEPARATE, 0, pstd.LINE_PIPELINED)):
             with pytest.raises(pstd.PstdError) as e:
                 g.set_variants(*bad)
             assert e.value.code == "EINVAL"
