@@ -32,9 +32,10 @@ METRIC = "PSTD cell-updates/s, FP32 vs FP64 at stated error (1 GB300); adjoint/f
 # DRAM bytes (read + write) of one cold launch at 128^3, from an ncu --set full capture of
 # that kernel (dram__bytes_read.sum + dram__bytes_write.sum); drop an entry when its kernel changes
 DRAM_TRAFFIC = {"xypass": 34.05e6, "zpass": 34.65e6}
-# the same for the 256^3 passes of the batched leg, captured with 4 members (the leg scales
-# them by the units processed to its own member count)
-BATCHED_TRAFFIC = {"xpass": 2.029e9, "zpass": 1.658e9}
+# the same for the 256^3 passes of the batched leg (the cluster-fused x+y pass and the z
+# pass, steps outside the DFT window), captured with 4 members; the leg scales them by the
+# units processed to its own member count
+BATCHED_TRAFFIC = {"xypass": 1.6117e9 + 0.8507e9, "zpass": 1.0848e9 + 0.5744e9}
 WORKLOAD = "gaussian-sum-128^3"
 
 
@@ -365,7 +366,7 @@ def run_gpu(args):
     # 48^3 block (128^3, FP32, 2000 steps, 128^2 points), timed against its forward run
     adjoint = None if args.skip_adjoint else adjoint_leg(pstd, inputs, stream, dev)
     # batched leg: 16 incidences against one potential on a 256^3 grid (HBM-bound regime)
-    batched = None if args.skip_batched else batched_leg(pstd, inputs, stream, dev, flush)
+    batched = None if args.skip_batched else batched_leg(pstd, inputs, stream, dev, flush, shell_points=args.shell_points)
     # spinor leg: two spin states of a sigma . B scattering problem on a 384^3 grid
     spinor = None if args.skip_spinor else spinor_leg(pstd, inputs, stream, dev, flush)
     # auxiliary-wave leg: arbitrary incident packets from the 1-D auxiliary axis
@@ -403,10 +404,12 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80):
+def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80, shell_points=1_000_000):
     """Cell-updates/s of the batched 256^3 x 16 configuration over 80 steps (the last half in
-    every member's DFT window), plus the HBM roofline of its dominant pass.  `members` < 16
-    keeps only the first members (a smaller case of the same kernels, for profiling)."""
+    every member's DFT window), with the step variants chosen by the library's autotuner, the
+    HBM roofline of the step, and the surface transform of every member to `shell_points`
+    seeded points between 0.5 D^2/lambda and 4 D^2/lambda (one pstd_transform_members call).
+    `members` < 16 keeps only the first members (a smaller case of the same kernels)."""
     import torch
     wl = inputs.batched_workload()
     if members:
@@ -415,10 +418,16 @@ def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80):
     B = len(wl.incidences)
     g = pstd.Grid(spec, precision=pstd.F32, batch=B, stream=stream.cuda_stream)
     g.set_potential(torch.from_numpy(wl.V).to(dev))
+    # each member's DFT window covers the same fraction of the timed steps as its last three
+    # carrier periods do of the workload's 3000 (k = 2 pi: 261 steps, k = pi: 1044)
+    wins = []
     for b, inc in enumerate(wl.incidences):
         g.set_incidence(b, inc.khat, inc.k, inc.ramp_time)
-        g.huygens_dft(b, [spec.hbar * inc.k ** 2 / (2 * spec.mass)], nsteps // 2, nsteps - nsteps // 2)
+        wlen = max(1, round(wl.windows[b][1] * nsteps / wl.nsteps))
+        wins.append(wlen)
+        g.huygens_dft(b, [spec.hbar * inc.k ** 2 / (2 * spec.mass)], nsteps - wlen, wlen)
     ncell = int(np.prod(spec.n))
+    variants = g.autotune(6)
     times = []
     for rep in range(3):   # the first repetition is a warm-up
         g.reset()
@@ -436,13 +445,32 @@ def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80):
     g.step(nsteps)
     ks = {name: g.kernel_stats(name) for name in STEP_KERNELS}
     g.set_timing(False)
+    shell = None
+    if shell_points:
+        D = (spec.tfsf_hi[0] - spec.taper_cells - (spec.tfsf_lo[0] + spec.taper_cells)) * spec.d[0]
+        pts = torch.from_numpy(inputs.shell_points(shell_points, 0.5 * D * D, 4.0 * D * D, 2408)).to(dev)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        psi = g.transform_members(list(range(B)), [0] * B, pts)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        t_tr = ev[0].elapsed_time(ev[1]) / 1e3
+        cells = sum(2 * (spec.huygens_hi[b] - spec.huygens_lo[b]) * (spec.huygens_hi[c] - spec.huygens_lo[c])
+                    for (b, c) in ((1, 2), (0, 2), (0, 1)))
+        shell = {"points": shell_points, "members": B, "surface_cells": cells, "s": round(t_tr, 3),
+                 "points_per_s": shell_points * B / t_tr, "pairs_per_s": shell_points * B * cells / t_tr,
+                 "geometry": f"radius uniform in [0.5, 4] D^2/lambda, D = {D}, lambda = 1; direction uniform (seed 2408)",
+                 "finite": bool(torch.isfinite(psi).all())}
     g.close()
     traffic = {k: v * B / 4 for k, v in BATCHED_TRAFFIC.items()}   # captured at 4 members
     return {"workload": f"batched-256^3: {B} incidences (8 Fibonacci directions x k in {{2pi, pi}}) on one "
-                        f"Gaussian-sum potential, FP32, {nsteps} steps ({nsteps - nsteps // 2} in the DFT window)",
+                        f"Gaussian-sum potential, FP32, {nsteps} steps; DFT windows of the last {max(wins)} (k = pi) "
+                        f"and {min(wins)} (k = 2 pi) steps, the workload's 3000-step proportions",
             "value": B * ncell * nsteps / t, "unit": "cell-updates/s", "ms_per_step": t / nsteps * 1e3,
             "state_bytes": 2 * B * ncell * 8,
             "kernels_us": {n: round(v[1] / max(1, v[0]) * 1e3, 1) for n, v in ks.items() if v[0]},
+            "variants": variants, "shell_transform": shell,
             "roofline": step_roofline(ks, ncell, B, nsteps, t, traffic)}
 
 
@@ -462,7 +490,10 @@ def spinor_leg(pstd, inputs, stream, dev, flush, nsteps=80):
     g.set_magnetic_field(wl.B, wl.gamma)
     for p, chi in enumerate(wl.chis):
         g.set_incidence_spinor(p, inc.khat, inc.k, inc.ramp_time, chi)
-    g.huygens_dft(-1, [w0], nsteps // 2, nsteps - nsteps // 2)
+    # the DFT window covers the same fraction of the timed steps as the workload's last three
+    # carrier periods do of its 6000 steps
+    wlen = max(1, round(wl.window_len * nsteps / wl.nsteps))
+    g.huygens_dft(-1, [w0], nsteps - wlen, wlen)
     ncell = int(np.prod(spec.n))
 
     def timed(fn):
@@ -492,7 +523,7 @@ def spinor_leg(pstd, inputs, stream, dev, flush, nsteps=80):
     g.close()
     return {"workload": f"spinor-384^3: gamma sigma . B of a point dipole (cut off inside r = 1 and outside r = 12), "
                         f"unpolarised incidence as 2 spinors = {B} members, FP32, {nsteps} steps "
-                        f"({nsteps - nsteps // 2} in the DFT window)",
+                        f"({wlen} in the DFT window, the workload's 6000-step proportion)",
             "value": B * ncell * nsteps / t, "unit": "cell-updates/s", "ms_per_step": t / nsteps * 1e3,
             "state_bytes": 2 * B * ncell * 8,
             "kernels_us": {n: round(v[1] / max(1, v[0]) * 1e3, 1) for n, v in ks.items() if v[0]},
@@ -733,6 +764,8 @@ def main():
                    help="run only the batched leg (with --batched-members / --batched-steps) and print it")
     p.add_argument("--batched-members", type=int, default=0)
     p.add_argument("--batched-steps", type=int, default=80)
+    p.add_argument("--shell-points", type=int, default=1_000_000,
+                   help="observation points of the batched leg's shell transform (0 skips it)")
     args = p.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -742,7 +775,7 @@ def main():
         dev = torch.device("cuda", 0)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
         print(json.dumps(batched_leg(pstd, inputs, torch.cuda.current_stream(), dev, flush,
-                                     args.batched_members or None, args.batched_steps)), flush=True)
+                                     args.batched_members or None, args.batched_steps, args.shell_points)), flush=True)
     elif args.aux_only:
         import torch
         from paper_2403_04053_gb300 import inputs, pstd

@@ -189,6 +189,15 @@ pstd_status pstd_step(pstd_grid* g, long nsteps);
  * `mem` applies to both xyz and out_psi.  ESTATE if the window has not completed. */
 pstd_status pstd_transform_to_points(pstd_grid* g, int b, int f, const double* xyz, long M, void* out_psi, int mem);
 
+/* The same transform for several members at once (Eq. Psi for each): out_psi[i * M + p] is
+ * Psi of member members[i] at its DFT frequency freqs[i] at point p.  Members whose
+ * wavenumbers agree are transformed together, up to four in one launch, every point-cell
+ * Green's weight and quadrature phase serving all of them (the batched incidences of one
+ * potential).  members, freqs: count host ints; xyz (M x 3 doubles) and out_psi (count * M
+ * complex128) in `mem`.  ESTATE if any member's window has not completed. */
+pstd_status pstd_transform_members(pstd_grid* g, int count, const int* members, const int* freqs, const double* xyz, long M,
+                                   void* out_psi, int mem);
+
 /* Far-field amplitude f(theta, phi) = lim r e^{-ikr} Psi(r rhat) (the r -> infinity limit of
  * the same per-cell integrals) and dsigma/dOmega = |f|^2 at M directions.  out_dsdo: M
  * doubles; out_f: M complex128 or NULL.  `mem` applies to theta, phi, out_dsdo, out_f. */
@@ -318,14 +327,18 @@ pstd_status pstd_graph_replays(pstd_grid* g, long* count);
  *   PSTD_LINE_TMA        FP32 128/192/256-point lines: a persistent CTA streams its tiles with
  *                        tensor copies into a ring of shared-memory slots (mbarrier-completed),
  *                        several tiles in flight while one is transformed.
+ * plans: bit a set = axis a's register-fed line passes use the alternative FFT plan of their
+ * size (FP32, 128 and 256 points: radix 8-4-4 and 8-8-4 with twice the threads a line,
+ * instead of 16-8 and 16-16); the cluster form takes one plan for x and y together.
  * All variants compute the same step.  pstd_set_variants forces them (EINVAL where a variant
  * does not exist for the grid); pstd_autotune times trial_steps steps of every available
- * combination from the grid's current state, keeps the fastest and puts the state back (step
- * counter included; the running DFT is not touched).  out_variants (may be NULL): {fused_xy,
- * y_pass, z_pass} chosen.  Both synchronise. */
+ * combination of the pass forms from the grid's current state, then each axis's alternative
+ * plan with the best forms, keeps the fastest and puts the state back (step counter
+ * included; the running DFT is not touched).  out_variants (may be NULL): {fused_xy, y_pass,
+ * z_pass, plans} chosen.  Both synchronise. */
 enum { PSTD_XY_SEPARATE = 0, PSTD_XY_PLANE = 1, PSTD_XY_CLUSTER = 2 };
 enum { PSTD_LINE_PLAIN = 0, PSTD_LINE_PIPELINED = 1, PSTD_LINE_TMA = 2 };
-pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int y_pass, int z_pass);
+pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int y_pass, int z_pass, int plans);
 pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants);
 
 /* Measured fused multiply-add peak of the current device in TFLOP/s (2 flops per FMA) for

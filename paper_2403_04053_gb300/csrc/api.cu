@@ -206,6 +206,10 @@ struct pstd_grid {
     long ckpt_slots = 0;
     long long ckpt_upto = -1;
     void* rec = nullptr;
+    void* rec_group = nullptr;              // records of a member group ([member][cell][2 G G])
+    size_t rec_group_cap = 0;
+    double2* group_out = nullptr;           // a group's transform output when its members are not consecutive
+    size_t group_out_cap = 0;
     int rec_member = -1, rec_freq = -1;
     long long rec_version = -1;
     void* Fdft[6][2] = {};                  // per face: DFT matrices along b (Nb x Nb) and c (Nc x Nc)
@@ -228,6 +232,7 @@ struct pstd_grid {
     int xy_mode = PSTD_XY_SEPARATE;         // fused x + y pass (every step; with the plane DFT on window steps)
     int y_mode = PSTD_LINE_PLAIN;           // y pass form (192/256-point lines: pipelined; 128-256: TMA-fed)
     bool tma_z = false;                     // TMA-fed z pass (128/192/256-point lines, steps without the DFT)
+    int plans = 0;                          // bit a: axis a uses the alternative FFT plan of its size
     void* tmaps = nullptr;                  // tensor maps [level buffer][y, z] (device memory, 4 x 128 B)
     bool tma_y_ok = false, tma_z_ok = false;
     // CUDA-graph replay of repeated runs (see run_steps)
@@ -611,6 +616,7 @@ template <typename R> StepArgs<R> step_args(pstd_grid* g)
     a.packet_mask = g->packet_mask;
     a.pipe_y = g->y_mode;
     a.tma_z = g->tma_z ? 1 : 0;
+    for (int ax = 0; ax < 3; ++ax) a.plan[ax] = (g->plans >> ax) & 1;
     if (g->tmaps) {
         a.tmap_y = static_cast<const char*>(g->tmaps) + (size_t)(2 * g->cur + 0) * sizeof(CUtensorMap);
         a.tmap_z = static_cast<const char*>(g->tmaps) + (size_t)(2 * g->cur + 1) * sizeof(CUtensorMap);
@@ -1079,11 +1085,13 @@ pstd_status check_window(pstd_grid* g, int b, int f)
     return PSTD_OK;
 }
 
-template <typename R> pstd_status prepare_records(pstd_grid* g, int b, int f)
+// the cell records of member b, frequency f, into dst (ncells * 2 G^2 values): the grid's
+// own record buffer (cached per member, frequency and phasor version) when dst is null
+template <typename R> pstd_status prepare_records(pstd_grid* g, int b, int f, void* dst = nullptr)
 {
     pstd_status st = setup_transform(g);
     if (st != PSTD_OK) return st;
-    if (g->rec_member == b && g->rec_freq == f && g->rec_version == g->phasor_version) return PSTD_OK;
+    if (!dst && g->rec_member == b && g->rec_freq == f && g->rec_version == g->phasor_version) return PSTD_OK;
     const MemberHost& m = g->mem[b];
     const cd scale = 1.0 / m.inc_phasor[f];   // Eqs. scaledphsiphasor, scaleddpsiphasor
     const int G = g->G;
@@ -1105,11 +1113,14 @@ template <typename R> pstd_status prepare_records(pstd_grid* g, int b, int f)
         }
         Timer t(g, 4);
         CK(g, launch_pack_records<R>(static_cast<const C*>(g->OutP), static_cast<const C*>(g->OutD), F.L, F.M, G,
-                                     g->gl_w_dev, 0.25 * F.db * F.dc, F.cell0, static_cast<C*>(g->rec), g->stream));
+                                     g->gl_w_dev, 0.25 * F.db * F.dc, F.cell0, static_cast<C*>(dst ? dst : g->rec),
+                                     g->stream));
     }
-    g->rec_member = b;
-    g->rec_freq = f;
-    g->rec_version = g->phasor_version;
+    if (!dst) {
+        g->rec_member = b;
+        g->rec_freq = f;
+        g->rec_version = g->phasor_version;
+    }
     return PSTD_OK;
 }
 
@@ -1217,6 +1228,58 @@ pstd_status run_transform(pstd_grid* g, int b, int f, const double* pts, long M,
     {
         Timer t(g, 5);
         CK(g, launch_reduce_partials(g->partial, (int)splits, M, out, nullptr, g->stream));
+    }
+    return PSTD_OK;
+}
+
+// Several members (all with the wavenumber k) at once: their records side by side, one
+// transform launch in which every point-cell pair's Green's weight serves all of them.
+// out: [member][M].
+template <typename R>
+pstd_status run_transform_group(pstd_grid* g, const int* members, const int* freqs, int count, const double* pts, long M,
+                                double2* out)
+{
+    pstd_status st = setup_transform(g);
+    if (st != PSTD_OK) return st;
+    using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    const size_t rec_elems = (size_t)g->ncells * 2 * g->G * g->G;
+    st = ensure(g, &g->rec_group, g->rec_group_cap, (size_t)kTransformMembers * rec_elems * sizeof(C));
+    if (st != PSTD_OK) return st;
+    for (int i = 0; i < count; ++i) {
+        st = prepare_records<R>(g, members[i], freqs[i], static_cast<C*>(g->rec_group) + (size_t)i * rec_elems);
+        if (st != PSTD_OK) return st;
+    }
+    TransformArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.rec = static_cast<const C*>(g->rec_group);
+    a.members = count;
+    a.ncells = g->ncells;
+    for (int fi = 0; fi < 6; ++fi) a.face[fi] = g->faces[fi];
+    a.pts = pts;
+    a.M = M;
+    a.k = wavenumber_of(g, members[0], freqs[0]);
+    for (int q = 0; q < g->G; ++q) a.gl_node[q] = g->gl_x[q];
+    const long long blocks = (M + 127) / 128;
+    const int CH = sizeof(R) == 4 ? 32 : 16;
+    const long long chunks = (g->ncells + CH - 1) / CH;
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev);
+    const long long target = 4LL * 4 * nsm;
+    long long splits = std::max(1LL, std::min(chunks, (target + blocks - 1) / blocks));
+    splits = std::min(splits, 4096LL);
+    long long cps = ((g->ncells + splits - 1) / splits + CH - 1) / CH * CH;
+    splits = (g->ncells + cps - 1) / cps;
+    a.cells_per_split = cps;
+    st = ensure(g, &g->partial, g->partial_cap, (size_t)splits * count * M * sizeof(double2));
+    if (st != PSTD_OK) return st;
+    a.partial = g->partial;
+    {
+        Timer t(g, 5);
+        CK(g, launch_transform<R>(a, g->G, (int)splits, g->stream));
+    }
+    {
+        Timer t(g, 5);
+        CK(g, launch_reduce_partials(g->partial, (int)splits, (long long)count * M, out, nullptr, g->stream));
     }
     return PSTD_OK;
 }
@@ -1585,7 +1648,7 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     for (void* p : {g->buf[0], g->buf[1], g->V, (void*)g->mem_dev, (void*)g->acc, (void*)g->flag, (void*)g->gl_w_dev,
                     (void*)g->dft_phase, (void*)g->window_first_dev, g->tfac,
                     g->T1, g->OutP, g->OutD, g->Pw, g->rec, (void*)g->partial, (void*)g->pts_dev,
-                    (void*)g->out_dev, (void*)g->dsdo_dev, g->tmaps})
+                    (void*)g->out_dev, (void*)g->dsdo_dev, g->tmaps, g->rec_group, (void*)g->group_out})
         if (p) cudaFree(p);
     for (int a = 0; a < 3; ++a)
         for (void* p : {g->tw[a], g->kin[a], g->mask[a], g->zeta[a], g->zeta1[a], g->zeta2[a], g->phase[a], g->dw[a]})
@@ -2097,6 +2160,63 @@ pstd_status pstd_transform_to_points(pstd_grid* g, int b, int f, const double* x
     return PSTD_OK;
 }
 
+pstd_status pstd_transform_members(pstd_grid* g, int count, const int* members, const int* freqs, const double* xyz,
+                                   long M, void* out_psi, int mem)
+{
+    if (!g || count < 0 || (count > 0 && (!members || !freqs)) || (M > 0 && count > 0 && (!xyz || !out_psi)))
+        return fail(g, PSTD_EINVAL, "null argument");
+    if (M < 0) return fail(g, PSTD_EINVAL, "M");
+    DeviceGuard dg(g->dev);
+    for (int i = 0; i < count; ++i) {
+        pstd_status st = check_window(g, members[i], freqs[i]);
+        if (st != PSTD_OK) return st;
+    }
+    if (M == 0 || count == 0) return PSTD_OK;
+    if (mem != PSTD_MEM_HOST && mem != PSTD_MEM_DEVICE) return fail(g, PSTD_EINVAL, "mem");
+    const double* pts = xyz;
+    double2* out = static_cast<double2*>(out_psi);
+    pstd_status st;
+    if (mem == PSTD_MEM_HOST) {
+        st = ensure(g, &g->pts_dev, g->pts_cap, sizeof(double) * 3 * M);
+        if (st != PSTD_OK) return st;
+        st = ensure(g, &g->out_dev, g->out_cap, sizeof(double2) * M * count);
+        if (st != PSTD_OK) return st;
+        CK(g, cudaMemcpyAsync(g->pts_dev, xyz, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, g->stream));
+        pts = g->pts_dev;
+        out = g->out_dev;
+    }
+    // groups of up to kTransformMembers members with the same wavenumber, in the given order
+    std::vector<char> done(count, 0);
+    for (int i = 0; i < count; ++i) {
+        if (done[i]) continue;
+        const double k = wavenumber_of(g, members[i], freqs[i]);
+        std::vector<int> idx;
+        for (int j = i; j < count && (int)idx.size() < kTransformMembers; ++j)
+            if (!done[j] && wavenumber_of(g, members[j], freqs[j]) == k) idx.push_back(j);
+        std::vector<int> mb, fq;
+        for (int j : idx) { mb.push_back(members[j]); fq.push_back(freqs[j]); done[j] = 1; }
+        // the group's outputs are contiguous only when its members are consecutive in the call;
+        // otherwise they go through the grid's buffer and are copied to their places
+        bool consecutive = true;
+        for (size_t q = 1; q < idx.size(); ++q) consecutive = consecutive && idx[q] == idx[q - 1] + 1;
+        double2* dst = out + (size_t)idx[0] * M;
+        if (!consecutive) {
+            st = ensure(g, &g->group_out, g->group_out_cap, sizeof(double2) * M * idx.size());
+            if (st != PSTD_OK) return st;
+            dst = g->group_out;
+        }
+        st = g->prec == PSTD_F64 ? run_transform_group<double>(g, mb.data(), fq.data(), (int)idx.size(), pts, M, dst)
+                                 : run_transform_group<float>(g, mb.data(), fq.data(), (int)idx.size(), pts, M, dst);
+        if (st != PSTD_OK) return st;
+        if (!consecutive)
+            for (size_t q = 0; q < idx.size(); ++q)
+                CK(g, cudaMemcpyAsync(out + (size_t)idx[q] * M, dst + q * M, sizeof(double2) * M, cudaMemcpyDeviceToDevice,
+                                      g->stream));
+    }
+    if (mem == PSTD_MEM_HOST) return copy_out(g, out_psi, g->out_dev, sizeof(double2) * M * count, PSTD_MEM_HOST);
+    return PSTD_OK;
+}
+
 pstd_status pstd_cross_section(pstd_grid* g, int b, int f, const double* theta, const double* phi, long M, double* out_dsdo,
                                void* out_f, int mem)
 {
@@ -2449,19 +2569,28 @@ bool zmode_possible(const pstd_grid* g, int mode)
 {
     return mode == PSTD_LINE_PLAIN || (mode == PSTD_LINE_TMA && g->tma_z_ok);
 }
+// the axes whose line length has an alternative FFT plan (FP32 grids, 128 and 256 points)
+int alt_plan_axes(const pstd_grid* g)
+{
+    int m = 0;
+    for (int ax = 0; ax < 3; ++ax)
+        if (g->prec == PSTD_F32 && (g->desc.n[ax] == 128 || g->desc.n[ax] == 256)) m |= 1 << ax;
+    return m;
+}
 }  // namespace
 
-pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int y_pass, int z_pass)
+pstd_status pstd_set_variants(pstd_grid* g, int fused_xy, int y_pass, int z_pass, int plans)
 {
     if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
     if (fused_xy < PSTD_XY_SEPARATE || fused_xy > PSTD_XY_CLUSTER || !xy_possible(g, fused_xy) || !ymode_possible(g, y_pass) ||
-        !zmode_possible(g, z_pass))
+        !zmode_possible(g, z_pass) || (plans & ~alt_plan_axes(g)) != 0)
         return fail(g, PSTD_EINVAL, "variant not available for this grid");
     DeviceGuard dg(g->dev);
     ++g->config_version;
     g->xy_mode = fused_xy;
     g->y_mode = y_pass;
     g->tma_z = z_pass == PSTD_LINE_TMA;
+    g->plans = plans;
     return PSTD_OK;
 }
 
@@ -2497,6 +2626,22 @@ pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants)
         cudaMemcpyAsync(saved, g->buf[0], sbytes, cudaMemcpyDeviceToDevice, g->stream);
         cudaMemcpyAsync(static_cast<char*>(saved) + sbytes, g->buf[1], sbytes, cudaMemcpyDeviceToDevice, g->stream);
     }
+    // one trial: steps of the current variants from the saved state, timed
+    auto trial = [&](float* ms) -> pstd_status {
+        pstd_status t = restore();
+        if (t != PSTD_OK) return t;
+        t = g->prec == PSTD_F64 ? run_steps<double>(g, 2, false) : run_steps<float>(g, 2, false);   // warm-up
+        if (t != PSTD_OK) return t;
+        cudaEventRecord(e0, g->stream);
+        t = g->prec == PSTD_F64 ? run_steps<double>(g, trial_steps, false) : run_steps<float>(g, trial_steps, false);
+        if (t != PSTD_OK) return t;
+        cudaEventRecord(e1, g->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return fail(g, PSTD_ECUDA, "tuning events");
+        cudaEventElapsedTime(ms, e0, e1);
+        return PSTD_OK;
+    };
+    int best_plans = g->plans;
+    // the pass forms with the default plans, then each axis's alternative plan with the best forms
     for (int xy = PSTD_XY_CLUSTER; xy >= PSTD_XY_SEPARATE && st == PSTD_OK; --xy)
         for (int ym = PSTD_LINE_TMA; ym >= PSTD_LINE_PLAIN && st == PSTD_OK; --ym)
         for (int zm = PSTD_LINE_TMA; zm >= PSTD_LINE_PLAIN && st == PSTD_OK; zm -= 2) {
@@ -2505,19 +2650,33 @@ pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants)
             g->xy_mode = xy;
             g->y_mode = ym;
             g->tma_z = zm == PSTD_LINE_TMA;
-            st = restore();
-            if (st != PSTD_OK) break;
-            st = g->prec == PSTD_F64 ? run_steps<double>(g, 2, false) : run_steps<float>(g, 2, false);   // warm-up
-            if (st != PSTD_OK) break;
-            cudaEventRecord(e0, g->stream);
-            st = g->prec == PSTD_F64 ? run_steps<double>(g, trial_steps, false) : run_steps<float>(g, trial_steps, false);
-            if (st != PSTD_OK) break;
-            cudaEventRecord(e1, g->stream);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(g, PSTD_ECUDA, "tuning events"); break; }
+            g->plans = 0;
             float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (best < 0 || ms < best) { best = ms; best_xy = xy; best_y = ym; best_z = zm == PSTD_LINE_TMA; }
+            st = trial(&ms);
+            if (st != PSTD_OK) break;
+            if (best < 0 || ms < best) { best = ms; best_xy = xy; best_y = ym; best_z = zm == PSTD_LINE_TMA; best_plans = 0; }
         }
+    const int axes = alt_plan_axes(g);
+    for (int ax = 0; ax < 3 && st == PSTD_OK; ++ax) {
+        if (!((axes >> ax) & 1)) continue;
+        g->xy_mode = best_xy;
+        g->y_mode = best_y;
+        g->tma_z = best_z;
+        // the fused and register-free forms use the default plan; the x and y axes change together
+        // in the cluster form
+        int flip = 1 << ax;
+        if (ax == 0 && best_xy == PSTD_XY_CLUSTER) flip |= 2;
+        if (ax == 1 && best_xy == PSTD_XY_CLUSTER) continue;
+        if (best_xy == PSTD_XY_PLANE && ax < 2) continue;
+        if (ax == 1 && best_y != PSTD_LINE_PLAIN) continue;
+        if (ax == 2 && best_z) continue;
+        if ((flip & ~axes) != 0) continue;
+        g->plans = best_plans ^ flip;
+        float ms = 0;
+        st = trial(&ms);
+        if (st != PSTD_OK) break;
+        if (ms < best) { best = ms; best_plans = g->plans; }
+    }
     const pstd_status rs = restore();
     if (st == PSTD_OK) st = rs;
     CK(g, cudaStreamSynchronize(g->stream));
@@ -2528,11 +2687,13 @@ pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants)
     g->xy_mode = best_xy;
     g->y_mode = best_y;
     g->tma_z = best_z;
+    g->plans = best_plans;
     ++g->config_version;
     if (out_variants) {
         out_variants[0] = g->xy_mode;
         out_variants[1] = g->y_mode;
         out_variants[2] = g->tma_z ? PSTD_LINE_TMA : PSTD_LINE_PLAIN;
+        out_variants[3] = g->plans;
     }
     return st;
 }

@@ -186,7 +186,14 @@ template <int RAD, int DIR, typename C> __device__ __forceinline__ void dft(C* x
 // plans: radices (forward order) and threads per line; E = N / T must be a multiple
 // of every radix so each thread runs E / R butterflies per stage
 // ---------------------------------------------------------------------------------
-template <int N> struct Plan;
+// PL = 0: the default plan of each size; PL = 1: an alternative for 128 and 256 with twice the
+// threads a line and half the values a thread (radix-8 and radix-4 stages, one more exchange),
+// whose butterflies fit the 64-register budget of two resident CTAs without spilling.  The
+// step variants' autotuner picks between them per axis.
+template <int N, int PL = 0> struct Plan;
+template <int N> constexpr bool has_alt_plan() { return N == 128 || N == 256; }
+template <> struct Plan<128, 1> { static constexpr int T = 16; static constexpr int S = 3; static constexpr int R[4] = {8, 4, 4, 0}; };
+template <> struct Plan<256, 1> { static constexpr int T = 32; static constexpr int S = 3; static constexpr int R[4] = {8, 8, 4, 0}; };
 template <> struct Plan<8>   { static constexpr int T = 1;  static constexpr int S = 1; static constexpr int R[4] = {8, 0, 0, 0}; };
 template <> struct Plan<12>  { static constexpr int T = 1;  static constexpr int S = 1; static constexpr int R[4] = {12, 0, 0, 0}; };
 template <> struct Plan<16>  { static constexpr int T = 1;  static constexpr int S = 1; static constexpr int R[4] = {16, 0, 0, 0}; };
@@ -271,11 +278,11 @@ template <int N, int T, int RADL> __device__ __forceinline__ int spec_pos(int q,
 // inputs sit in the tile (x-lines loaded by a transposing copy) instead of v.  PS: the
 // exchange tile's row pitch (kLanes itself is conflict-free for the column passes, whose
 // lanes are consecutive; the transposing x-line copy needs kLanes + 1).
-template <int N, bool FIRST_FROM_SMEM, int PS = kPitch, typename C, int E>
+template <int N, bool FIRST_FROM_SMEM, int PS = kPitch, int PL = 0, typename C, int E>
 __device__ __forceinline__ void kinetic_line(C (&v)[E], C* sm, int lane, int j, const C* __restrict__ tw,
                                              const decltype(C::x)* __restrict__ kin, decltype(C::x) scale)
 {
-    using P = Plan<N>;
+    using P = Plan<N, PL>;
     constexpr int T = P::T;
     static_assert(E == N / T, "E");
     constexpr int R0 = P::R[0], R1 = P::R[1], R2 = P::R[2], R3 = P::R[3];

@@ -49,6 +49,7 @@ template <typename R> struct StepArgs {
     int mode;                // PSTD_TFSF_EXACT / PSTD_TFSF_PAPER
     int pipe_y;              // y pass form where available: PSTD_LINE_PIPELINED or PSTD_LINE_TMA (autotuner)
     int tma_z;               // z pass fed by tensor copies where available (autotuner)
+    int plan[3];             // per axis: 1 = the alternative FFT plan of the size (128, 256; FP32)
     const void* tmap_y;      // tensor maps of the current level (device memory): boxes of 32 y lines
     const void* tmap_z;      //   and of 32 z lines (see colpass_tma_kernel)
     int pf_l1;               // the state exceeds L2: the z pass prefetches its update operand to L1
@@ -187,6 +188,7 @@ template <typename R> cudaError_t launch_spectrum_pack(const typename std::condi
 template <typename R> struct TransformArgs {
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
     const C* rec;             // per cell: G*G psi node values then G*G dpsi node values (weights folded in)
+    int members;              // members transformed together (records [member][cell], all with wavenumber k)
     long long ncells;
     FaceGeom face[6];
     const double* pts;        // M x 3 points
@@ -194,7 +196,7 @@ template <typename R> struct TransformArgs {
     double k;
     double gl_node[16];       // Gauss-Legendre nodes on [-1, 1]
     long long cells_per_split;
-    double2* partial;         // [split][M]
+    double2* partial;         // [split][member][M]
 };
 
 // points per thread of the surface transform (CTAs of 128 threads): two points share each
@@ -203,6 +205,9 @@ template <typename R> struct TransformArgs {
 #define PSTD_TRANSFORM_PT 2
 #endif
 template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, int G, int splits, cudaStream_t s);
+// members per launch of the member-batched transform (one Green's weight per point-cell pair
+// serves every member's record)
+constexpr int kTransformMembers = 4;
 
 // ---------------------------------------------------------------------------------
 // discrete adjoint (see adjoint_kernels.cuh)

@@ -45,11 +45,11 @@ template <typename T> __device__ __forceinline__ void prefetch_l1(const T* p)
 // thread, 2048 threads an SM): 4 CTAs of 256 threads let the 512 CTAs of a 128^3 pass run
 // in one wave on 152 SMs; for the 512-thread CTAs of N = 192 and 256 (at most 16 values a
 // thread) 2 CTAs, so that HBM-bound passes keep enough loads in flight.
-template <typename R, int N> constexpr int pass_min_blocks()
+template <typename R, int N, int PL = 0> constexpr int pass_min_blocks()
 {
     return !(sizeof(R) == 4) ? 1
-           : Plan<N>::T <= 8 ? (PSTD_PREFETCH_PREV ? 2 : 4) * (32 / kLanes)
-           : (Plan<N>::T == 16 && N / Plan<N>::T <= 16) ? 2 * (32 / kLanes)
+           : Plan<N, PL>::T <= 8 ? (PSTD_PREFETCH_PREV ? 2 : 4) * (32 / kLanes)
+           : (Plan<N, PL>::T == 16 && N / Plan<N, PL>::T <= 16) ? 2 * (32 / kLanes)
            : 1;
 }
 
@@ -200,12 +200,12 @@ __device__ __forceinline__ void dft_finish(const C (&part)[4], C* red, int lane,
 // contiguous, so the tile is one contiguous block of 32 * nx values)
 // ---------------------------------------------------------------------------------
 // The x-line work of one CTA: rows [row0, row0 + kLanes) of member b (row = z * ny + y).
-template <typename R, int N, bool DFT>
+template <typename R, int N, bool DFT, int PL = 0>
 __device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R>& d, int b, int row0,
                                            typename StepArgs<R>::C* sm)
 {
     using C = typename StepArgs<R>::C;
-    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
+    constexpr int T = Plan<N, PL>::T, E = N / T, R0 = Plan<N, PL>::R[0];
     const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
     const int rows = a.ny * a.nz;
     const int nrows = min(kLanes, rows - row0);
@@ -241,7 +241,7 @@ __device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R
     C part[4];
     if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
     const R eta = R(a.mem[b].eta);
-    kinetic_line<N, false>(v, sm, lane, j, a.tw[0], a.kin[0], eta);
+    kinetic_line<N, false, kPitch, PL>(v, sm, lane, j, a.tw[0], a.kin[0], eta);
     __syncthreads();
     if (dft) dft_finish<R, T>(part, sm, lane, j, d, b, row0 + lane, lane < nrows);   // plane [z][y]: pixel = row
 #pragma unroll
@@ -265,12 +265,12 @@ __device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R
     }
 }
 
-template <typename R, int N, bool DFT>
-__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) xpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+template <typename R, int N, bool DFT, int PL = 0>
+__global__ void __launch_bounds__(kLanes * Plan<N, PL>::T, (pass_min_blocks<R, N, PL>())) xpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
 {
     step_kernel_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
-    xpass_tile<R, N, DFT>(a, d, blockIdx.y, blockIdx.x * kLanes, reinterpret_cast<typename StepArgs<R>::C*>(smraw));
+    xpass_tile<R, N, DFT, PL>(a, d, blockIdx.y, blockIdx.x * kLanes, reinterpret_cast<typename StepArgs<R>::C*>(smraw));
 }
 
 // ---------------------------------------------------------------------------------
@@ -285,12 +285,12 @@ template <bool CG, typename C> __device__ __forceinline__ C load_prev(const C* p
 }
 
 // The y-line work of one CTA: columns [x0, x0 + kLanes) of z plane z, member b.
-template <typename R, int N, bool DFT, bool CG = false>
+template <typename R, int N, bool DFT, bool CG = false, int PL = 0>
 __device__ __forceinline__ void ypass_tile(const StepArgs<R>& a, const DftArgs<R>& d, int x0, int z, int b,
                                            typename StepArgs<R>::C* sm)
 {
     using C = typename StepArgs<R>::C;
-    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
+    constexpr int T = Plan<N, PL>::T, E = N / T, R0 = Plan<N, PL>::R[0];
     const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
     const int x = x0 + lane;
     const bool act = x < a.nx;
@@ -316,7 +316,7 @@ __device__ __forceinline__ void ypass_tile(const StepArgs<R>& a, const DftArgs<R
     C part[4];
     if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
     const R eta = R(a.mem[b].eta);
-    kinetic_line<N, false>(v, sm, lane, j, a.tw[1], a.kin[1], eta);
+    kinetic_line<N, false, kPitch, PL>(v, sm, lane, j, a.tw[1], a.kin[1], eta);
     if (dft) {
         __syncthreads();   // the exchange tile is free again
         dft_stage<T>(part, sm, lane, j);
@@ -345,12 +345,13 @@ __device__ __forceinline__ void ypass_tile(const StepArgs<R>& a, const DftArgs<R
     if (dft && j == 0) dft_commit<R, T>(sm, lane, d, b, (long long)z * a.nx + x);   // plane [z][x]
 }
 
-template <typename R, int N, bool DFT>
-__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) ypass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+template <typename R, int N, bool DFT, int PL = 0>
+__global__ void __launch_bounds__(kLanes * Plan<N, PL>::T, (pass_min_blocks<R, N, PL>())) ypass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
 {
     step_kernel_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
-    ypass_tile<R, N, DFT>(a, d, blockIdx.x * kLanes, blockIdx.y, blockIdx.z, reinterpret_cast<typename StepArgs<R>::C*>(smraw));
+    ypass_tile<R, N, DFT, false, PL>(a, d, blockIdx.x * kLanes, blockIdx.y, blockIdx.z,
+                                     reinterpret_cast<typename StepArgs<R>::C*>(smraw));
 }
 
 // ---------------------------------------------------------------------------------
@@ -377,10 +378,10 @@ __device__ __forceinline__ void cluster_sync_acq_rel()
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-template <typename R, int N, bool DFT>
-__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) xycl_kernel(const __grid_constant__ StepArgs<R> a,
-                                                                                           const __grid_constant__ DftArgs<R> dx,
-                                                                                           const __grid_constant__ DftArgs<R> dy)
+template <typename R, int N, bool DFT, int PL = 0>
+__global__ void __launch_bounds__(kLanes * Plan<N, PL>::T, (pass_min_blocks<R, N, PL>())) xycl_kernel(const __grid_constant__ StepArgs<R> a,
+                                                                                                   const __grid_constant__ DftArgs<R> dx,
+                                                                                                   const __grid_constant__ DftArgs<R> dy)
 {
     step_kernel_entry();
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -388,9 +389,9 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
     C* sm = reinterpret_cast<C*>(smraw);
     const int r = blockIdx.x;                  // rank in the cluster (the grid's x extent is the cluster)
     const int z = blockIdx.y, b = blockIdx.z;
-    xpass_tile<R, N, DFT>(a, dx, b, z * N + r * kLanes, sm);
+    xpass_tile<R, N, DFT, PL>(a, dx, b, z * N + r * kLanes, sm);
     cluster_sync_acq_rel();
-    ypass_tile<R, N, DFT, true>(a, dy, r * kLanes, z, b, sm);
+    ypass_tile<R, N, DFT, true, PL>(a, dy, r * kLanes, z, b, sm);
 }
 
 // ---------------------------------------------------------------------------------
@@ -751,12 +752,12 @@ __global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ Ste
 // ---------------------------------------------------------------------------------
 // SRC: 0 no V-term or source; otherwise the source form (source_acc's KIND: 1 scalar CW
 // members only, 3 CW and wave packets, 4 CW and the auxiliary wave, 2 any members)
-template <typename R, int N, bool DFT, int SRC>
-__global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())) zpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+template <typename R, int N, bool DFT, int SRC, int PL = 0>
+__global__ void __launch_bounds__(kLanes * Plan<N, PL>::T, (pass_min_blocks<R, N, PL>())) zpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
 {
     step_kernel_entry();
     using C = typename StepArgs<R>::C;
-    constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0];
+    constexpr int T = Plan<N, PL>::T, E = N / T, R0 = Plan<N, PL>::R[0];
     extern __shared__ __align__(16) unsigned char smraw[];
     C* sm = reinterpret_cast<C*>(smraw);
     const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
@@ -785,7 +786,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, (pass_min_blocks<R, N>())
 #endif
     C part[4];
     if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
-    kinetic_line<N, false>(v, sm, lane, j, a.tw[2], a.kin[2], R(a.mem[b].eta));
+    kinetic_line<N, false, kPitch, PL>(v, sm, lane, j, a.tw[2], a.kin[2], R(a.mem[b].eta));
     if (dft) {
         __syncthreads();   // the exchange tile is free again
         dft_stage<T>(part, sm, lane, j);
@@ -1191,15 +1192,25 @@ template <auto kernel> cudaError_t set_smem_once(size_t bytes)
     return e;
 }
 
-template <typename R, int N> cudaError_t xpass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
+// the alternative plan of a size where it exists, for FP32 (the per-axis choice in StepArgs::plan)
+template <typename R, int N> constexpr bool alt_plan_built() { return sizeof(R) == 4 && has_alt_plan<N>(); }
+
+template <typename R, int N, int PL> cudaError_t xpass_pl(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
     const size_t sm = pass_smem<R, N>();
-    cudaError_t e = d ? set_smem_once<xpass_kernel<R, N, true>>(sm) : set_smem_once<xpass_kernel<R, N, false>>(sm);
+    cudaError_t e = d ? set_smem_once<xpass_kernel<R, N, true, PL>>(sm) : set_smem_once<xpass_kernel<R, N, false, PL>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.ny * a.nz + kLanes - 1) / kLanes, batch);
     const DftArgs<R> none{};
-    if (d) return launch_step_kernel(xpass_kernel<R, N, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
-    return launch_step_kernel(xpass_kernel<R, N, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
+    if (d) return launch_step_kernel(xpass_kernel<R, N, true, PL>, grid, dim3(kLanes * Plan<N, PL>::T), sm, s, a, *d);
+    return launch_step_kernel(xpass_kernel<R, N, false, PL>, grid, dim3(kLanes * Plan<N, PL>::T), sm, s, a, none);
+}
+
+template <typename R, int N> cudaError_t xpass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
+{
+    if constexpr (alt_plan_built<R, N>())
+        if (a.plan[0]) return xpass_pl<R, N, 1>(a, d, batch, s);
+    return xpass_pl<R, N, 0>(a, d, batch, s);
 }
 inline int sm_count()
 {
@@ -1242,30 +1253,45 @@ template <typename R, int N, int AXIS, int SRC> cudaError_t colpass_tma_n(const 
     }
 }
 
+template <typename R, int N, int PL> cudaError_t ypass_pl(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
+{
+    const size_t sm = pass_smem<R, N>();
+    cudaError_t e = d ? set_smem_once<ypass_kernel<R, N, true, PL>>(sm) : set_smem_once<ypass_kernel<R, N, false, PL>>(sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.nx + kLanes - 1) / kLanes, a.nz, batch);
+    const DftArgs<R> none{};
+    if (d) return launch_step_kernel(ypass_kernel<R, N, true, PL>, grid, dim3(kLanes * Plan<N, PL>::T), sm, s, a, *d);
+    return launch_step_kernel(ypass_kernel<R, N, false, PL>, grid, dim3(kLanes * Plan<N, PL>::T), sm, s, a, none);
+}
+
 template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
     if constexpr (tma_pass_supported<R, N>())
         if (!d && a.pipe_y == PSTD_LINE_TMA) return colpass_tma_n<R, N, 1, 0>(a, batch, s);
     if constexpr (pipe_supported<R, N>())
         if (!d && a.pipe_y == PSTD_LINE_PIPELINED) return colpass_pipe_n<R, N, 1, false>(a, batch, s);
-    const size_t sm = pass_smem<R, N>();
-    cudaError_t e = d ? set_smem_once<ypass_kernel<R, N, true>>(sm) : set_smem_once<ypass_kernel<R, N, false>>(sm);
-    if (e != cudaSuccess) return e;
-    dim3 grid((a.nx + kLanes - 1) / kLanes, a.nz, batch);
-    const DftArgs<R> none{};
-    if (d) return launch_step_kernel(ypass_kernel<R, N, true>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, *d);
-    return launch_step_kernel(ypass_kernel<R, N, false>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, none);
+    if constexpr (alt_plan_built<R, N>())
+        if (a.plan[1]) return ypass_pl<R, N, 1>(a, d, batch, s);
+    return ypass_pl<R, N, 0>(a, d, batch, s);
 }
+template <typename R, int N, bool DFT, int SRC, int PL>
+cudaError_t zpass_launch_pl(const StepArgs<R>& a, const DftArgs<R>& d, int batch, cudaStream_t s)
+{
+    const size_t sm = pass_smem<R, N>();
+    cudaError_t e = set_smem_once<zpass_kernel<R, N, DFT, SRC, PL>>(sm);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.nx + kLanes - 1) / kLanes, a.ny, batch);
+    return launch_step_kernel(zpass_kernel<R, N, DFT, SRC, PL>, grid, dim3(kLanes * Plan<N, PL>::T), sm, s, a, d);
+}
+
 template <typename R, int N, bool DFT, int SRC>
 cudaError_t zpass_launch(const StepArgs<R>& a, const DftArgs<R>& d, int batch, cudaStream_t s)
 {
     if constexpr (!DFT && tma_pass_supported<R, N>())
         if (a.tma_z) return colpass_tma_n<R, N, 2, SRC>(a, batch, s);
-    const size_t sm = pass_smem<R, N>();
-    cudaError_t e = set_smem_once<zpass_kernel<R, N, DFT, SRC>>(sm);
-    if (e != cudaSuccess) return e;
-    dim3 grid((a.nx + kLanes - 1) / kLanes, a.ny, batch);
-    return launch_step_kernel(zpass_kernel<R, N, DFT, SRC>, grid, dim3(kLanes * Plan<N>::T), sm, s, a, d);
+    if constexpr (alt_plan_built<R, N>())
+        if (a.plan[2]) return zpass_launch_pl<R, N, DFT, SRC, 1>(a, d, batch, s);
+    return zpass_launch_pl<R, N, DFT, SRC, 0>(a, d, batch, s);
 }
 
 template <typename R, int N>
@@ -1371,15 +1397,15 @@ template <typename R> bool xypass_available(int nx, int ny, int mode)
     if (mode == PSTD_XY_CLUSTER) return nx == 128 || nx == 192 || nx == 256;
     return false;
 }
-template <typename R, int N, bool DFT>
+template <typename R, int N, bool DFT, int PL = 0>
 cudaError_t xycl_launch(const StepArgs<R>& a, const DftArgs<R>& dx, const DftArgs<R>& dy, int batch, cudaStream_t s)
 {
     const size_t sm = pass_smem<R, N>();
-    cudaError_t e = set_smem_once<xycl_kernel<R, N, DFT>>(sm);
+    cudaError_t e = set_smem_once<xycl_kernel<R, N, DFT, PL>>(sm);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(N / kLanes, a.nz, batch);
-    cfg.blockDim = dim3(kLanes * Plan<N>::T);
+    cfg.blockDim = dim3(kLanes * Plan<N, PL>::T);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
@@ -1395,15 +1421,21 @@ cudaError_t xycl_launch(const StepArgs<R>& a, const DftArgs<R>& dx, const DftArg
 #endif
     cfg.attrs = attr;
     cfg.numAttrs = na;
-    return cudaLaunchKernelEx(&cfg, xycl_kernel<R, N, DFT>, a, dx, dy);
+    return cudaLaunchKernelEx(&cfg, xycl_kernel<R, N, DFT, PL>, a, dx, dy);
 }
 
 template <typename R, int N>
 cudaError_t xycl_n(const StepArgs<R>& a, const DftArgs<R>* dx, const DftArgs<R>* dy, int batch, cudaStream_t s)
 {
     if constexpr (xycl_supported<R, N>()) {
-        if (dx && dy) return xycl_launch<R, N, true>(a, *dx, *dy, batch, s);
         const DftArgs<R> none{};
+        if constexpr (alt_plan_built<R, N>()) {
+            if (a.plan[0] && a.plan[1]) {
+                if (dx && dy) return xycl_launch<R, N, true, 1>(a, *dx, *dy, batch, s);
+                return xycl_launch<R, N, false, 1>(a, none, none, batch, s);
+            }
+        }
+        if (dx && dy) return xycl_launch<R, N, true>(a, *dx, *dy, batch, s);
         return xycl_launch<R, N, false>(a, none, none, batch, s);
     } else {
         return cudaErrorInvalidValue;

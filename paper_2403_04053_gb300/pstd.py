@@ -58,6 +58,7 @@ _SIGS = {
     "pstd_step": (c_int, [c_void_p, c_long]),
     "pstd_transform_to_points": (c_int, [c_void_p, c_int, c_int, c_void_p, c_long, c_void_p, c_int]),
     "pstd_cross_section": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_long, c_void_p, c_void_p, c_int]),
+    "pstd_transform_members": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), c_void_p, c_long, c_void_p, c_int]),
     "pstd_cross_section_noalloc": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_long, c_void_p, c_void_p]),
     "pstd_get_field": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
     "pstd_set_field": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_int]),
@@ -81,7 +82,7 @@ _SIGS = {
     "pstd_set_magnetic_field": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_double, c_int, c_int]),
     "pstd_set_incidence_spinor": (c_int, [c_void_p, c_int, POINTER(c_double), c_double, c_double, POINTER(c_double)]),
     "pstd_graph_replays": (c_int, [c_void_p, POINTER(c_long)]),
-    "pstd_set_variants": (c_int, [c_void_p, c_int, c_int, c_int]),
+    "pstd_set_variants": (c_int, [c_void_p, c_int, c_int, c_int, c_int]),
     "pstd_autotune": (c_int, [c_void_p, c_long, POINTER(c_int)]),
 }
 
@@ -329,17 +330,19 @@ class Grid:
                 "pstd_transform_adjoint")
         return self.split_phasors(out)
 
-    def set_variants(self, fused_xy: int, y_pass: int = 0, z_pass: int = 0):
+    def set_variants(self, fused_xy: int, y_pass: int = 0, z_pass: int = 0, plans: int = 0):
         """Force the step-kernel variants (pstd_set_variants): fused_xy is XY_SEPARATE, XY_PLANE
-        or XY_CLUSTER; y_pass and z_pass are LINE_PLAIN, LINE_PIPELINED (y only) or LINE_TMA."""
-        self._c(self.lib.pstd_set_variants(self.h, int(fused_xy), int(y_pass), int(z_pass)), "pstd_set_variants")
+        or XY_CLUSTER; y_pass and z_pass are LINE_PLAIN, LINE_PIPELINED (y only) or LINE_TMA;
+        plans has bit a set for the alternative FFT plan along axis a."""
+        self._c(self.lib.pstd_set_variants(self.h, int(fused_xy), int(y_pass), int(z_pass), int(plans)),
+                "pstd_set_variants")
 
     def autotune(self, trial_steps: int = 20):
         """Time the available step-kernel variants and keep the fastest (pstd_autotune);
-        returns {"fused_xy": XY_*, "y_pass": LINE_*, "z_pass": LINE_*}."""
-        out = (c_int * 3)()
+        returns {"fused_xy": XY_*, "y_pass": LINE_*, "z_pass": LINE_*, "plans": bits}."""
+        out = (c_int * 4)()
         self._c(self.lib.pstd_autotune(self.h, int(trial_steps), out), "pstd_autotune")
-        return {"fused_xy": int(out[0]), "y_pass": int(out[1]), "z_pass": int(out[2])}
+        return {"fused_xy": int(out[0]), "y_pass": int(out[1]), "z_pass": int(out[2]), "plans": int(out[3])}
 
     def graph_replays(self) -> int:
         n = c_long()
@@ -391,6 +394,25 @@ class Grid:
         self._c(self.lib.pstd_transform_to_points(self.h, b, f, pts.ctypes.data_as(c_void_p), len(pts),
                                                   res.ctypes.data_as(c_void_p), MEM_HOST), "pstd_transform_to_points")
         return res
+
+    def transform_members(self, members, freqs, xyz):
+        """Psi of several members at the same points (pstd_transform_members): an array (or a
+        CUDA tensor, for device points) of shape (len(members), M)."""
+        n = len(members)
+        mb = (c_int * n)(*[int(b) for b in members])
+        fq = (c_int * n)(*[int(f) for f in freqs])
+        if _is_cuda_tensor(xyz):
+            import torch
+            M = xyz.shape[0]
+            out = torch.empty((n, M), dtype=torch.complex128, device=xyz.device)
+            self._c(self.lib.pstd_transform_members(self.h, n, mb, fq, c_void_p(xyz.data_ptr()), M, c_void_p(out.data_ptr()),
+                                                    MEM_DEVICE), "pstd_transform_members")
+            return out
+        pts = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        out = np.empty((n, len(pts)), dtype=np.complex128)
+        self._c(self.lib.pstd_transform_members(self.h, n, mb, fq, pts.ctypes.data_as(c_void_p), len(pts),
+                                                out.ctypes.data_as(c_void_p), MEM_HOST), "pstd_transform_members")
+        return out
 
     def cross_section(self, b: int, f: int, theta, phi):
         """(dsigma/dOmega, f) at the given directions."""

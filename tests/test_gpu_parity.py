@@ -441,6 +441,56 @@ def test_batched_members_equal_separate_runs():
             assert np.array_equal(g.transform_to_points(b, 0, [[5.0, 5.0, 9.0]]), outs[b][1])
 
 
+@pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-12), (pstd.F32, 1e-5)])
+def test_transform_members_equals_single_member_transforms(prec, tol):
+    # three members, two wavenumbers, two DFT frequencies: the batched call groups members 0 and
+    # 1 (k = 2 pi, not adjacent in the call) and member 2 (k = pi) and must give each row of
+    # the single-member transform
+    spec = ragged_spec()
+    V = random_core_V(spec, 2)
+    incs = [((0.3, -0.5, 0.81), K), ((-0.6, 0.0, 0.8), K), ((0.0, 0.6, 0.8), K / 2)]
+    pts = np.array([[3.0, -2.0, 5.5], [30.0, 10.0, 40.0], [-200.0, 50.0, 120.0], [0.5, 0.2, -9.0]])
+    with pstd.Grid(spec, precision=prec, batch=3) as g:
+        g.set_potential(V)
+        for b, (kh, k) in enumerate(incs):
+            g.set_incidence(b, kh, k, 0.05)
+            g.huygens_dft(b, [0.5 * k * k, 0.45 * k * k], 10, 20)
+        g.step(30)
+        order, freqs = [0, 2, 1, 0], [0, 1, 0, 1]
+        got = g.transform_members(order, freqs, pts)
+        for row, (b, f) in enumerate(zip(order, freqs)):
+            assert rel(got[row], g.transform_to_points(b, f, pts)) < tol
+        import torch
+        dev = g.transform_members(order, freqs, torch.from_numpy(pts).cuda()).cpu().numpy()
+        assert np.array_equal(dev, got)
+
+
+def test_batched_256_cube_shell_transform_against_the_oracle():
+    # the batched configuration at full size (16 incidences, 256^3, FP32): all sixteen members
+    # transformed in one call to seeded points of the shell 0.5 D^2/lambda .. 4 D^2/lambda; the
+    # members with k = 2 pi and k = pi checked at two points against the oracle's literal mode
+    # sum of the GPU's own phasors, and every member against its single-member transform
+    from oracle import ntdf_oracle as no_
+    wl = inputs.batched_workload()
+    spec = wl.spec
+    B = len(wl.incidences)
+    D = (spec.tfsf_hi[0] - spec.taper_cells - (spec.tfsf_lo[0] + spec.taper_cells)) * spec.d[0]
+    pts = inputs.shell_points(64, 0.5 * D * D, 4.0 * D * D, 2408)
+    with pstd.Grid(spec, precision=pstd.F32, batch=B) as g:
+        g.set_potential(wl.V)
+        for b, inc in enumerate(wl.incidences):
+            g.set_incidence(b, inc.khat, inc.k, inc.ramp_time)
+            g.huygens_dft(b, [0.5 * inc.k ** 2], 700, 200)
+        g.step(900)            # the scattered waves have reached the Huygens planes
+        got = g.transform_members(list(range(B)), [0] * B, pts)
+        for b in (0, 5, 9, 15):
+            assert rel(got[b], g.transform_to_points(b, 0, pts)) < 1e-5
+        for b in (3, 12):
+            k = wl.incidences[b].k
+            ref = no_.transform_to_points(spec, k, g.get_phasors(b, 0), pts[[7, 23, 40]])
+            assert rel(got[b][[7, 23, 40]], ref) < 1e-4
+
+
 def test_device_buffers_match_host_buffers():
     import torch
     spec = ragged_spec()
@@ -743,7 +793,16 @@ VARIANTS = [("square-64x64x48", (X.XY_PLANE, L.LINE_PLAIN, L.LINE_PLAIN)),
             ("line256-z", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_TMA)),
             ("line256-z", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN)),
             ("line128-z", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_TMA)),
-            ("line192-z", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_TMA))]
+            ("line192-z", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_TMA)),
+            # the alternative FFT plans (radix 8-8-4 at 256 points, 8-4-4 at 128)
+            ("line256-x", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN, 0b001)),
+            ("line256-y", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN, 0b010)),
+            ("line256-z", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN, 0b100)),
+            ("line128-z", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN, 0b100)),
+            ("square-256x256x12", (X.XY_CLUSTER, L.LINE_PLAIN, L.LINE_PLAIN, 0b011)),
+            ("square-256x256x12", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN, 0b011)),
+            ("square-128x128x16", (X.XY_CLUSTER, L.LINE_PLAIN, L.LINE_PLAIN, 0b011)),
+            ("square-128x128x16", (X.XY_SEPARATE, L.LINE_PLAIN, L.LINE_PLAIN, 0b011))]
 
 
 @pytest.mark.parametrize("name,variants", VARIANTS)
@@ -765,6 +824,30 @@ def test_every_variant_matches_oracle(name, variants):
         assert rel(g.get_field(0), sim.cur) < 2e-6
 
 
+@pytest.mark.parametrize("name,variants", [("square-256x256x12", (pstd.XY_CLUSTER, 0, 0, 0b011)),
+                                           ("square-256x256x12", (pstd.XY_SEPARATE, 0, 0, 0b011)),
+                                           ("square-192x192x12", (pstd.XY_SEPARATE, 0, 0, 0))])
+@pytest.mark.parametrize("prec", [pstd.F32])
+def test_windowed_run_of_each_variant(name, variants, prec):
+    # the DFT-window forms of the alternative-plan passes (cluster and separate) and of the
+    # separate passes on 192-point lines
+    spec, steps, win = RUN_SPECS[name]("exact")
+    V = random_core_V(spec, 1)
+    khat = (0.3, -0.5, 0.81)
+    sim = po.Simulation(spec, V, khat, K, 0.05, window=win, omegas=[E0])
+    sim.step(steps)
+    with pstd.Grid(spec, precision=prec) as g:
+        g.set_variants(*variants)
+        g.set_potential(V)
+        g.set_incidence(0, khat, K, 0.05)
+        g.huygens_dft(0, [E0], *win)
+        g.step(steps)
+        assert rel(g.get_field(0), sim.cur) < 2e-5
+        got = g.get_phasors(0, 0)
+    for (gp, gd), (rp, rd) in zip(got, sim.scaled_phasors(0)):
+        assert rel(gp, rp) < 2e-4 and rel(gd, rd) < 2e-4
+
+
 def test_autotune_keeps_the_state_and_picks_available_variants():
     spec = ONE_STEP_SPECS["square-64x64x48"]("exact")
     V = random_core_V(spec, 3)
@@ -778,7 +861,8 @@ def test_autotune_keeps_the_state_and_picks_available_variants():
         assert chosen["fused_xy"] in (pstd.XY_SEPARATE, pstd.XY_PLANE)
         assert g.get_step() == n and np.array_equal(g.get_field(0), before)
         for bad in ((pstd.XY_SEPARATE, pstd.LINE_PIPELINED, 0), (pstd.XY_CLUSTER, 0, 0), (3, 0, 0),
-                    (pstd.XY_SEPARATE, pstd.LINE_TMA, 0), (pstd.XY_SEPARATE, 0, pstd.LINE_PIPELINED)):
+                    (pstd.XY_SEPARATE, pstd.LINE_TMA, 0), (pstd.XY_SEPARATE, 0, pstd.LINE_PIPELINED),
+                    (pstd.XY_SEPARATE, 0, 0, 0b001)):
             with pytest.raises(pstd.PstdError) as e:
                 g.set_variants(*bad)
             assert e.value.code == "EINVAL"
