@@ -165,6 +165,59 @@ def oracle_error(state, psi, ds, fa):
             "targets": {"psi": 2e-4, "cross_sections": 1e-3}}
 
 
+LEG_SAMPLES = os.path.join(ROOT, "tests", "golden", "leg_samples_fp64_oracle.npz")
+
+
+def leg_one_step_error(kind, g, wl):
+    """One step of a leg's grid, in the leg's launch configuration, from the seeded random states
+    for which the FP64 oracle's results at sampled nodes are stored (tests/golden, written by
+    make_leg_samples.py, which runs only the oracle); the relative L2 error over those nodes.
+    Runs outside the timed regions; it overwrites the grid's state."""
+    from paper_2403_04053_gb300 import inputs
+    try:
+        gd = np.load(LEG_SAMPLES)
+    except OSError:
+        return None
+    shape = wl.spec.shape
+
+    def at(field, nodes):
+        return np.array([field[k, j, i] for i, j, k in nodes])
+
+    errs = {}
+    if kind == "batched":
+        nodes = gd["batched_nodes"]
+        for b, (s0, s1) in zip((3, 12), ((60, 61), (62, 63))):
+            if b >= g.batch:
+                continue
+            g.set_field(b, inputs.random_field_c64(shape, s0), inputs.random_field_c64(shape, s1), 200)
+        g.step(1)
+        for b in (3, 12):
+            if b < g.batch:
+                ref = gd[f"batched_ref_{b}"]
+                errs[f"member_{b}_rel_l2"] = float(np.linalg.norm(at(g.get_field(b), nodes) - ref) / np.linalg.norm(ref))
+        errs["sample"] = "one step from seeded random states at n = 200, 64 nodes off the absorbing layers"
+    elif kind == "spinor":
+        nodes = gd["spinor_nodes"]
+        for b in range(4):
+            g.set_field(b, inputs.random_field_c64(shape, 40 + b), inputs.random_field_c64(shape, 50 + b), 300)
+        g.step(1)
+        got = np.stack([np.stack([at(g.get_field(2 * p + s), nodes) for s in range(2)], axis=1) for p in range(2)])
+        ref = gd["spinor_ref"]
+        errs["rel_l2"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        errs["sample"] = "one step from seeded random states at n = 300, both spinors, 56 nodes (corners, random, B's support)"
+    elif kind == "aux":
+        flat = gd["aux_nodes"]
+        prev = inputs.random_field(shape, 5).astype(np.complex64)
+        cur = inputs.random_field(shape, 6).astype(np.complex64)
+        g.set_field(0, prev, cur, 17)
+        g.step(1)
+        ref = gd["aux_ref"]
+        errs["rel_l2"] = float(np.linalg.norm(g.get_field(0).ravel()[flat] - ref) / np.linalg.norm(ref))
+        errs["sample"] = "one step from seeded random states at n = 17, 4096 seeded nodes"
+    errs["target"] = 2e-6
+    return errs
+
+
 # ----------------------------------------------------------------------------------
 # roofline of the leapfrog step
 # ----------------------------------------------------------------------------------
@@ -404,12 +457,13 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80, shell_points=1_000_000):
+def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80, shell_points=1_000_000, force=None):
     """Cell-updates/s of the batched 256^3 x 16 configuration over 80 steps (the last half in
     every member's DFT window), with the step variants chosen by the library's autotuner, the
     HBM roofline of the step, and the surface transform of every member to `shell_points`
     seeded points between 0.5 D^2/lambda and 4 D^2/lambda (one pstd_transform_members call).
-    `members` < 16 keeps only the first members (a smaller case of the same kernels)."""
+    `members` < 16 keeps only the first members (a smaller case of the same kernels); `force`
+    (fused_xy, y_pass, z_pass, plans) sets the step variants instead of the autotuner."""
     import torch
     wl = inputs.batched_workload()
     if members:
@@ -427,7 +481,11 @@ def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80, shell
         wins.append(wlen)
         g.huygens_dft(b, [spec.hbar * inc.k ** 2 / (2 * spec.mass)], nsteps - wlen, wlen)
     ncell = int(np.prod(spec.n))
-    variants = g.autotune(6)
+    if force:
+        g.set_variants(*force)
+        variants = dict(zip(("fused_xy", "y_pass", "z_pass", "plans"), force), forced=True)
+    else:
+        variants = g.autotune(6)
     times = []
     for rep in range(3):   # the first repetition is a warm-up
         g.reset()
@@ -462,6 +520,7 @@ def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80, shell
                  "points_per_s": shell_points * B / t_tr, "pairs_per_s": shell_points * B * cells / t_tr,
                  "geometry": f"radius uniform in [0.5, 4] D^2/lambda, D = {D}, lambda = 1; direction uniform (seed 2408)",
                  "finite": bool(torch.isfinite(psi).all())}
+    err = leg_one_step_error("batched", g, wl) if B == 16 else None
     g.close()
     traffic = {k: v * B / 4 for k, v in BATCHED_TRAFFIC.items()}   # captured at 4 members
     return {"workload": f"batched-256^3: {B} incidences (8 Fibonacci directions x k in {{2pi, pi}}) on one "
@@ -470,7 +529,7 @@ def batched_leg(pstd, inputs, stream, dev, flush, members=None, nsteps=80, shell
             "value": B * ncell * nsteps / t, "unit": "cell-updates/s", "ms_per_step": t / nsteps * 1e3,
             "state_bytes": 2 * B * ncell * 8,
             "kernels_us": {n: round(v[1] / max(1, v[0]) * 1e3, 1) for n, v in ks.items() if v[0]},
-            "variants": variants, "shell_transform": shell,
+            "variants": variants, "shell_transform": shell, "err_vs_fp64_oracle": err,
             "roofline": step_roofline(ks, ncell, B, nsteps, t, traffic)}
 
 
@@ -520,6 +579,7 @@ def spinor_leg(pstd, inputs, stream, dev, flush, nsteps=80):
     th, ph = torch.from_numpy(wl.far_theta).to(dev), torch.from_numpy(wl.far_phi).to(dev)
     t_tr = sum(timed(lambda: g.transform_to_points(b, 0, pts))[0] for b in range(B))
     t_ff = sum(timed(lambda: g.cross_section(b, 0, th, ph))[0] for b in range(B))
+    err = leg_one_step_error("spinor", g, wl)
     g.close()
     return {"workload": f"spinor-384^3: gamma sigma . B of a point dipole (cut off inside r = 1 and outside r = 12), "
                         f"unpolarised incidence as 2 spinors = {B} members, FP32, {nsteps} steps "
@@ -529,6 +589,7 @@ def spinor_leg(pstd, inputs, stream, dev, flush, nsteps=80):
             "kernels_us": {n: round(v[1] / max(1, v[0]) * 1e3, 1) for n, v in ks.items() if v[0]},
             "fresnel_transform_ms": round(t_tr * 1e3, 2), "fresnel_points_per_member": len(wl.fresnel_points),
             "far_field_ms": round(t_ff * 1e3, 2), "far_field_directions": len(wl.far_theta),
+            "err_vs_fp64_oracle": err,
             "roofline": step_roofline(ks, ncell, B, nsteps, t, {})}
 
 
@@ -547,6 +608,7 @@ def aux_leg(pstd, inputs, stream, dev, flush, nsteps=300):
     prof = np.exp(-x * x / (4 * sigma * sigma) + 1j * inc.k * x)
     ncell = int(np.prod(spec.n))
     out = {}
+    err_aux = None
     for kind in ("cw", "packet", "aux"):
         g = pstd.Grid(spec, precision=pstd.F32, stream=stream.cuda_stream)
         g.set_potential(torch.from_numpy(wl.V).to(dev))
@@ -574,6 +636,8 @@ def aux_leg(pstd, inputs, stream, dev, flush, nsteps=300):
         g.step(nsteps)
         n_aux, ms_aux = g.kernel_stats("aux")
         g.set_timing(False)
+        if kind == "aux":
+            err_aux = leg_one_step_error("aux", g, wl)
         g.close()
         out[kind] = {"value": ncell * nsteps / t, "ms_per_step": t / nsteps * 1e3}
         if kind == "aux":
@@ -583,6 +647,7 @@ def aux_leg(pstd, inputs, stream, dev, flush, nsteps=300):
                         f"auxiliary axis ({n1} points, dd = {dd}, Gaussian profile sigma = {sigma}), the same packet "
                         f"in closed form, and the CW wave",
             "unit": "cell-updates/s", "aux": out["aux"], "packet": out["packet"], "cw": out["cw"],
+            "err_vs_fp64_oracle": err_aux,
             "aux_overhead": round(out["aux"]["ms_per_step"] / out["cw"]["ms_per_step"] - 1.0, 4),
             "packet_overhead": round(out["packet"]["ms_per_step"] / out["cw"]["ms_per_step"] - 1.0, 4)}
 
@@ -625,6 +690,20 @@ def adjoint_leg(pstd, inputs, stream, dev):
         torch.cuda.synchronize()
         times.append((ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])))
     g.close()
+    # the same gradient in FP64 (the FP64 path is itself checked against the oracle's discrete
+    # adjoint at 48^3 and against central differences at 32 voxels of this workload)
+    g64 = pstd.Grid(wl.spec, precision=pstd.F64, stream=stream.cuda_stream)
+    g64.set_incidence(0, inc.khat, inc.k, inc.ramp_time)
+    g64.huygens_dft(0, [w0], wl.window_first, wl.window_len)
+    g64.set_potential(V)
+    g64.reset()
+    g64.step(wl.nsteps)
+    psi64 = g64.transform_to_points(0, 0, pts)
+    mag64 = psi64.abs()
+    g64pts = 2 * (mag64 - target) * psi64 / mag64
+    grad64 = g64.adjoint_gradient(wl.nsteps, g64.transform_adjoint(0, 0, pts, g64pts), lo, hi)
+    g64.close()
+    grad_err = float(torch.linalg.norm(grad.double() - grad64) / torch.linalg.norm(grad64))
     fwd = statistics.median(t[0] for t in times[1:])
     adj = statistics.median(t[1] for t in times[1:])
     return {"workload": "adjoint-128^3: V on the central 48^3 block (seeded smoothed noise), 2000 steps, "
@@ -632,7 +711,10 @@ def adjoint_leg(pstd, inputs, stream, dev):
             "forward_ms": round(fwd, 3), "adjoint_ms": round(adj, 3), "adjoint_over_forward": round(adj / fwd, 3),
             "checkpoint_interval": K, "checkpoints": "recorded by the forward run", "grad_box": [48, 48, 48],
             "loss": float(loss),
-            "grad_max_abs": float(grad.abs().max())}
+            "grad_max_abs": float(grad.abs().max()),
+            "err_fp32_vs_fp64_gradient": grad_err,
+            "oracle_checks": "FP64 adjoint vs the oracle's discrete adjoint at 48^3 (1e-9) and vs central differences "
+                             "at 32 voxels of this workload (1e-6 of max |grad|), tests/test_gpu_adjoint.py"}
 
 
 # ----------------------------------------------------------------------------------
@@ -766,6 +848,8 @@ def main():
     p.add_argument("--batched-steps", type=int, default=80)
     p.add_argument("--shell-points", type=int, default=1_000_000,
                    help="observation points of the batched leg's shell transform (0 skips it)")
+    p.add_argument("--batched-variants", default="",
+                   help="fused_xy,y_pass,z_pass,plans for the batched leg instead of the autotuner (profiling)")
     args = p.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -774,8 +858,10 @@ def main():
         from paper_2403_04053_gb300 import inputs, pstd
         dev = torch.device("cuda", 0)
         flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        force = tuple(int(v) for v in args.batched_variants.split(",")) if args.batched_variants else None
         print(json.dumps(batched_leg(pstd, inputs, torch.cuda.current_stream(), dev, flush,
-                                     args.batched_members or None, args.batched_steps, args.shell_points)), flush=True)
+                                     args.batched_members or None, args.batched_steps, args.shell_points, force)),
+              flush=True)
     elif args.aux_only:
         import torch
         from paper_2403_04053_gb300 import inputs, pstd

@@ -190,13 +190,22 @@ pstd_status pstd_step(pstd_grid* g, long nsteps);
 pstd_status pstd_transform_to_points(pstd_grid* g, int b, int f, const double* xyz, long M, void* out_psi, int mem);
 
 /* The same transform for several members at once (Eq. Psi for each): out_psi[i * M + p] is
- * Psi of member members[i] at its DFT frequency freqs[i] at point p.  Members whose
- * wavenumbers agree are transformed together, up to four in one launch, every point-cell
- * Green's weight and quadrature phase serving all of them (the batched incidences of one
- * potential).  members, freqs: count host ints; xyz (M x 3 doubles) and out_psi (count * M
- * complex128) in `mem`.  ESTATE if any member's window has not completed. */
+ * Psi of member members[i] at its DFT frequency freqs[i] (and that frequency's wavenumber) at
+ * point p.  Up to 16 (member, frequency) pairs go into one launch over their records side by
+ * side: the batched incidences of one potential share the surface geometry and the points.
+ * members, freqs: count host ints; xyz (M x 3 doubles) and out_psi (count * M complex128) in
+ * `mem`.  ESTATE if any member's window has not completed.  The records of a launch take
+ * count * ncells * 2 G^2 working-precision values of device memory (2 GB at 256^3 x 16). */
 pstd_status pstd_transform_members(pstd_grid* g, int count, const int* members, const int* freqs, const double* xyz, long M,
                                    void* out_psi, int mem);
+
+/* Gauss-Legendre nodes per cell edge of the surface transform's cell quadrature (and of its
+ * adjoint): 4, 6 or 8; 0 restores the default (6 for PSTD_F32, 8 for PSTD_F64).  Each cell
+ * integral of the trigonometric interpolant times the linearised Green's phase is a G x G sum;
+ * G = 4 takes about half the work of G = 6, at a larger error on interpolant modes near the
+ * plane's Nyquist limit.  The far field (pstd_cross_section) is exact and does not depend on it.
+ * Drops the grid's transform set-up when the order changes; synchronises. */
+pstd_status pstd_set_transform_order(pstd_grid* g, int G);
 
 /* Far-field amplitude f(theta, phi) = lim r e^{-ikr} Psi(r rhat) (the r -> infinity limit of
  * the same per-cell integrals) and dsigma/dOmega = |f|^2 at M directions.  out_dsdo: M

@@ -303,6 +303,7 @@ template <typename R, int G> cudaError_t transform_adjoint_g(const AdjointTransf
 template <typename R> cudaError_t launch_transform_adjoint(const AdjointTransformArgs<R>& a, int G, int splits, cudaStream_t s)
 {
     switch (G) {
+    case 4: return transform_adjoint_g<R, 4>(a, splits, s);
     case 6: return transform_adjoint_g<R, 6>(a, splits, s);
     case 8: return transform_adjoint_g<R, 8>(a, splits, s);
     default: return cudaErrorInvalidValue;

@@ -163,6 +163,7 @@ struct pstd_grid {
     int* flag = nullptr;
     // transform
     int G = 8;
+    int G_order = 0;                        // quadrature nodes a cell edge chosen by the caller (0: default)
     std::vector<double> gl_x, gl_w;
     double* gl_w_dev = nullptr;
     FaceGeom faces[6];
@@ -208,8 +209,6 @@ struct pstd_grid {
     void* rec = nullptr;
     void* rec_group = nullptr;              // records of a member group ([member][cell][2 G G])
     size_t rec_group_cap = 0;
-    double2* group_out = nullptr;           // a group's transform output when its members are not consecutive
-    size_t group_out_cap = 0;
     int rec_member = -1, rec_freq = -1;
     long long rec_version = -1;
     void* Fdft[6][2] = {};                  // per face: DFT matrices along b (Nb x Nb) and c (Nc x Nc)
@@ -969,7 +968,7 @@ pstd_status setup_transform(pstd_grid* g)
 {
     if (g->MbT[0]) return PSTD_OK;
     const pstd_grid_desc& d = g->desc;
-    g->G = g->prec == PSTD_F64 ? 8 : 6;
+    g->G = g->G_order ? g->G_order : (g->prec == PSTD_F64 ? 8 : 6);
     gauss_legendre(g->G, g->gl_x, g->gl_w);
     const int G = g->G;
     CK(g, dalloc(&g->gl_w_dev, sizeof(double) * G));
@@ -1232,9 +1231,8 @@ pstd_status run_transform(pstd_grid* g, int b, int f, const double* pts, long M,
     return PSTD_OK;
 }
 
-// Several members (all with the wavenumber k) at once: their records side by side, one
-// transform launch in which every point-cell pair's Green's weight serves all of them.
-// out: [member][M].
+// Several members at once: their records side by side, one transform launch whose grid's z
+// extent indexes the member (each with its own wavenumber).  out: [member][M].
 template <typename R>
 pstd_status run_transform_group(pstd_grid* g, const int* members, const int* freqs, int count, const double* pts, long M,
                                 double2* out)
@@ -1243,28 +1241,30 @@ pstd_status run_transform_group(pstd_grid* g, const int* members, const int* fre
     if (st != PSTD_OK) return st;
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
     const size_t rec_elems = (size_t)g->ncells * 2 * g->G * g->G;
-    st = ensure(g, &g->rec_group, g->rec_group_cap, (size_t)kTransformMembers * rec_elems * sizeof(C));
+    st = ensure(g, &g->rec_group, g->rec_group_cap, (size_t)count * rec_elems * sizeof(C));
     if (st != PSTD_OK) return st;
+    TransformArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
     for (int i = 0; i < count; ++i) {
         st = prepare_records<R>(g, members[i], freqs[i], static_cast<C*>(g->rec_group) + (size_t)i * rec_elems);
         if (st != PSTD_OK) return st;
+        a.km[i] = wavenumber_of(g, members[i], freqs[i]);
     }
-    TransformArgs<R> a;
-    std::memset(&a, 0, sizeof(a));
     a.rec = static_cast<const C*>(g->rec_group);
     a.members = count;
     a.ncells = g->ncells;
     for (int fi = 0; fi < 6; ++fi) a.face[fi] = g->faces[fi];
     a.pts = pts;
     a.M = M;
-    a.k = wavenumber_of(g, members[0], freqs[0]);
+    a.k = a.km[0];
     for (int q = 0; q < g->G; ++q) a.gl_node[q] = g->gl_x[q];
-    const long long blocks = (M + 127) / 128;
+    const long long per_block = 128 * PSTD_TRANSFORM_PT;
+    const long long blocks = (M + per_block - 1) / per_block * count;
     const int CH = sizeof(R) == 4 ? 32 : 16;
     const long long chunks = (g->ncells + CH - 1) / CH;
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev);
-    const long long target = 4LL * 4 * nsm;
+    const long long target = 4LL * 7 * nsm;
     long long splits = std::max(1LL, std::min(chunks, (target + blocks - 1) / blocks));
     splits = std::min(splits, 4096LL);
     long long cps = ((g->ncells + splits - 1) / splits + CH - 1) / CH * CH;
@@ -1648,7 +1648,7 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     for (void* p : {g->buf[0], g->buf[1], g->V, (void*)g->mem_dev, (void*)g->acc, (void*)g->flag, (void*)g->gl_w_dev,
                     (void*)g->dft_phase, (void*)g->window_first_dev, g->tfac,
                     g->T1, g->OutP, g->OutD, g->Pw, g->rec, (void*)g->partial, (void*)g->pts_dev,
-                    (void*)g->out_dev, (void*)g->dsdo_dev, g->tmaps, g->rec_group, (void*)g->group_out})
+                    (void*)g->out_dev, (void*)g->dsdo_dev, g->tmaps, g->rec_group})
         if (p) cudaFree(p);
     for (int a = 0; a < 3; ++a)
         for (void* p : {g->tw[a], g->kin[a], g->mask[a], g->zeta[a], g->zeta1[a], g->zeta2[a], g->phase[a], g->dw[a]})
@@ -1680,6 +1680,33 @@ pstd_status pstd_destroy_grid(pstd_grid* g)
     for (auto& t : g->timed) { cudaEventDestroy(t.a); cudaEventDestroy(t.b); }
     for (auto e : g->event_pool) cudaEventDestroy(e);
     delete g;
+    return PSTD_OK;
+}
+
+pstd_status pstd_set_transform_order(pstd_grid* g, int G)
+{
+    if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
+    if (G != 0 && G != 4 && G != 6 && G != 8) return fail(g, PSTD_EINVAL, "quadrature order must be 0, 4, 6 or 8");
+    DeviceGuard dg(g->dev);
+    const int want = G ? G : (g->prec == PSTD_F64 ? 8 : 6);
+    g->G_order = G;
+    if (!g->MbT[0] || want == g->G) return PSTD_OK;
+    // the interpolation matrices, records and their adjoint buffers depend on G: drop them, and
+    // the next transform sets them up again
+    CK(g, cudaStreamSynchronize(g->stream));
+    for (int f = 0; f < 6; ++f) {
+        for (void** p : {&g->MbT[f], &g->Mc[f], &g->MbTH[f], &g->McH[f], &g->Fdft[f][0], &g->Fdft[f][1]}) {
+            if (*p) cudaFree(*p);
+            *p = nullptr;
+        }
+    }
+    for (void** p : {(void**)&g->specP, (void**)&g->specD, &g->ct, &g->T1, &g->OutP, &g->OutD, &g->Pw, &g->rec, &g->adj_PA,
+                     &g->adj_rec, (void**)&g->gl_w_dev, &g->rec_group}) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+    g->rec_group_cap = 0;
+    g->rec_member = g->ct_member = -1;
     return PSTD_OK;
 }
 
@@ -2185,33 +2212,12 @@ pstd_status pstd_transform_members(pstd_grid* g, int count, const int* members, 
         pts = g->pts_dev;
         out = g->out_dev;
     }
-    // groups of up to kTransformMembers members with the same wavenumber, in the given order
-    std::vector<char> done(count, 0);
-    for (int i = 0; i < count; ++i) {
-        if (done[i]) continue;
-        const double k = wavenumber_of(g, members[i], freqs[i]);
-        std::vector<int> idx;
-        for (int j = i; j < count && (int)idx.size() < kTransformMembers; ++j)
-            if (!done[j] && wavenumber_of(g, members[j], freqs[j]) == k) idx.push_back(j);
-        std::vector<int> mb, fq;
-        for (int j : idx) { mb.push_back(members[j]); fq.push_back(freqs[j]); done[j] = 1; }
-        // the group's outputs are contiguous only when its members are consecutive in the call;
-        // otherwise they go through the grid's buffer and are copied to their places
-        bool consecutive = true;
-        for (size_t q = 1; q < idx.size(); ++q) consecutive = consecutive && idx[q] == idx[q - 1] + 1;
-        double2* dst = out + (size_t)idx[0] * M;
-        if (!consecutive) {
-            st = ensure(g, &g->group_out, g->group_out_cap, sizeof(double2) * M * idx.size());
-            if (st != PSTD_OK) return st;
-            dst = g->group_out;
-        }
-        st = g->prec == PSTD_F64 ? run_transform_group<double>(g, mb.data(), fq.data(), (int)idx.size(), pts, M, dst)
-                                 : run_transform_group<float>(g, mb.data(), fq.data(), (int)idx.size(), pts, M, dst);
+    // up to kTransformLaunchMembers members a launch, in the given order
+    for (int i0 = 0; i0 < count; i0 += kTransformLaunchMembers) {
+        const int n = std::min(kTransformLaunchMembers, count - i0);
+        st = g->prec == PSTD_F64 ? run_transform_group<double>(g, members + i0, freqs + i0, n, pts, M, out + (size_t)i0 * M)
+                                 : run_transform_group<float>(g, members + i0, freqs + i0, n, pts, M, out + (size_t)i0 * M);
         if (st != PSTD_OK) return st;
-        if (!consecutive)
-            for (size_t q = 0; q < idx.size(); ++q)
-                CK(g, cudaMemcpyAsync(out + (size_t)idx[q] * M, dst + q * M, sizeof(double2) * M, cudaMemcpyDeviceToDevice,
-                                      g->stream));
     }
     if (mem == PSTD_MEM_HOST) return copy_out(g, out_psi, g->out_dev, sizeof(double2) * M * count, PSTD_MEM_HOST);
     return PSTD_OK;

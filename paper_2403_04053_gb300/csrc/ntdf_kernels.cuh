@@ -108,9 +108,9 @@ __device__ __forceinline__ void node_sum(const C* __restrict__ rec, const declty
     id_out = cadd(id_out, cadd(ida[0], ida[1]));
 }
 
-// MB: records of up to MB members (a.members of them, sharing the wavenumber) are summed with
-// the same per-pair Green's weight, phase factors and node trigonometry; PT points a thread.
-template <typename R, int G, int PT = kTransformPT, int MB = 1>
+// blockIdx.z selects the member when several are transformed in one launch (a.members > 0:
+// records [member][cell], wavenumbers a.km, partial sums [split][member][M]); PT points a thread.
+template <typename R, int G, int PT = kTransformPT>
 __global__ void __launch_bounds__(kTransformThreads) transform_kernel(const __grid_constant__ TransformArgs<R> a)
 {
     using C = typename TransformArgs<R>::C;
@@ -118,10 +118,11 @@ __global__ void __launch_bounds__(kTransformThreads) transform_kernel(const __gr
     constexpr int REC = 2 * G * G;
     constexpr int CH = sizeof(R) == 4 ? 32 : 16;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C* srec = reinterpret_cast<C*>(smraw);      // [member][cell of the chunk][REC]
-    C* scen = srec + MB * CH * REC;             // per-cell centre offsets of the chunk
-    const int nmem = MB == 1 ? 1 : a.members;
-    const double k = a.k;
+    C* srec = reinterpret_cast<C*>(smraw);
+    C* scen = srec + CH * REC;   // per-cell centre offsets of the chunk
+    const int member = blockIdx.z;
+    const C* __restrict__ rec = a.rec + (size_t)member * a.ncells * REC;
+    const double k = a.members > 0 ? a.km[member] : a.k;
 
     long long pidx[PT];
     bool valid[PT];
@@ -133,11 +134,9 @@ __global__ void __launch_bounds__(kTransformThreads) transform_kernel(const __gr
         const long long p = valid[i] ? pidx[i] : 0;
         px[i] = a.pts[3 * p + 0]; py[i] = a.pts[3 * p + 1]; pz[i] = a.pts[3 * p + 2];
     }
-    double accx[PT][MB], accy[PT][MB];
+    double accx[PT], accy[PT];
 #pragma unroll
-    for (int i = 0; i < PT; ++i)
-#pragma unroll
-        for (int m = 0; m < MB; ++m) { accx[i][m] = 0.0; accy[i][m] = 0.0; }
+    for (int i = 0; i < PT; ++i) { accx[i] = 0.0; accy[i] = 0.0; }
     R node[H];
 #pragma unroll
     for (int g = 0; g < H; ++g) node[g] = R(a.gl_node[g]);
@@ -173,18 +172,14 @@ __global__ void __launch_bounds__(kTransformThreads) transform_kernel(const __gr
         }
         const R kr = R(k);
         const R pref = R(-F.sigma / (4.0 * 3.14159265358979323846));
-        C fsum[PT][MB];
+        C fsum[PT];
 #pragma unroll
-        for (int i = 0; i < PT; ++i)
-#pragma unroll
-            for (int m = 0; m < MB; ++m) fsum[i][m] = mk<C>(R(0), R(0));
+        for (int i = 0; i < PT; ++i) fsum[i] = mk<C>(R(0), R(0));
 
         for (long long cc0 = f_begin; cc0 < f_end; cc0 += CH) {
             const int nch = (int)min((long long)CH, f_end - cc0);
             __syncthreads();
-            for (int m = 0; m < nmem; ++m)
-                for (int e = threadIdx.x; e < nch * REC; e += kTransformThreads)
-                    srec[m * CH * REC + e] = a.rec[((long long)m * a.ncells + cc0) * REC + e];
+            for (int e = threadIdx.x; e < nch * REC; e += kTransformThreads) srec[e] = rec[cc0 * REC + e];
             if (threadIdx.x < nch) {
                 // cell centre minus face centre, once per cell of the chunk (double precision
                 // and the index division stay out of the per-point loop)
@@ -199,9 +194,7 @@ __global__ void __launch_bounds__(kTransformThreads) transform_kernel(const __gr
                 const C* P = srec + ci * REC;
 #pragma unroll
                 for (int i = 0; i < PT; ++i) {
-                    C ip[MB], id[MB];
-#pragma unroll
-                    for (int m = 0; m < MB; ++m) { ip[m] = mk<C>(R(0), R(0)); id[m] = mk<C>(R(0), R(0)); }
+                    C ip = mk<C>(R(0), R(0)), id = mk<C>(R(0), R(0));
                     C w;               // e^{ikR}/R
                     R ha, cfr;         // bracket = Id + (cfr + i k) ha Ip
                     {
@@ -223,63 +216,44 @@ __global__ void __launch_bounds__(kTransformThreads) transform_kernel(const __gr
                             sincos_small<R>(bb * node[g], &sb[g], &cb[g]);
                             sincos_small<R>(bc * node[g], &sc[g], &cc[g]);
                         }
-#pragma unroll
-                        for (int m = 0; m < MB; ++m)
-                            if (m < nmem) node_sum<C, H>(P + m * CH * REC, cb, sb, cc, sc, ip[m], id[m]);
+                        node_sum<C, H>(P, cb, sb, cc, sc, ip, id);
                         ha = ra * Rinv;
                         cfr = -Rinv;
                     }
                     const C cf = mk<C>(cfr * ha, kr * ha);
-#pragma unroll
-                    for (int m = 0; m < MB; ++m) {
-                        const C br = cadd(id[m], cmul(cf, ip[m]));
-                        fsum[i][m] = cadd(fsum[i][m], cmul(w, br));
-                    }
+                    const C br = cadd(id, cmul(cf, ip));
+                    fsum[i] = cadd(fsum[i], cmul(w, br));
                 }
             }
             // flush the chunk's partial sums into double accumulators
 #pragma unroll
-            for (int i = 0; i < PT; ++i)
-#pragma unroll
-                for (int m = 0; m < MB; ++m) {
-                    accx[i][m] += double(pref * fsum[i][m].x);
-                    accy[i][m] += double(pref * fsum[i][m].y);
-                    fsum[i][m] = mk<C>(R(0), R(0));
-                }
+            for (int i = 0; i < PT; ++i) {
+                accx[i] += double(pref * fsum[i].x);
+                accy[i] += double(pref * fsum[i].y);
+                fsum[i] = mk<C>(R(0), R(0));
+            }
         }
     }
 #pragma unroll
     for (int i = 0; i < PT; ++i)
-#pragma unroll
-        for (int m = 0; m < MB; ++m)
-            if (valid[i] && m < nmem)
-                a.partial[((long long)blockIdx.y * nmem + m) * a.M + pidx[i]] = make_double2(accx[i][m], accy[i][m]);
-}
-
-template <typename R, int G, int PT, int MB> cudaError_t transform_gm(const TransformArgs<R>& a, int splits, cudaStream_t s)
-{
-    using C = typename TransformArgs<R>::C;
-    constexpr int CH = sizeof(R) == 4 ? 32 : 16;
-    const size_t sm = sizeof(C) * CH * (MB * 2 * G * G + 1);
-    if (sm > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(transform_kernel<R, G, PT, MB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)sm);
-        if (e != cudaSuccess) return e;
-    }
-    dim3 grid((unsigned)((a.M + kTransformThreads * PT - 1) / (kTransformThreads * PT)), splits);
-    transform_kernel<R, G, PT, MB><<<grid, kTransformThreads, sm, s>>>(a);
-    return cudaGetLastError();
+        if (valid[i]) a.partial[((long long)blockIdx.y * gridDim.z + member) * a.M + pidx[i]] = make_double2(accx[i], accy[i]);
 }
 
 template <typename R, int G> cudaError_t transform_g(const TransformArgs<R>& a, int splits, cudaStream_t s)
 {
-    if (a.members > 1) return transform_gm<R, G, 1, kTransformMembers>(a, splits, s);
-    return transform_gm<R, G, kTransformPT, 1>(a, splits, s);
+    using C = typename TransformArgs<R>::C;
+    constexpr int CH = sizeof(R) == 4 ? 32 : 16;
+    const size_t sm = sizeof(C) * CH * (2 * G * G + 1);
+    dim3 grid((unsigned)((a.M + kTransformThreads * kTransformPT - 1) / (kTransformThreads * kTransformPT)), splits,
+              (unsigned)(a.members > 0 ? a.members : 1));
+    transform_kernel<R, G><<<grid, kTransformThreads, sm, s>>>(a);
+    return cudaGetLastError();
 }
 
 template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, int G, int splits, cudaStream_t s)
 {
     switch (G) {
+    case 4: return transform_g<R, 4>(a, splits, s);
     case 6: return transform_g<R, 6>(a, splits, s);
     case 8: return transform_g<R, 8>(a, splits, s);
     default: return cudaErrorInvalidValue;

@@ -185,10 +185,14 @@ template <typename R> cudaError_t launch_spectrum_pack(const typename std::condi
                                                        typename std::conditional<sizeof(R) == 4, float2, double2>::type* ct,
                                                        cudaStream_t s);
 
+// members per launch of the multi-member surface transform (bounds its record buffer)
+constexpr int kTransformLaunchMembers = 16;
+
 template <typename R> struct TransformArgs {
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
     const C* rec;             // per cell: G*G psi node values then G*G dpsi node values (weights folded in)
-    int members;              // members transformed together (records [member][cell], all with wavenumber k)
+    int members;              // > 0: members in one launch (records [member][cell], wavenumbers km)
+    double km[kTransformLaunchMembers];
     long long ncells;
     FaceGeom face[6];
     const double* pts;        // M x 3 points
@@ -205,9 +209,7 @@ template <typename R> struct TransformArgs {
 #define PSTD_TRANSFORM_PT 2
 #endif
 template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, int G, int splits, cudaStream_t s);
-// members per launch of the member-batched transform (one Green's weight per point-cell pair
-// serves every member's record)
-constexpr int kTransformMembers = 4;
+
 
 // ---------------------------------------------------------------------------------
 // discrete adjoint (see adjoint_kernels.cuh)

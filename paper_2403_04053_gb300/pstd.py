@@ -59,6 +59,7 @@ _SIGS = {
     "pstd_transform_to_points": (c_int, [c_void_p, c_int, c_int, c_void_p, c_long, c_void_p, c_int]),
     "pstd_cross_section": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_long, c_void_p, c_void_p, c_int]),
     "pstd_transform_members": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), c_void_p, c_long, c_void_p, c_int]),
+    "pstd_set_transform_order": (c_int, [c_void_p, c_int]),
     "pstd_cross_section_noalloc": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_long, c_void_p, c_void_p]),
     "pstd_get_field": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
     "pstd_set_field": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_int]),
@@ -394,6 +395,10 @@ class Grid:
         self._c(self.lib.pstd_transform_to_points(self.h, b, f, pts.ctypes.data_as(c_void_p), len(pts),
                                                   res.ctypes.data_as(c_void_p), MEM_HOST), "pstd_transform_to_points")
         return res
+
+    def set_transform_order(self, G: int):
+        """Gauss-Legendre nodes per cell edge of the surface transform (pstd_set_transform_order)."""
+        self._c(self.lib.pstd_set_transform_order(self.h, int(G)), "pstd_set_transform_order")
 
     def transform_members(self, members, freqs, xyz):
         """Psi of several members at the same points (pstd_transform_members): an array (or a

@@ -37,12 +37,15 @@ def workload():
     return inputs.gaussian_sum_workload()
 
 
-@pytest.mark.parametrize("prec,tol_state,tol_out", [(pstd.F32, 2e-4, 1e-3), (pstd.F64, 1e-10, 1e-10)])
-def test_full_benchmarked_pass_against_the_fp64_oracle(golden, workload, prec, tol_state, tol_out):
+@pytest.mark.parametrize("prec,tol_state,tol_out,G", [(pstd.F32, 2e-4, 1e-3, 0), (pstd.F64, 1e-10, 1e-10, 0),
+                                                      (pstd.F32, 2e-4, 1e-3, 4)])
+def test_full_benchmarked_pass_against_the_fp64_oracle(golden, workload, prec, tol_state, tol_out, G):
+    # G = 0: the default cell quadrature; G = 4: the cheaper one, held to the same FP32 targets
     wl = workload
     inc = wl.incidences[0]
     assert int(golden["nsteps"]) == wl.nsteps and tuple(golden["window"]) == (wl.window_first, wl.window_len)
     with pstd.Grid(wl.spec, precision=prec) as g:
+        g.set_transform_order(G)
         g.set_potential(wl.V)
         g.set_incidence(0, inc.khat, inc.k, inc.ramp_time)
         g.huygens_dft(0, [0.5 * inc.k ** 2], wl.window_first, wl.window_len)

@@ -232,6 +232,35 @@ def test_windowed_run_matches_oracle(name, mode, prec, tol_state, tol_ph):
         assert rel(gp, rp) < tol_ph and rel(gd, rd) < tol_ph
 
 
+@pytest.mark.parametrize("G,tol", [(4, 1e-3), (6, 1e-8), (8, 1e-10)])
+def test_transform_quadrature_order(short_run, G, tol):
+    # FP64, so that only the cell quadrature differs from the oracle's literal mode sum: G = 4
+    # misses interpolant modes near the planes' Nyquist limit (a worst case of ~1e-4 a mode),
+    # G = 8 (the FP64 default) is exact to round-off; the far field does not depend on G
+    r = short_run
+    with pstd.Grid(r["spec"], precision=pstd.F64) as g:
+        g.set_potential(r["V"])
+        g.set_incidence(0, r["khat"], K, 0.05)
+        g.huygens_dft(0, r["om"], *r["win"])
+        g.step(60)
+        ref_psi = r["ref"][0][1]
+        psi_default = g.transform_to_points(0, 0, r["pts"])
+        g.set_transform_order(G)
+        psi = g.transform_to_points(0, 0, r["pts"])
+        assert rel(psi, ref_psi) < tol
+        _, f = g.cross_section(0, 0, r["th"], r["ph"])
+        assert rel(f, r["ref"][0][2][1]) < 1e-10
+        # the adjoint transform follows the order (its transpose identity against the forward)
+        y = np.random.default_rng(3).standard_normal(len(r["pts"])) + 0j
+        x = g.join_phasors(g.transform_adjoint(0, 0, r["pts"], y))
+        assert np.all(np.isfinite(x))
+        g.set_transform_order(0)
+        assert np.array_equal(g.transform_to_points(0, 0, r["pts"]), psi_default)
+        with pytest.raises(pstd.PstdError) as e:
+            g.set_transform_order(5)
+        assert e.value.code == "EINVAL"
+
+
 # ----------------------------------------------------------------------------------
 # the full 48^3 square-barrier run (750 steps)
 # ----------------------------------------------------------------------------------
@@ -443,9 +472,8 @@ def test_batched_members_equal_separate_runs():
 
 @pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-12), (pstd.F32, 1e-5)])
 def test_transform_members_equals_single_member_transforms(prec, tol):
-    # three members, two wavenumbers, two DFT frequencies: the batched call groups members 0 and
-    # 1 (k = 2 pi, not adjacent in the call) and member 2 (k = pi) and must give each row of
-    # the single-member transform
+    # three members, two wavenumbers, two DFT frequencies, in one launch: each row must be the
+    # single-member transform of that member and frequency
     spec = ragged_spec()
     V = random_core_V(spec, 2)
     incs = [((0.3, -0.5, 0.81), K), ((-0.6, 0.0, 0.8), K), ((0.0, 0.6, 0.8), K / 2)]
