@@ -358,6 +358,12 @@ pstd_status pstd_autotune(pstd_grid* g, long trial_steps, int* out_variants);
  * auxiliary-wave evaluation, the FP64 passes).  Not part of the paper's method; synchronises. */
 pstd_status pstd_measure_fma_peak(int precision, double* tflops);
 
+/* Self-test of failure detection: one CTA waits, with the time-bounded mbarrier wait of the
+ * TMA-fed passes, on a barrier that nothing arrives on, for limit_s seconds (0 < limit_s <= 1).
+ * Returns PSTD_ETIMEOUT when the wait gave up as it must (waited_s: how long it waited), and
+ * leaves the context usable.  Not part of the paper's method; synchronises. */
+pstd_status pstd_selftest_bounded_wait(double limit_s, double* waited_s);
+
 /* Message of the last failure on g (or of the last failed pstd_create_grid when g is NULL). */
 const char* pstd_last_error(const pstd_grid* g);
 

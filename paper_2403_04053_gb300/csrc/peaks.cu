@@ -67,3 +67,47 @@ extern "C" pstd_status pstd_measure_fma_peak(int precision, double* tflops)
     if (!tflops || (precision != PSTD_F32 && precision != PSTD_F64)) return PSTD_EINVAL;
     return precision == PSTD_F32 ? measure<float>(tflops) : measure<double>(tflops);
 }
+
+// ---------------------------------------------------------------------------------------
+// Self-test of the bounded mbarrier wait that the TMA-fed passes use: a barrier on which
+// nothing ever arrives, waited on with a caller-given limit.  The wait must give up after
+// the limit and the kernel return normally, leaving the context usable.
+// ---------------------------------------------------------------------------------------
+#include "step_kernels.cuh"
+
+namespace {
+
+__global__ void wait_probe_kernel(unsigned long long limit_ns, unsigned long long* out)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        pstd::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const unsigned long long t0 = pstd::global_ns();
+    const bool completed = pstd::mbar_wait_bounded(&bar, 0, limit_ns);   // nothing arrives
+    const unsigned long long waited = pstd::global_ns() - t0;
+    if (threadIdx.x == 0) {
+        out[0] = completed ? 1ull : 0ull;
+        out[1] = waited;
+    }
+}
+
+}  // namespace
+
+extern "C" pstd_status pstd_selftest_bounded_wait(double limit_s, double* waited_s)
+{
+    if (!(limit_s > 0.0) || limit_s > 1.0 || !waited_s) return PSTD_EINVAL;
+    unsigned long long* d = nullptr;
+    if (cudaMalloc(&d, 2 * sizeof(unsigned long long)) != cudaSuccess) return PSTD_ENOMEM;
+    unsigned long long h[2] = {2, 0};
+    pstd_status st = PSTD_ECUDA;
+    wait_probe_kernel<<<1, 32>>>((unsigned long long)(limit_s * 1e9), d);
+    if (cudaGetLastError() == cudaSuccess && cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost) == cudaSuccess) {
+        *waited_s = (double)h[1] * 1e-9;
+        st = h[0] == 0 ? PSTD_ETIMEOUT : PSTD_OK;
+    }
+    cudaFree(d);
+    return st;
+}

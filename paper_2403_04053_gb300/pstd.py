@@ -68,6 +68,7 @@ _SIGS = {
     "pstd_get_step": (c_int, [c_void_p, POINTER(c_long)]),
     "pstd_get_device": (c_int, [c_void_p, POINTER(c_int)]),
     "pstd_measure_fma_peak": (c_int, [c_int, POINTER(c_double)]),
+    "pstd_selftest_bounded_wait": (c_int, [c_double, POINTER(c_double)]),
     "pstd_stability_dt_max": (c_int, [POINTER(GridDesc), c_double, POINTER(c_double)]),
     "pstd_set_timing": (c_int, [c_void_p, c_int]),
     "pstd_kernel_stats": (c_int, [c_void_p, c_int, POINTER(c_long), POINTER(c_double)]),
@@ -164,6 +165,14 @@ def measure_fma_peak(precision: int) -> float:
     out = c_double()
     _check(load_library().pstd_measure_fma_peak(int(precision), byref(out)), "pstd_measure_fma_peak")
     return out.value
+
+
+def selftest_bounded_wait(limit_s: float):
+    """(status name, seconds waited) of pstd_selftest_bounded_wait: "ETIMEOUT" when the bounded
+    wait on a barrier that nothing arrives on gave up, as it must."""
+    out = c_double()
+    st = load_library().pstd_selftest_bounded_wait(float(limit_s), byref(out))
+    return STATUS.get(st, str(st)), out.value
 
 
 def stability_dt_max(spec, vmax: float) -> float:

@@ -894,3 +894,26 @@ def test_autotune_keeps_the_state_and_picks_available_variants():
             with pytest.raises(pstd.PstdError) as e:
                 g.set_variants(*bad)
             assert e.value.code == "EINVAL"
+
+
+def test_bounded_wait_gives_up_and_the_context_survives():
+    # the time-bounded mbarrier wait of the TMA-fed passes, on a barrier nothing arrives on
+    status, waited = pstd.selftest_bounded_wait(0.05)
+    assert status == "ETIMEOUT" and 0.05 <= waited < 1.0
+    assert pstd.selftest_bounded_wait(2.0)[0] == "EINVAL"          # limits above a second are refused
+    # the context still runs the step kernels afterwards
+    spec = ONE_STEP_SPECS["line256-z"]("exact")
+    V = random_core_V(spec, 3)
+    prev = inputs.random_field(spec.shape, 5)
+    cur = inputs.random_field(spec.shape, 6)
+    sim = po.Simulation(spec, V, (0.3, -0.5, 0.81), K, 0.05)
+    sim.prev, sim.cur, sim.n = prev.copy(), cur.copy(), 17
+    sim.step(1)
+    with pstd.Grid(spec, precision=pstd.F32) as g:
+        g.set_variants(pstd.XY_SEPARATE, pstd.LINE_PLAIN, pstd.LINE_TMA)
+        g.set_potential(V)
+        g.set_incidence(0, (0.3, -0.5, 0.81), K, 0.05)
+        g.set_field(0, prev.astype(np.complex64), cur.astype(np.complex64), 17)
+        g.step(1)
+        g.synchronize()
+        assert rel(g.get_field(0), sim.cur) < 2e-6
