@@ -215,10 +215,20 @@ template <> struct Plan<384> { static constexpr int T = 32; static constexpr int
 constexpr int kLanes = PSTD_LANES;    // lines per CTA (thread index = j * kLanes + line)
 constexpr int kPitch = kLanes + 1;    // shared-memory row pitch (complex elements)
 
+// Element (pos, lane) of an exchange tile: at pos * PS + lane * LS (the [pos][lane] tile of
+// kLanes lines by default), or, with PS == 0, in row `lane` of N values with the low four bits
+// of pos XORed with the next four.  The swizzled rows serve lines whose 16 threads are
+// consecutive lanes (the x pass at N = 256): a stage writing positions 16 j + r and the next
+// reading positions j + 16 r then touch 16 distinct bank pairs per half-warp.
+template <int N, int PS, int LS> __device__ __forceinline__ int tile_addr(int pos, int lane)
+{
+    if constexpr (PS == 0) return lane * N + (pos ^ ((pos >> 4) & 15));
+    else return pos * PS + lane * LS;
+}
+
 // One Stockham stage.  v holds the thread's E values; on entry they are the stage's
 // inputs when !FROM_SMEM, otherwise the inputs are read from the tile.  On exit the
-// outputs are in v, and also in the tile when TO_SMEM.  Element (pos, lane) of the tile
-// sits at sm[pos * PS + lane * LS] (default: the [pos][lane] tile of kLanes lines).
+// outputs are in v, and also in the tile when TO_SMEM (addressed by tile_addr).
 template <int N, int T, int RAD, int NS, int DIR, bool FROM_SMEM, bool TO_SMEM, int PS = kPitch, int LS = 1,
           typename C, int E>
 __device__ __forceinline__ void stockham_stage(C (&v)[E], C* sm, int lane, int j, const C* __restrict__ tw)
@@ -230,7 +240,7 @@ __device__ __forceinline__ void stockham_stage(C (&v)[E], C* sm, int lane, int j
         for (int t = 0; t < NB; ++t) {
             const int b = j + t * T;
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) v[t * RAD + r] = sm[(b + r * (N / RAD)) * PS + lane * LS];
+            for (int r = 0; r < RAD; ++r) v[t * RAD + r] = sm[tile_addr<N, PS, LS>(b + r * (N / RAD), lane)];
         }
         if constexpr (TO_SMEM) __syncthreads();
     }
@@ -255,7 +265,7 @@ __device__ __forceinline__ void stockham_stage(C (&v)[E], C* sm, int lane, int j
             const int b = j + t * T;
             const int base = (b / NS) * NS * RAD + (b % NS);
 #pragma unroll
-            for (int r = 0; r < RAD; ++r) sm[(base + r * NS) * PS + lane * LS] = v[t * RAD + r];
+            for (int r = 0; r < RAD; ++r) sm[tile_addr<N, PS, LS>(base + r * NS, lane)] = v[t * RAD + r];
         }
         __syncthreads();
     }
@@ -289,7 +299,7 @@ __device__ __forceinline__ void kinetic_line(C (&v)[E], C* sm, int lane, int j, 
     if constexpr (P::S == 1) {
         if constexpr (FIRST_FROM_SMEM) {
 #pragma unroll
-            for (int q = 0; q < E; ++q) v[q] = sm[slot_pos<N, T, R0>(q, j) * PS + lane];
+            for (int q = 0; q < E; ++q) v[q] = sm[tile_addr<N, PS, 1>(slot_pos<N, T, R0>(q, j), lane)];
         }
         stockham_stage<N, T, R0, 1, -1, false, false, PS>(v, sm, lane, j, tw);
 #pragma unroll

@@ -206,10 +206,42 @@ __device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R
 {
     using C = typename StepArgs<R>::C;
     constexpr int T = Plan<N, PL>::T, E = N / T, R0 = Plan<N, PL>::R[0];
-    const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
     const int rows = a.ny * a.nz;
     const int nrows = min(kLanes, rows - row0);
     const long long tile0 = (long long)b * a.ncell + (long long)row0 * N;
+    if constexpr (N == 256 && PL == 0) {
+        // the 16 threads of a line are consecutive lanes: thread j holds positions j + 16 q of
+        // its row, so the row is read and updated straight from global memory (two 128-byte
+        // segments a warp access) and only the transform's exchanges use shared memory, in
+        // swizzled rows (tile_addr with PS = 0)
+        static_assert(T == 16 && R0 == 16, "the swizzle assumes 16 threads of 16 values a line");
+        const int lane = threadIdx.x / T, j = threadIdx.x % T;
+        const bool act = lane < nrows;
+        const C* __restrict__ row = a.cur + tile0 + (long long)lane * N;
+        C* __restrict__ prow = a.prev + tile0 + (long long)lane * N;
+        C v[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) v[q] = act ? row[slot_pos<N, T, R0>(q, j)] : zero_c<R, C>();
+        if (a.pf_l1 && act) prefetch_l1(prow + 16 * j);   // the row's 16 cache lines, one a thread
+        const bool dft = DFT && ((d.member_mask >> b) & 1ull);
+        C part[4];
+        if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
+        kinetic_line<N, false, 0, PL>(v, sm, lane, j, a.tw[0], a.kin[0], R(a.mem[b].eta));
+        __syncthreads();
+        if (dft) dft_finish<R, T>(part, sm, lane, j, d, b, row0 + lane, act);   // plane [z][y]: pixel = row
+        if (!act) return;
+#pragma unroll
+        for (int q0 = 0; q0 < E; q0 += 4) {
+            C pg[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) pg[i] = prow[slot_pos<N, T, R0>(q0 + i, j)];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                prow[slot_pos<N, T, R0>(q0 + i, j)] = mk<C>(pg[i].x + v[q0 + i].y, pg[i].y - v[q0 + i].x);   // p - i w
+        }
+        return;
+    }
+    const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
     // the tile's kLanes * N values, E a thread: every load of a thread in flight before its
     // first shared-memory store
     constexpr int NT = kLanes * T;
