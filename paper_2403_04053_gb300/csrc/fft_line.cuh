@@ -31,6 +31,67 @@ template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk<C>
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 template <typename C> __device__ __forceinline__ C cconjmul(C a, C w) { return mk<C>(a.x * w.x + a.y * w.y, a.y * w.x - a.x * w.y); }
 template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
+// Butterfly sums, differences and scalings of the small DFTs below.  With PSTD_F32X2 those of
+// FP32 values (float2) are single packed two-lane instructions (add/sub/mul .f32x2, round to
+// nearest: each lane rounds exactly as the scalar operation does).  cs32, an FP32 complex of
+// another type, keeps the scalar forms for kernels where they schedule better.
+#ifndef PSTD_F32X2
+#define PSTD_F32X2 1
+#endif
+struct __align__(8) cs32 { float x, y; };
+template <typename C> __device__ __forceinline__ C ldg_c(const C* p) { return __ldg(p); }
+template <> __device__ __forceinline__ cs32 ldg_c<cs32>(const cs32* p)
+{
+    const float2 w = __ldg(reinterpret_cast<const float2*>(p));
+    return cs32{w.x, w.y};
+}
+template <typename C> __device__ __forceinline__ C bfadd(C a, C b) { return cadd(a, b); }
+template <typename C> __device__ __forceinline__ C bfsub(C a, C b) { return csub(a, b); }
+template <typename C> __device__ __forceinline__ C bfscale(C a, decltype(C::x) s) { return cscale(a, s); }
+#if PSTD_F32X2
+__device__ __forceinline__ unsigned long long pk2(float2 a)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ float2 up2(unsigned long long r)
+{
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(r));
+    return d;
+}
+template <> __device__ __forceinline__ float2 bfadd<float2>(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return up2(d);
+}
+template <> __device__ __forceinline__ float2 bfsub<float2>(float2 a, float2 b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(b)));
+    return up2(d);
+}
+template <> __device__ __forceinline__ float2 bfscale<float2>(float2 a, float s)
+{
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pk2(a)), "l"(pk2(make_float2(s, s))));
+    return up2(d);
+}
+#endif
+#ifndef PSTD_F32X2_KIN
+#define PSTD_F32X2_KIN 1
+#endif
+// the spectral multiply of kinetic_line (packed with PSTD_F32X2_KIN: 5% off the 256-point passes)
+template <typename C> __device__ __forceinline__ C kscale(C a, decltype(C::x) s)
+{
+#if PSTD_F32X2_KIN
+    return bfscale(a, s);
+#else
+    return cscale(a, s);
+#endif
+}
 // multiply by -i*DIR... helpers: i*a and -i*a
 template <typename C> __device__ __forceinline__ C mul_i(C a) { return mk<C>(-a.y, a.x); }
 template <typename C> __device__ __forceinline__ C mul_mi(C a) { return mk<C>(a.y, -a.x); }
@@ -43,32 +104,32 @@ template <int DIR, typename C> __device__ __forceinline__ C mul_dir_i(C a) { ret
 template <int DIR, typename C> __device__ __forceinline__ void dft2(C& a, C& b)
 {
     C t = a;
-    a = cadd(t, b);
-    b = csub(t, b);
+    a = bfadd(t, b);
+    b = bfsub(t, b);
 }
 
 template <int DIR, typename C> __device__ __forceinline__ void dft3(C& a, C& b, C& c)
 {
     using R = decltype(C::x);
     const R h = R(0.8660254037844386467637231707529362);   // sin(2 pi / 3)
-    C s = cadd(b, c);
-    C d = csub(b, c);
+    C s = bfadd(b, c);
+    C d = bfsub(b, c);
     C m = mk<C>(a.x - R(0.5) * s.x, a.y - R(0.5) * s.y);
-    a = cadd(a, s);
+    a = bfadd(a, s);
     // DIR i sin(2pi/3) (b - c)
-    C r = cscale(mul_dir_i<DIR>(d), h);
-    b = cadd(m, r);
-    c = csub(m, r);
+    C r = bfscale(mul_dir_i<DIR>(d), h);
+    b = bfadd(m, r);
+    c = bfsub(m, r);
 }
 
 template <int DIR, typename C> __device__ __forceinline__ void dft4(C& a, C& b, C& c, C& d)
 {
-    C t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = csub(b, d);
+    C t0 = bfadd(a, c), t1 = bfsub(a, c), t2 = bfadd(b, d), t3 = bfsub(b, d);
     C r = mul_dir_i<DIR>(t3);
-    a = cadd(t0, t2);
-    c = csub(t0, t2);
-    b = cadd(t1, r);
-    d = csub(t1, r);
+    a = bfadd(t0, t2);
+    c = bfsub(t0, t2);
+    b = bfadd(t1, r);
+    d = bfsub(t1, r);
 }
 
 // twiddle w_R^k for compile-time R, k with sign DIR (cos 2pi k/R + DIR i sin 2pi k/R)
@@ -78,9 +139,9 @@ template <int DIR, typename C> __device__ __forceinline__ C tw_mul8(C a, int k)
     using R = decltype(C::x);
     const R s = R(0.7071067811865475244008443621048490);
     if (k == 0) return a;
-    if (k == 1) return cscale(cadd(a, mul_dir_i<DIR>(a)), s);
+    if (k == 1) return bfscale(bfadd(a, mul_dir_i<DIR>(a)), s);
     if (k == 2) return mul_dir_i<DIR>(a);
-    return cscale(csub(mul_dir_i<DIR>(a), a), s);
+    return bfscale(bfsub(mul_dir_i<DIR>(a), a), s);
 }
 
 template <int DIR, typename C> __device__ __forceinline__ void dft8(C* x)
@@ -93,10 +154,10 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8(C* x)
     o1 = tw_mul8<DIR>(o1, 1);
     o2 = tw_mul8<DIR>(o2, 2);
     o3 = tw_mul8<DIR>(o3, 3);
-    x[0] = cadd(e0, o0); x[4] = csub(e0, o0);
-    x[1] = cadd(e1, o1); x[5] = csub(e1, o1);
-    x[2] = cadd(e2, o2); x[6] = csub(e2, o2);
-    x[3] = cadd(e3, o3); x[7] = csub(e3, o3);
+    x[0] = bfadd(e0, o0); x[4] = bfsub(e0, o0);
+    x[1] = bfadd(e1, o1); x[5] = bfsub(e1, o1);
+    x[2] = bfadd(e2, o2); x[6] = bfsub(e2, o2);
+    x[3] = bfadd(e3, o3); x[7] = bfsub(e3, o3);
 }
 
 template <int DIR, typename C> __device__ __forceinline__ C tw16(C a, int k)
@@ -253,7 +314,7 @@ __device__ __forceinline__ void stockham_stage(C (&v)[E], C* sm, int lane, int j
             constexpr int step = N / (NS * RAD);
 #pragma unroll
             for (int r = 1; r < RAD; ++r) {
-                const C w = __ldg(&tw[r * bm * step]);
+                const C w = ldg_c(&tw[r * bm * step]);
                 x[r] = DIR < 0 ? cmul(x[r], w) : cconjmul(x[r], w);
             }
         }
@@ -303,13 +364,13 @@ __device__ __forceinline__ void kinetic_line(C (&v)[E], C* sm, int lane, int j, 
         }
         stockham_stage<N, T, R0, 1, -1, false, false, PS>(v, sm, lane, j, tw);
 #pragma unroll
-        for (int q = 0; q < E; ++q) v[q] = cscale(v[q], __ldg(&kin[spec_pos<N, T, R0>(q, j)]) * scale);
+        for (int q = 0; q < E; ++q) v[q] = kscale(v[q], __ldg(&kin[spec_pos<N, T, R0>(q, j)]) * scale);
         stockham_stage<N, T, R0, 1, +1, false, false, PS>(v, sm, lane, j, tw);
     } else if constexpr (P::S == 2) {
         stockham_stage<N, T, R0, 1, -1, FIRST_FROM_SMEM, true, PS>(v, sm, lane, j, tw);
         stockham_stage<N, T, R1, R0, -1, true, false, PS>(v, sm, lane, j, tw);
 #pragma unroll
-        for (int q = 0; q < E; ++q) v[q] = cscale(v[q], __ldg(&kin[spec_pos<N, T, R1>(q, j)]) * scale);
+        for (int q = 0; q < E; ++q) v[q] = kscale(v[q], __ldg(&kin[spec_pos<N, T, R1>(q, j)]) * scale);
         __syncthreads();   // every thread has read the tile before it is rewritten
         stockham_stage<N, T, R1, 1, +1, false, true, PS>(v, sm, lane, j, tw);
         stockham_stage<N, T, R0, R1, +1, true, false, PS>(v, sm, lane, j, tw);
@@ -319,7 +380,7 @@ __device__ __forceinline__ void kinetic_line(C (&v)[E], C* sm, int lane, int j, 
         stockham_stage<N, T, R2, R0 * R1, -1, true, true, PS>(v, sm, lane, j, tw);
         stockham_stage<N, T, R3, R0 * R1 * R2, -1, true, false, PS>(v, sm, lane, j, tw);
 #pragma unroll
-        for (int q = 0; q < E; ++q) v[q] = cscale(v[q], __ldg(&kin[spec_pos<N, T, R3>(q, j)]) * scale);
+        for (int q = 0; q < E; ++q) v[q] = kscale(v[q], __ldg(&kin[spec_pos<N, T, R3>(q, j)]) * scale);
         __syncthreads();
         stockham_stage<N, T, R3, 1, +1, false, true, PS>(v, sm, lane, j, tw);
         stockham_stage<N, T, R2, R3, +1, true, true, PS>(v, sm, lane, j, tw);
@@ -330,7 +391,7 @@ __device__ __forceinline__ void kinetic_line(C (&v)[E], C* sm, int lane, int j, 
         stockham_stage<N, T, R1, R0, -1, true, true, PS>(v, sm, lane, j, tw);
         stockham_stage<N, T, R2, R0 * R1, -1, true, false, PS>(v, sm, lane, j, tw);
 #pragma unroll
-        for (int q = 0; q < E; ++q) v[q] = cscale(v[q], __ldg(&kin[spec_pos<N, T, R2>(q, j)]) * scale);
+        for (int q = 0; q < E; ++q) v[q] = kscale(v[q], __ldg(&kin[spec_pos<N, T, R2>(q, j)]) * scale);
         __syncthreads();
         stockham_stage<N, T, R2, 1, +1, false, true, PS>(v, sm, lane, j, tw);
         stockham_stage<N, T, R1, R2, +1, true, true, PS>(v, sm, lane, j, tw);

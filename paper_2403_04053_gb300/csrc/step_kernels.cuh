@@ -470,24 +470,27 @@ __global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid
 {
     step_kernel_entry();
     using C = typename StepArgs<R>::C;
+    // the plane's values and FFTs: FP32 ones as cs32, whose butterflies stay scalar (packed
+    // ones schedule worse in this 1024-thread kernel)
+    using V = std::conditional_t<sizeof(R) == 4, cs32, C>;
     constexpr int T = Plan<N>::T, E = N / T, R0 = Plan<N>::R[0], R1 = Plan<N>::R[1], P = N + 1;
     extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
+    V* sm = reinterpret_cast<V*>(smraw);
     const int lane = threadIdx.x & 31, j = (threadIdx.x >> 5) % T, grp = threadIdx.x / (32 * T);
     const int z = blockIdx.x, b = blockIdx.y;
     const int x = grp * 32 + lane;             // column of this thread in steps 1 and 3
     const int my = grp * 32 + lane;            // row (spectral y index) in step 2
-    C* smc = sm + grp * 32;                    // columns: (pos, lane) at pos * P + lane
-    C* smr = sm + grp * 32 * P;                // rows:    (pos, lane) at lane * P + pos
+    V* smc = sm + grp * 32;                    // columns: (pos, lane) at pos * P + lane
+    V* smr = sm + grp * 32 * P;                // rows:    (pos, lane) at lane * P + pos
     const long long pbase = (long long)b * a.ncell + (long long)z * N * N;
-    const C* __restrict__ cur = a.cur + pbase + x;
+    const V* __restrict__ cur = reinterpret_cast<const V*>(a.cur + pbase + x);
     C* __restrict__ prev = a.prev + pbase + x;
-    const C* __restrict__ twx = a.tw[0];
-    const C* __restrict__ twy = a.tw[1];
-    C v[E];
+    const V* __restrict__ twx = reinterpret_cast<const V*>(a.tw[0]);
+    const V* __restrict__ twy = reinterpret_cast<const V*>(a.tw[1]);
+    V v[E];
     const bool dft = DFT && ((dx.member_mask >> b) & 1ull);
     // DFT scratch after the plane: y-plane partials [group][4][T][32], then x-plane sums [N][4]
-    C* red_y = sm + (size_t)N * P;
+    C* red_y = reinterpret_cast<C*>(sm + (size_t)N * P);
     C* sum_x = red_y + (size_t)4 * T * N;
     if (dft && threadIdx.x < N) {
         dft_prefetch_acc<R>(dx, b, (long long)z * N + threadIdx.x);   // plane [z][y]
@@ -530,8 +533,10 @@ __global__ void __launch_bounds__(xy_threads<N>(), 1) xypass_kernel(const __grid
     if (dft) {
         // y planes from the raw column values (the barriers of the FFT stages below order
         // these stores before the commit at the end)
-        C part[4];
-        dft_partials<N, T, R0>(v, j, dy.dw, dy.h[0], dy.h[1], part);
+        C part[4], vc[E];
+#pragma unroll
+        for (int q = 0; q < E; ++q) vc[q] = mk<C>(v[q].x, v[q].y);
+        dft_partials<N, T, R0>(vc, j, dy.dw, dy.h[0], dy.h[1], part);
         dft_stage<T>(part, red_y + (size_t)grp * 4 * T * 32, lane, j);
     }
     stockham_stage<N, T, R0, 1, -1, false, true, P, 1>(v, smc, lane, j, twy);
@@ -784,17 +789,15 @@ __global__ void __launch_bounds__(128) source_kernel(const __grid_constant__ Ste
 // ---------------------------------------------------------------------------------
 // SRC: 0 no V-term or source; otherwise the source form (source_acc's KIND: 1 scalar CW
 // members only, 3 CW and wave packets, 4 CW and the auxiliary wave, 2 any members)
+// The z-line work of one CTA: columns [x0, x0 + kLanes) of row y, member b.
 template <typename R, int N, bool DFT, int SRC, int PL = 0>
-__global__ void __launch_bounds__(kLanes * Plan<N, PL>::T, (pass_min_blocks<R, N, PL>())) zpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+__device__ __forceinline__ void ztile(const StepArgs<R>& a, const DftArgs<R>& d, int x0, int y, int b,
+                                      typename StepArgs<R>::C* sm)
 {
-    step_kernel_entry();
     using C = typename StepArgs<R>::C;
     constexpr int T = Plan<N, PL>::T, E = N / T, R0 = Plan<N, PL>::R[0];
-    extern __shared__ __align__(16) unsigned char smraw[];
-    C* sm = reinterpret_cast<C*>(smraw);
     const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
-    const int x = blockIdx.x * kLanes + lane;
-    const int y = blockIdx.y, b = blockIdx.z;
+    const int x = x0 + lane;
     const bool act = x < a.nx;
     const long long stride = (long long)a.nx * a.ny;
     const long long base = (long long)b * a.ncell + (long long)y * a.nx + x;
@@ -866,6 +869,14 @@ __global__ void __launch_bounds__(kLanes * Plan<N, PL>::T, (pass_min_blocks<R, N
     }
     if (!ok) atomicOr(a.flag, 1);
     if (dft && j == 0) dft_commit<R, T>(sm, lane, d, b, (long long)y * a.nx + x);   // plane [y][x]
+}
+
+template <typename R, int N, bool DFT, int SRC, int PL = 0>
+__global__ void __launch_bounds__(kLanes * Plan<N, PL>::T, (pass_min_blocks<R, N, PL>())) zpass_kernel(const __grid_constant__ StepArgs<R> a, const __grid_constant__ DftArgs<R> d)
+{
+    step_kernel_entry();
+    extern __shared__ __align__(16) unsigned char smraw[];
+    ztile<R, N, DFT, SRC, PL>(a, d, blockIdx.x * kLanes, blockIdx.y, blockIdx.z, reinterpret_cast<typename StepArgs<R>::C*>(smraw));
 }
 
 // ---------------------------------------------------------------------------------
