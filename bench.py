@@ -29,13 +29,14 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PSTD cell-updates/s, FP32 vs FP64 at stated error (1 GB300); adjoint/forward time"
 
-# DRAM bytes (read + write) of one cold launch at 128^3, from an ncu --set full capture of
-# that kernel (dram__bytes_read.sum + dram__bytes_write.sum); drop an entry when its kernel changes
-DRAM_TRAFFIC = {"xypass": 34.05e6, "zpass": 34.65e6}
+# DRAM bytes (read + write) of one cold launch at 128^3: dram__bytes_read.sum +
+# dram__bytes_write.sum from an ncu capture of two launches of each kernel (mean); drop an
+# entry when its kernel changes
+DRAM_TRAFFIC = {"xypass": 33.593e6 + 0.306e6, "zpass": 34.647e6 + 0.0}
 # the same for the 256^3 passes of the batched leg (the cluster-fused x+y pass and the z
 # pass, steps outside the DFT window), captured with 4 members; the leg scales them by the
 # units processed to its own member count
-BATCHED_TRAFFIC = {"xypass": 1.6117e9 + 0.8507e9, "zpass": 1.0848e9 + 0.5744e9}
+BATCHED_TRAFFIC = {"xypass": 1.0930e9 + 1.0030e9, "zpass": 1.0847e9 + 0.5944e9}
 WORKLOAD = "gaussian-sum-128^3"
 
 

@@ -185,6 +185,24 @@ __device__ __forceinline__ void dft_commit(const C* red, int lane, const DftArgs
     dft_accumulate<R>(d, b, pix, ef, d.mem[b].nfreq, tot[2], tot[3], tot[0], tot[1]);
 }
 
+// The line passes' shared memory: the [pos][lane] exchange tile of N x kPitch values, and on
+// DFT steps, where it fits, a region after it for the T partial sums of each line (4 values a
+// thread), so that the partials are staged right after they are formed and hold no registers
+// through the line transform.
+template <typename R, int N> __host__ __device__ constexpr size_t pass_smem_bytes() { return sizeof(typename StepArgs<R>::C) * (size_t)N * kPitch; }
+template <typename R, int N, int PL> __host__ __device__ constexpr size_t dft_red_bytes()
+{
+    return sizeof(typename StepArgs<R>::C) * (size_t)4 * Plan<N, PL>::T * kLanes;
+}
+template <typename R, int N, int PL> __host__ __device__ constexpr bool dft_red_separate()
+{
+    return pass_smem_bytes<R, N>() + dft_red_bytes<R, N, PL>() <= (size_t)227 * 1024;
+}
+template <typename R, int N, bool DFT, int PL> constexpr size_t line_pass_smem()
+{
+    return pass_smem_bytes<R, N>() + (DFT && dft_red_separate<R, N, PL>() ? dft_red_bytes<R, N, PL>() : 0);
+}
+
 template <typename R, int T, typename C>
 __device__ __forceinline__ void dft_finish(const C (&part)[4], C* red, int lane, int j, const DftArgs<R>& d, int b,
                                            long long pix, bool act)
@@ -200,7 +218,10 @@ __device__ __forceinline__ void dft_finish(const C (&part)[4], C* red, int lane,
 // contiguous, so the tile is one contiguous block of 32 * nx values)
 // ---------------------------------------------------------------------------------
 // The x-line work of one CTA: rows [row0, row0 + kLanes) of member b (row = z * ny + y).
-template <typename R, int N, bool DFT, int PL = 0>
+// On DFT steps the line partials go to slot SLOT of the region after the exchange tile;
+// COMMIT = false leaves their commit to the caller (the fused x+y pass commits both axes at
+// its end, off the path to its cluster barrier).
+template <typename R, int N, bool DFT, int PL = 0, bool COMMIT = true, int SLOT = 0>
 __device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R>& d, int b, int row0,
                                            typename StepArgs<R>::C* sm)
 {
@@ -224,11 +245,18 @@ __device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R
         for (int q = 0; q < E; ++q) v[q] = act ? row[slot_pos<N, T, R0>(q, j)] : zero_c<R, C>();
         if (a.pf_l1 && act) prefetch_l1(prow + 16 * j);   // the row's 16 cache lines, one a thread
         const bool dft = DFT && ((d.member_mask >> b) & 1ull);
+        constexpr bool SEP = dft_red_separate<R, N, PL>();
+        static_assert(SEP || (COMMIT && SLOT == 0), "a deferred commit needs the separate region");
+        C* red = sm + (size_t)N * kPitch + (size_t)SLOT * 4 * T * kLanes;
+        if (dft && j == 0 && act) dft_prefetch_acc<R>(d, b, row0 + lane);
         C part[4];
         if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
+        if constexpr (SEP)
+            if (dft) dft_stage<T>(part, red, lane, j);   // read after the transform's barriers
         kinetic_line<N, false, 0, PL>(v, sm, lane, j, a.tw[0], a.kin[0], R(a.mem[b].eta));
         __syncthreads();
-        if (dft) dft_finish<R, T>(part, sm, lane, j, d, b, row0 + lane, act);   // plane [z][y]: pixel = row
+        if constexpr (!SEP)
+            if (dft) dft_finish<R, T>(part, sm, lane, j, d, b, row0 + lane, act);   // plane [z][y]: pixel = row
         if (!act) return;
 #pragma unroll
         for (int q0 = 0; q0 < E; q0 += 4) {
@@ -239,6 +267,8 @@ __device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R
             for (int i = 0; i < 4; ++i)
                 prow[slot_pos<N, T, R0>(q0 + i, j)] = mk<C>(pg[i].x + v[q0 + i].y, pg[i].y - v[q0 + i].x);   // p - i w
         }
+        if constexpr (SEP && COMMIT)
+            if (dft && j == 0) dft_commit<R, T>(red, lane, d, b, row0 + lane);   // plane [z][y]: pixel = row
         return;
     }
     const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
@@ -270,12 +300,19 @@ __device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R
     for (int q = 0; q < E; ++q) v[q] = sm[slot_pos<N, T, R0>(q, j) * kPitch + lane];
     __syncthreads();
     const bool dft = DFT && ((d.member_mask >> b) & 1ull);
+    constexpr bool SEP = dft_red_separate<R, N, PL>();
+    static_assert(SEP || (COMMIT && SLOT == 0), "a deferred commit needs the separate region");
+    C* red = sm + (size_t)N * kPitch + (size_t)SLOT * 4 * T * kLanes;
+    if (dft && j == 0 && lane < nrows) dft_prefetch_acc<R>(d, b, row0 + lane);
     C part[4];
     if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
+    if constexpr (SEP)
+        if (dft) dft_stage<T>(part, red, lane, j);   // read after the transform's barriers
     const R eta = R(a.mem[b].eta);
     kinetic_line<N, false, kPitch, PL>(v, sm, lane, j, a.tw[0], a.kin[0], eta);
     __syncthreads();
-    if (dft) dft_finish<R, T>(part, sm, lane, j, d, b, row0 + lane, lane < nrows);   // plane [z][y]: pixel = row
+    if constexpr (!SEP)
+        if (dft) dft_finish<R, T>(part, sm, lane, j, d, b, row0 + lane, lane < nrows);   // plane [z][y]: pixel = row
 #pragma unroll
     for (int q = 0; q < E; ++q) sm[slot_pos<N, T, R0>(q, j) * kPitch + lane] = v[q];
     __syncthreads();
@@ -295,6 +332,8 @@ __device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R
             }
         }
     }
+    if constexpr (SEP && COMMIT)
+        if (dft && j == 0 && lane < nrows) dft_commit<R, T>(red, lane, d, b, row0 + lane);   // plane [z][y]: pixel = row
 }
 
 template <typename R, int N, bool DFT, int PL = 0>
@@ -316,8 +355,9 @@ template <bool CG, typename C> __device__ __forceinline__ C load_prev(const C* p
     else return *p;
 }
 
-// The y-line work of one CTA: columns [x0, x0 + kLanes) of z plane z, member b.
-template <typename R, int N, bool DFT, bool CG = false, int PL = 0>
+// The y-line work of one CTA: columns [x0, x0 + kLanes) of z plane z, member b (DFT partials
+// in slot SLOT of the region after the exchange tile).
+template <typename R, int N, bool DFT, bool CG = false, int PL = 0, int SLOT = 0>
 __device__ __forceinline__ void ypass_tile(const StepArgs<R>& a, const DftArgs<R>& d, int x0, int z, int b,
                                            typename StepArgs<R>::C* sm)
 {
@@ -345,14 +385,22 @@ __device__ __forceinline__ void ypass_tile(const StepArgs<R>& a, const DftArgs<R
     for (int q = 0; q < E; ++q) pv[q] = act ? load_prev<CG>(a.prev + base + slot_pos<N, T, R0>(q, j) * stride) : zero_c<R, C>();
 #endif
     const bool dft = DFT && ((d.member_mask >> b) & 1ull);
+    constexpr bool SEP = dft_red_separate<R, N, PL>();
+    static_assert(SEP || SLOT == 0, "slot 1 needs the separate region");
+    C* red = SEP ? sm + (size_t)N * kPitch + (size_t)SLOT * 4 * T * kLanes : sm;
+    if (dft && j == 0 && act) dft_prefetch_acc<R>(d, b, (long long)z * a.nx + x);
     C part[4];
     if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
+    if constexpr (SEP)
+        if (dft) dft_stage<T>(part, red, lane, j);   // read after the transform's barriers
     const R eta = R(a.mem[b].eta);
     kinetic_line<N, false, kPitch, PL>(v, sm, lane, j, a.tw[1], a.kin[1], eta);
-    if (dft) {
-        __syncthreads();   // the exchange tile is free again
-        dft_stage<T>(part, sm, lane, j);
-        __syncthreads();
+    if constexpr (!SEP) {
+        if (dft) {
+            __syncthreads();   // the exchange tile is free again
+            dft_stage<T>(part, sm, lane, j);
+            __syncthreads();
+        }
     }
     if (!act) return;
     constexpr int GR = N >= 192 ? 4 : 1;   // update operands read GR at a time (see the z pass)
@@ -374,7 +422,7 @@ __device__ __forceinline__ void ypass_tile(const StepArgs<R>& a, const DftArgs<R
             a.prev[idx] = mk<C>(p.x + v[q].y, p.y - v[q].x);
         }
     }
-    if (dft && j == 0) dft_commit<R, T>(sm, lane, d, b, (long long)z * a.nx + x);   // plane [z][x]
+    if (dft && j == 0) dft_commit<R, T>(red, lane, d, b, (long long)z * a.nx + x);   // plane [z][x]
 }
 
 template <typename R, int N, bool DFT, int PL = 0>
@@ -421,9 +469,22 @@ __global__ void __launch_bounds__(kLanes * Plan<N, PL>::T, (pass_min_blocks<R, N
     C* sm = reinterpret_cast<C*>(smraw);
     const int r = blockIdx.x;                  // rank in the cluster (the grid's x extent is the cluster)
     const int z = blockIdx.y, b = blockIdx.z;
-    xpass_tile<R, N, DFT, PL>(a, dx, b, z * N + r * kLanes, sm);
+    const int row0 = z * N + r * kLanes;
+    // on DFT steps the row phase's partials wait in slot 0 and are committed after the
+    // column phase, whose own partials use slot 1
+    xpass_tile<R, N, DFT, PL, false, 0>(a, dx, b, row0, sm);
     cluster_sync_acq_rel();
-    ypass_tile<R, N, DFT, true, PL>(a, dy, r * kLanes, z, b, sm);
+    ypass_tile<R, N, DFT, true, PL, 1>(a, dy, r * kLanes, z, b, sm);
+    if constexpr (DFT) {
+        constexpr int T = Plan<N, PL>::T;
+        // the row phase's thread-to-line map: consecutive lanes of a line at N = 256 (default
+        // plan), lane-major otherwise
+        const bool rows_consecutive = N == 256 && PL == 0;
+        const int lane = rows_consecutive ? threadIdx.x / T : threadIdx.x % kLanes;
+        const int j = rows_consecutive ? threadIdx.x % T : threadIdx.x / kLanes;
+        if (((dx.member_mask >> b) & 1ull) && j == 0)
+            dft_commit<R, T>(sm + (size_t)N * kPitch, lane, dx, b, row0 + lane);   // plane [z][y]: pixel = row
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -819,13 +880,19 @@ __device__ __forceinline__ void ztile(const StepArgs<R>& a, const DftArgs<R>& d,
         }
     }
 #endif
+    constexpr bool SEP = dft_red_separate<R, N, PL>();
+    C* red = SEP ? sm + (size_t)N * kPitch : sm;
     C part[4];
     if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
+    if constexpr (SEP)
+        if (dft) dft_stage<T>(part, red, lane, j);   // read after the transform's barriers
     kinetic_line<N, false, kPitch, PL>(v, sm, lane, j, a.tw[2], a.kin[2], R(a.mem[b].eta));
-    if (dft) {
-        __syncthreads();   // the exchange tile is free again
-        dft_stage<T>(part, sm, lane, j);
-        __syncthreads();
+    if constexpr (!SEP) {
+        if (dft) {
+            __syncthreads();   // the exchange tile is free again
+            dft_stage<T>(part, sm, lane, j);
+            __syncthreads();
+        }
     }
     if (!act) return;
     const R gxy = a.mask[0][x] * a.mask[1][y];
@@ -868,7 +935,7 @@ __device__ __forceinline__ void ztile(const StepArgs<R>& a, const DftArgs<R>& d,
     }
     }
     if (!ok) atomicOr(a.flag, 1);
-    if (dft && j == 0) dft_commit<R, T>(sm, lane, d, b, (long long)y * a.nx + x);   // plane [y][x]
+    if (dft && j == 0) dft_commit<R, T>(red, lane, d, b, (long long)y * a.nx + x);   // plane [y][x]
 }
 
 template <typename R, int N, bool DFT, int SRC, int PL = 0>
@@ -1219,7 +1286,7 @@ __global__ void __launch_bounds__(kLanes * Plan<N>::T, tma_ctas_sm<N>()) colpass
 // ---------------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------------
-template <typename R, int N> size_t pass_smem() { return sizeof(typename StepArgs<R>::C) * (size_t)N * kPitch; }
+template <typename R, int N> size_t pass_smem() { return pass_smem_bytes<R, N>(); }
 
 // Raise a kernel's dynamic shared-memory limit once per device instead of on every launch
 // (one flag word per kernel: the template is keyed on the kernel itself).
@@ -1240,7 +1307,7 @@ template <typename R, int N> constexpr bool alt_plan_built() { return sizeof(R) 
 
 template <typename R, int N, int PL> cudaError_t xpass_pl(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
-    const size_t sm = pass_smem<R, N>();
+    const size_t sm = d ? line_pass_smem<R, N, true, PL>() : line_pass_smem<R, N, false, PL>();
     cudaError_t e = d ? set_smem_once<xpass_kernel<R, N, true, PL>>(sm) : set_smem_once<xpass_kernel<R, N, false, PL>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.ny * a.nz + kLanes - 1) / kLanes, batch);
@@ -1298,7 +1365,7 @@ template <typename R, int N, int AXIS, int SRC> cudaError_t colpass_tma_n(const 
 
 template <typename R, int N, int PL> cudaError_t ypass_pl(const StepArgs<R>& a, const DftArgs<R>* d, int batch, cudaStream_t s)
 {
-    const size_t sm = pass_smem<R, N>();
+    const size_t sm = d ? line_pass_smem<R, N, true, PL>() : line_pass_smem<R, N, false, PL>();
     cudaError_t e = d ? set_smem_once<ypass_kernel<R, N, true, PL>>(sm) : set_smem_once<ypass_kernel<R, N, false, PL>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + kLanes - 1) / kLanes, a.nz, batch);
@@ -1320,7 +1387,7 @@ template <typename R, int N> cudaError_t ypass_n(const StepArgs<R>& a, const Dft
 template <typename R, int N, bool DFT, int SRC, int PL>
 cudaError_t zpass_launch_pl(const StepArgs<R>& a, const DftArgs<R>& d, int batch, cudaStream_t s)
 {
-    const size_t sm = pass_smem<R, N>();
+    const size_t sm = line_pass_smem<R, N, DFT, PL>();
     cudaError_t e = set_smem_once<zpass_kernel<R, N, DFT, SRC, PL>>(sm);
     if (e != cudaSuccess) return e;
     dim3 grid((a.nx + kLanes - 1) / kLanes, a.ny, batch);
@@ -1443,7 +1510,8 @@ template <typename R> bool xypass_available(int nx, int ny, int mode)
 template <typename R, int N, bool DFT, int PL = 0>
 cudaError_t xycl_launch(const StepArgs<R>& a, const DftArgs<R>& dx, const DftArgs<R>& dy, int batch, cudaStream_t s)
 {
-    const size_t sm = pass_smem<R, N>();
+    static_assert(!DFT || pass_smem_bytes<R, N>() + 2 * dft_red_bytes<R, N, PL>() <= (size_t)227 * 1024, "two DFT slots");
+    const size_t sm = pass_smem_bytes<R, N>() + (DFT ? 2 * dft_red_bytes<R, N, PL>() : 0);
     cudaError_t e = set_smem_once<xycl_kernel<R, N, DFT, PL>>(sm);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
