@@ -122,12 +122,22 @@ __device__ __forceinline__ void dft_accumulate(const DftArgs<R>& a, int b, long 
         double2* dp0 = accf + a.face_off[f0] + a.face_size[f0] + pix;
         double2* ps1 = accf + a.face_off[f1] + pix;
         double2* dp1 = accf + a.face_off[f1] + a.face_size[f1] + pix;
-        const double q0x = p0.x, q0y = p0.y, q1x = p1.x, q1y = p1.y;
-        const double e0x = d0.x, e0y = d0.y, e1x = d1.x, e1y = d1.y;
-        ps0->x += q0x * cf - q0y * sf;  ps0->y += q0x * sf + q0y * cf;
-        ps1->x += q1x * cf - q1y * sf;  ps1->y += q1x * sf + q1y * cf;
-        dp0->x += e0x * cf - e0y * sf;  dp0->y += e0x * sf + e0y * cf;
-        dp1->x += e1x * cf - e1y * sf;  dp1->y += e1x * sf + e1y * cf;
+        if constexpr (sizeof(R) == 4) {
+            // FP32 values: the phase products in FP32 (the values carry FP32 precision), the
+            // sums in FP64 -- half the FP64 instructions of the all-double form
+            const float c = float(cf), sn = float(sf);
+            ps0->x += double(p0.x * c - p0.y * sn);  ps0->y += double(p0.x * sn + p0.y * c);
+            ps1->x += double(p1.x * c - p1.y * sn);  ps1->y += double(p1.x * sn + p1.y * c);
+            dp0->x += double(d0.x * c - d0.y * sn);  dp0->y += double(d0.x * sn + d0.y * c);
+            dp1->x += double(d1.x * c - d1.y * sn);  dp1->y += double(d1.x * sn + d1.y * c);
+        } else {
+            const double q0x = p0.x, q0y = p0.y, q1x = p1.x, q1y = p1.y;
+            const double e0x = d0.x, e0y = d0.y, e1x = d1.x, e1y = d1.y;
+            ps0->x += q0x * cf - q0y * sf;  ps0->y += q0x * sf + q0y * cf;
+            ps1->x += q1x * cf - q1y * sf;  ps1->y += q1x * sf + q1y * cf;
+            dp0->x += e0x * cf - e0y * sf;  dp0->y += e0x * sf + e0y * cf;
+            dp1->x += e1x * cf - e1y * sf;  dp1->y += e1x * sf + e1y * cf;
+        }
     }
 }
 
@@ -150,6 +160,32 @@ __device__ __forceinline__ void dft_partials(const C (&v)[E], int j, const C* __
 {
 #pragma unroll
     for (int k = 0; k < 4; ++k) part[k] = mk<C>(decltype(C::x)(0), decltype(C::x)(0));
+#if PSTD_F32X2
+    if constexpr (std::is_same_v<C, float2>) {
+        // sum_q v_q w_q as two packed sums, A = sum v.x (w.x, w.y) and B = sum v.y (w.x, w.y):
+        // the complex sum is (A.x - B.y, A.y + B.x); each plane takes two fma.f32x2 a value
+        unsigned long long A[2] = {0ull, 0ull}, B[2] = {0ull, 0ull};
+#pragma unroll
+        for (int q = 0; q < E; ++q) {
+            const int pos = slot_pos<N, T, R0>(q, j);
+            const unsigned long long vx = pk2(make_float2(v[q].x, v[q].x)), vy = pk2(make_float2(v[q].y, v[q].y));
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const unsigned long long w = pk2(__ldg(&dw[p * N + pos]));
+                asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(A[p]) : "l"(vx), "l"(w));
+                asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(B[p]) : "l"(vy), "l"(w));
+            }
+            if (pos == h0) part[2] = v[q];
+            if (pos == h1) part[3] = v[q];
+        }
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float2 a = up2(A[p]), b = up2(B[p]);
+            part[p] = make_float2(a.x - b.y, a.y + b.x);
+        }
+        return;
+    }
+#endif
 #pragma unroll
     for (int q = 0; q < E; ++q) {
         const int pos = slot_pos<N, T, R0>(q, j);
@@ -248,7 +284,7 @@ __device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R
         constexpr bool SEP = dft_red_separate<R, N, PL>();
         static_assert(SEP || (COMMIT && SLOT == 0), "a deferred commit needs the separate region");
         C* red = sm + (size_t)N * kPitch + (size_t)SLOT * 4 * T * kLanes;
-        if (dft && j == 0 && act) dft_prefetch_acc<R>(d, b, row0 + lane);
+        if (dft && threadIdx.x < nrows) dft_prefetch_acc<R>(d, b, row0 + threadIdx.x);
         C part[4];
         if (dft) dft_partials<N, T, R0>(v, j, d.dw, d.h[0], d.h[1], part);
         if constexpr (SEP)
@@ -267,8 +303,10 @@ __device__ __forceinline__ void xpass_tile(const StepArgs<R>& a, const DftArgs<R
             for (int i = 0; i < 4; ++i)
                 prow[slot_pos<N, T, R0>(q0 + i, j)] = mk<C>(pg[i].x + v[q0 + i].y, pg[i].y - v[q0 + i].x);   // p - i w
         }
+        // the commit: thread t < 32 (one warp) takes line t, so that the FP64 accumulation runs
+        // in one warp instead of two lanes of every warp
         if constexpr (SEP && COMMIT)
-            if (dft && j == 0) dft_commit<R, T>(red, lane, d, b, row0 + lane);   // plane [z][y]: pixel = row
+            if (dft && threadIdx.x < nrows) dft_commit<R, T>(red, threadIdx.x, d, b, row0 + threadIdx.x);   // plane [z][y]: pixel = row
         return;
     }
     const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
@@ -476,14 +514,10 @@ __global__ void __launch_bounds__(kLanes * Plan<N, PL>::T, (pass_min_blocks<R, N
     cluster_sync_acq_rel();
     ypass_tile<R, N, DFT, true, PL, 1>(a, dy, r * kLanes, z, b, sm);
     if constexpr (DFT) {
-        constexpr int T = Plan<N, PL>::T;
-        // the row phase's thread-to-line map: consecutive lanes of a line at N = 256 (default
-        // plan), lane-major otherwise
-        const bool rows_consecutive = N == 256 && PL == 0;
-        const int lane = rows_consecutive ? threadIdx.x / T : threadIdx.x % kLanes;
-        const int j = rows_consecutive ? threadIdx.x % T : threadIdx.x / kLanes;
-        if (((dx.member_mask >> b) & 1ull) && j == 0)
-            dft_commit<R, T>(sm + (size_t)N * kPitch, lane, dx, b, row0 + lane);   // plane [z][y]: pixel = row
+        // one warp commits the row phase's sums, thread t line t (the partials are stored by
+        // line, whatever the phase's thread-to-line map)
+        if (((dx.member_mask >> b) & 1ull) && threadIdx.x < kLanes)
+            dft_commit<R, Plan<N, PL>::T>(sm + (size_t)N * kPitch, threadIdx.x, dx, b, row0 + threadIdx.x);   // plane [z][y]
     }
 }
 
