@@ -253,6 +253,18 @@ __device__ __forceinline__ void dft_finish(const C (&part)[4], C* red, int lane,
 // x pass: 32 consecutive rows per CTA, staged through shared memory (rows are
 // contiguous, so the tile is one contiguous block of 32 * nx values)
 // ---------------------------------------------------------------------------------
+// Offsets of a thread's line values in the y and z passes.  On lines of 192 points or more they
+// are 32-bit and relative to the member (a member holds fewer than 2^32 cells): o holds the
+// line's start plus j * st, and slot q adds slot_pos(q, 0) * st, one multiply-add a value
+// (256^3 x 16 step 3.72 -> 3.67 ms).  Shorter lines keep 64-bit offsets from the batch's start,
+// o excluding j: the 32-bit form made the 128-point z pass slower (17.8 against 16.7 us).
+template <int N> using line_off_t = std::conditional_t<(N >= 192), unsigned, long long>;
+template <int N, int T, int R0> __device__ __forceinline__ line_off_t<N> line_off(int q, int j, line_off_t<N> o, line_off_t<N> st)
+{
+    if constexpr (N >= 192) return o + (line_off_t<N>)slot_pos<N, T, R0>(q, 0) * st;
+    else return o + (line_off_t<N>)slot_pos<N, T, R0>(q, j) * st;
+}
+
 // The x-line work of one CTA: rows [row0, row0 + kLanes) of member b (row = z * ny + y).
 // On DFT steps the line partials go to slot SLOT of the region after the exchange tile;
 // COMMIT = false leaves their commit to the caller (the fused x+y pass commits both axes at
@@ -404,23 +416,28 @@ __device__ __forceinline__ void ypass_tile(const StepArgs<R>& a, const DftArgs<R
     const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
     const int x = x0 + lane;
     const bool act = x < a.nx;
-    const long long stride = a.nx;
-    const long long base = (long long)b * a.ncell + (long long)z * a.nx * a.ny + x;
+    using Off = line_off_t<N>;
+    constexpr bool W32 = N >= 192;
+    const long long mbase = (long long)b * a.ncell;
+    const C* curm = a.cur + (W32 ? mbase : 0);
+    C* prevm = a.prev + (W32 ? mbase : 0);
+    const Off st = (Off)a.nx;
+    const Off o0 = (Off)z * (Off)a.nx * (Off)a.ny + (Off)x + (W32 ? (Off)j * st : (Off)mbase);
     C v[E];
 #pragma unroll
-    for (int q = 0; q < E; ++q) v[q] = act ? a.cur[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
+    for (int q = 0; q < E; ++q) v[q] = act ? curm[line_off<N, T, R0>(q, j, o0, st)] : zero_c<R, C>();
 #if !PSTD_PREFETCH_PREV
     if constexpr (N >= 192 && !CG) {
         if (a.pf_l1 && act) {
 #pragma unroll
-            for (int q = 0; q < E; ++q) prefetch_l1(a.prev + base + slot_pos<N, T, R0>(q, j) * stride);
+            for (int q = 0; q < E; ++q) prefetch_l1(prevm + line_off<N, T, R0>(q, j, o0, st));
         }
     }
 #endif
 #if PSTD_PREFETCH_PREV
     C pv[E];
 #pragma unroll
-    for (int q = 0; q < E; ++q) pv[q] = act ? load_prev<CG>(a.prev + base + slot_pos<N, T, R0>(q, j) * stride) : zero_c<R, C>();
+    for (int q = 0; q < E; ++q) pv[q] = act ? load_prev<CG>(prevm + line_off<N, T, R0>(q, j, o0, st)) : zero_c<R, C>();
 #endif
     const bool dft = DFT && ((d.member_mask >> b) & 1ull);
     constexpr bool SEP = dft_red_separate<R, N, PL>();
@@ -447,17 +464,17 @@ __device__ __forceinline__ void ypass_tile(const StepArgs<R>& a, const DftArgs<R
 #if !PSTD_PREFETCH_PREV
         C pg[GR];
 #pragma unroll
-        for (int i = 0; i < GR; ++i) pg[i] = load_prev<CG>(a.prev + base + slot_pos<N, T, R0>(q0 + i, j) * stride);
+        for (int i = 0; i < GR; ++i) pg[i] = load_prev<CG>(prevm + line_off<N, T, R0>(q0 + i, j, o0, st));
 #endif
 #pragma unroll
         for (int q = q0; q < q0 + GR; ++q) {
-            const long long idx = base + slot_pos<N, T, R0>(q, j) * stride;
+            const Off off = line_off<N, T, R0>(q, j, o0, st);
 #if PSTD_PREFETCH_PREV
             const C p = pv[q];
 #else
             const C p = pg[q - q0];
 #endif
-            a.prev[idx] = mk<C>(p.x + v[q].y, p.y - v[q].x);
+            prevm[off] = mk<C>(p.x + v[q].y, p.y - v[q].x);
         }
     }
     if (dft && j == 0) dft_commit<R, T>(red, lane, d, b, (long long)z * a.nx + x);   // plane [z][x]
@@ -894,15 +911,20 @@ __device__ __forceinline__ void ztile(const StepArgs<R>& a, const DftArgs<R>& d,
     const int lane = threadIdx.x % kLanes, j = threadIdx.x / kLanes;
     const int x = x0 + lane;
     const bool act = x < a.nx;
-    const long long stride = (long long)a.nx * a.ny;
-    const long long base = (long long)b * a.ncell + (long long)y * a.nx + x;
+    using Off = line_off_t<N>;
+    constexpr bool W32 = N >= 192;
+    const long long mbase = (long long)b * a.ncell;
+    const C* curm = a.cur + (W32 ? mbase : 0);
+    C* prevm = a.prev + (W32 ? mbase : 0);
+    const Off st = (Off)a.nx * (Off)a.ny;
+    const Off o0 = (Off)y * (Off)a.nx + (Off)x + (W32 ? (Off)j * st : (Off)mbase);
     C v[E];
 #pragma unroll
-    for (int q = 0; q < E; ++q) v[q] = act ? a.cur[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
+    for (int q = 0; q < E; ++q) v[q] = act ? curm[line_off<N, T, R0>(q, j, o0, st)] : zero_c<R, C>();
 #if PSTD_PREFETCH_PREV
     C pv[E];
 #pragma unroll
-    for (int q = 0; q < E; ++q) pv[q] = act ? a.prev[base + slot_pos<N, T, R0>(q, j) * stride] : zero_c<R, C>();
+    for (int q = 0; q < E; ++q) pv[q] = act ? prevm[line_off<N, T, R0>(q, j, o0, st)] : zero_c<R, C>();
 #endif
     const bool dft = DFT && ((d.member_mask >> b) & 1ull);
     if (dft && j == 0 && act) dft_prefetch_acc<R>(d, b, (long long)y * a.nx + x);   // plane [y][x]
@@ -910,7 +932,7 @@ __device__ __forceinline__ void ztile(const StepArgs<R>& a, const DftArgs<R>& d,
     if constexpr (N >= 192) {   // compiled in for long lines only: its mere presence slows the 128-point pass
         if (a.pf_l1 && act) {
 #pragma unroll
-            for (int q = 0; q < E; ++q) prefetch_l1(a.prev + base + slot_pos<N, T, R0>(q, j) * stride);
+            for (int q = 0; q < E; ++q) prefetch_l1(prevm + line_off<N, T, R0>(q, j, o0, st));
         }
     }
 #endif
@@ -945,12 +967,12 @@ __device__ __forceinline__ void ztile(const StepArgs<R>& a, const DftArgs<R>& d,
 #if !PSTD_PREFETCH_PREV
     C pg[GR];
 #pragma unroll
-    for (int i = 0; i < GR; ++i) pg[i] = a.prev[base + slot_pos<N, T, R0>(q0 + i, j) * stride];
+    for (int i = 0; i < GR; ++i) pg[i] = prevm[line_off<N, T, R0>(q0 + i, j, o0, st)];
 #endif
 #pragma unroll
     for (int q = q0; q < q0 + GR; ++q) {
         const int z = slot_pos<N, T, R0>(q, j);
-        const long long idx = base + z * stride;
+        const Off off = line_off<N, T, R0>(q, j, o0, st);
 #if PSTD_PREFETCH_PREV
         C p = pv[q];
 #else
@@ -958,14 +980,14 @@ __device__ __forceinline__ void ztile(const StepArgs<R>& a, const DftArgs<R>& d,
 #endif
         if constexpr (SRC) {
             if (src_col && z >= slo[2] && z < shi[2]) {
-                const C sa = source_acc<R, C, SRC>(a, b, s, x, y, z, idx);
+                const C sa = source_acc<R, C, SRC>(a, b, s, x, y, z, (W32 ? mbase : 0) + (long long)off);
                 p = mk<C>(p.x + a.c2 * sa.y, p.y - a.c2 * sa.x);
             }
         }
         const R g = gxy * a.mask[2][z];
         const C acc = mk<C>(g * (p.x + v[q].y), g * (p.y - v[q].x));
         ok = ok && finite_c<R>(acc.x, acc.y);
-        a.prev[idx] = acc;
+        prevm[off] = acc;
     }
     }
     if (!ok) atomicOr(a.flag, 1);
