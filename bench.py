@@ -32,11 +32,11 @@ METRIC = "PSTD cell-updates/s, FP32 vs FP64 at stated error (1 GB300); adjoint/f
 # DRAM bytes (read + write) of one cold launch at 128^3: dram__bytes_read.sum +
 # dram__bytes_write.sum from an ncu capture of two launches of each kernel (mean); drop an
 # entry when its kernel changes
-DRAM_TRAFFIC = {"xypass": 33.594e6 + 0.299e6, "zpass": 34.645e6 + 0.0}
+DRAM_TRAFFIC = {"xypass": 33.593e6 + 0.295e6, "zpass": 34.645e6 + 0.0}
 # the same for the 256^3 passes of the batched leg (the cluster-fused x+y pass and the z
 # pass, steps outside the DFT window), captured with 4 members; the leg scales them by the
 # units processed to its own member count
-BATCHED_TRAFFIC = {"xypass": 1.0899e9 + 0.8993e9, "zpass": 1.0841e9 + 0.5595e9}
+BATCHED_TRAFFIC = {"xypass": 1.0906e9 + 0.9002e9, "zpass": 1.0861e9 + 0.5505e9}
 WORKLOAD = "gaussian-sum-128^3"
 
 
