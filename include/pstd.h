@@ -290,18 +290,20 @@ pstd_status pstd_transform_adjoint(pstd_grid* g, int b, int f, const double* xyz
 
 /* dL/dV on the box [box_lo, box_hi) of grid nodes (x fastest, doubles) for a loss that is
  * a function of the scaled phasors of a run of nsteps leapfrog steps from rest, given
- * dl_dphasors = the gradient of L with respect to them (one block per frequency of the
- * member's DFT window, each in the layout of pstd_get_phasors).  Batch-1 grids only
- * (EINVAL otherwise); needs the incidence and the DFT window (ESTATE), and the window must
- * end within nsteps (EINVAL).  The discrete adjoint of Eq. PSTDupdating with Eq. expmask:
+ * dl_dphasors = the gradient of L with respect to them: for member 0, 1, ... in order, one
+ * block per frequency of the member's DFT window, each in the layout of pstd_get_phasors.
+ * On a batch the members share V, so the result is the sum of their contributions (a loss
+ * over several incidences).  Every member needs its CW incidence and its DFT window
+ * (ESTATE), each window must end within nsteps (EINVAL); packet, auxiliary-wave and spinor
+ * grids are refused (EINVAL).  The discrete adjoint of Eq. PSTDupdating with Eq. expmask:
  * the forward run is repeated with checkpoints of (psi^{n-1}, psi^n) every
  * checkpoint_interval steps (0: ceil(sqrt(nsteps))), each segment is recomputed, and the
  * adjoint levels are stepped backward with the forward kernels (the adjoint of the update
  * is its complex conjugate with no incident wave), accumulating
- * dL/dV = (2 dt/hbar) sum_n Im[nu^{n+1} (psi^n + psi_inc^n)] (no psi_inc in the PAPER form).
- * Device memory: 2 ceil(nsteps/K) + K + 2 + nfreq states.  Leaves the grid at rest (state
- * zero, step 0) with its DFT sums untouched.  `mem` applies to dl_dphasors and dl_dv;
- * synchronises. */
+ * dL/dV = (2 dt/hbar) sum_b sum_n Im[nu_b^{n+1} (psi_b^n + psi_inc,b^n)] (no psi_inc in the
+ * PAPER form).  Device memory: 2 ceil(nsteps/K) + K + 2 states of the whole batch plus one
+ * member state per (member, frequency).  Leaves the grid at rest (state zero, step 0) with
+ * its DFT sums untouched.  `mem` applies to dl_dphasors and dl_dv; synchronises. */
 pstd_status pstd_adjoint_gradient(pstd_grid* g, long nsteps, const void* dl_dphasors, const int box_lo[3],
                                   const int box_hi[3], long checkpoint_interval, double* dl_dv, int mem);
 
@@ -310,7 +312,8 @@ pstd_status pstd_adjoint_gradient(pstd_grid* g, long nsteps, const void* dl_dpha
  * up to max_steps steps (allocated now: 2 ceil(max_steps/interval) states).  A later
  * pstd_adjoint_gradient over nsteps <= the recorded run with the same checkpoint interval then
  * uses them instead of repeating the forward run.  pstd_set_potential and pstd_set_incidence
- * discard the record; pstd_set_field stops it.  interval 0 stops recording.  Batch-1 grids. */
+ * discard the record; pstd_set_field stops it.  interval 0 stops recording.  A state here holds
+ * every member of the batch. */
 pstd_status pstd_set_checkpointing(pstd_grid* g, long interval, long max_steps);
 
 /* CUDA-graph replay of pstd_step (on by default).  A pstd_step call that repeats the previous

@@ -58,7 +58,7 @@ __global__ void injection_kernel(const __grid_constant__ InjectionArgs<R> a)
     a.J[e] = mk<C>(R(sx * a.scale.x - sy * a.scale.y), R(sx * a.scale.y + sy * a.scale.x));
 }
 
-// prev += coef * J over the whole state (member 0)
+// prev += coef * J over one member's state
 template <typename R, typename C>
 __global__ void inject_kernel(C* __restrict__ prev, const C* __restrict__ J, C coef, long long n)
 {
@@ -69,7 +69,8 @@ __global__ void inject_kernel(C* __restrict__ prev, const C* __restrict__ J, C c
     prev[e] = mk<C>(p.x + coef.x * j.x - coef.y * j.y, p.y + coef.x * j.y + coef.y * j.x);
 }
 
-// grad[box] += (2 dt / hbar) Im[nu (u + s phase)] on the box [lo, hi) (x fastest)
+// grad[box] += (2 dt / hbar) sum_b Im[nu_b (u_b + s_b phase_b)] on the box [lo, hi) (x
+// fastest): the members share V, so their contributions add
 template <typename R>
 __global__ void grad_kernel(const __grid_constant__ GradArgs<R> a)
 {
@@ -82,13 +83,17 @@ __global__ void grad_kernel(const __grid_constant__ GradArgs<R> a)
     const int y = a.lo[1] + (int)((e / bx) % by);
     const int z = a.lo[2] + (int)(e / ((long long)bx * by));
     const long long idx = ((long long)z * a.ny + y) * a.nx + x;
-    const C nu = a.nu[idx];
-    C u = a.u[idx];
-    if (a.with_inc) {
-        const C p = cmul(cmul(cmul(a.s, a.phase[0][x]), a.phase[1][y]), a.phase[2][z]);
-        u = cadd(u, p);
+    double acc = 0.0;
+    for (int b = 0; b < a.batch; ++b) {
+        const C nu = a.nu[b * a.ncell + idx];
+        C u = a.u[b * a.ncell + idx];
+        if (a.with_inc) {
+            const C p = cmul(cmul(cmul(a.s[b], a.phase[0][b * a.nx + x]), a.phase[1][b * a.ny + y]), a.phase[2][b * a.nz + z]);
+            u = cadd(u, p);
+        }
+        acc += double(nu.x) * double(u.y) + double(nu.y) * double(u.x);
     }
-    a.grad[e] += a.c2 * (double(nu.x) * double(u.y) + double(nu.y) * double(u.x));
+    a.grad[e] += a.c2 * acc;
 }
 
 // ---------------------------------------------------------------------------------

@@ -825,12 +825,13 @@ template <typename R> void plan_steps(pstd_grid* g, long nsteps, bool dft, long 
 }
 
 // Enqueue planned steps.  With `record` the checkpoints of the run from rest are copied aside
-// before steps n = s K; with `save` the state after each step goes to save + (s + 1) * ncell.
+// before steps n = s K; with `save` the state after each step goes to save + (s + 1) * the
+// size of one state of every member.
 template <typename R>
 pstd_status enqueue_steps(pstd_grid* g, const std::vector<PlannedStep<R>>& plan, bool record, void* save)
 {
     const bool need_src = g->desc.tfsf_mode == PSTD_TFSF_PAPER || g->vhi[0] > g->vlo[0] || (g->spinor && g->bhi[0] > g->blo[0]);
-    const size_t sb = (size_t)g->ncell * g->csize;
+    const size_t sb = (size_t)g->batch * g->ncell * g->csize;
     if (g->aux_mask && need_src && !plan.empty()) {
         // the aux members' Fourier coefficients for every step of this call
         using C = typename StepArgs<R>::C;
@@ -864,7 +865,7 @@ void drop_graph(pstd_grid* g)
 
 // nsteps leapfrog steps from the grid's current state.  dft = false leaves the running DFT
 // (device sums and host incident phasors) untouched; a non-null `save` receives, in stream
-// order, the state after each step: save + (s + 1) * ncell for step s (batch 1).
+// order, the state after each step: save + (s + 1) * batch * ncell for step s.
 //
 // A run that repeats the previous run's key (first step, count, level parity, table pointers
 // and configuration version: everything the kernel arguments hold) is captured once into a
@@ -1370,46 +1371,56 @@ pstd_status run_transform_adjoint(pstd_grid* g, int b, int f, const double* pts,
     return PSTD_OK;
 }
 
-// dL/dV on the box [lo, hi) by the discrete adjoint of an nsteps run from rest (batch 1),
-// given gph (device, nfreq blocks in the phasor layout) = dL/d(scaled phasors).  The forward
-// run is repeated with checkpoints of (psi^{n-1}, psi^n) every K steps; each segment is then
-// recomputed, and the adjoint levels nu are stepped backward with the forward kernels.
+// dL/dV on the box [lo, hi) by the discrete adjoint of an nsteps run from rest, given gph
+// (device) = dL/d(scaled phasors): for each member in order, one block per frequency of its
+// window, each in the phasor layout.  The members share V, so the gradient sums their
+// contributions.  The forward run is repeated with checkpoints of (psi^{n-1}, psi^n) of every
+// member every K steps; each segment is then recomputed, and the adjoint levels nu of every
+// member are stepped backward together with the forward kernels.
 template <typename R>
 pstd_status run_adjoint(pstd_grid* g, long nsteps, const double2* gph, const int lo[3], const int hi[3], long K, double* grad_out)
 {
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
-    const MemberHost& m = g->mem[0];
-    const size_t sbytes = (size_t)g->ncell * g->csize;
-    const int nf = m.nfreq;
-    // incident phasors at r_O over the window (Eq. incpsiphasor): S_f
-    std::vector<cd> S(nf, cd(0, 0));
-    for (long long n = m.first; n < m.first + m.len; ++n) {
-        const double t = n * g->desc.dt;
-        const cd inc = incident_at_origin(m, t, g->desc.hbar, g->desc.mass);
-        for (int f = 0; f < nf; ++f) S[f] += inc * std::exp(cd(0.0, m.omega[f] * t));
-    }
-    for (int f = 0; f < nf; ++f)
-        if (std::abs(S[f]) == 0.0) return fail(g, PSTD_ESTATE, "incident phasor at r_O is zero");
-    // injection volumes J_f = (1 / S_f) E^T conj(g_f)
-    pstd_status st = ensure(g, &g->adj_J, g->adj_J_cap, (size_t)nf * sbytes);
-    if (st != PSTD_OK) return st;
-    for (int f = 0; f < nf; ++f) {
-        InjectionArgs<R> ia;
-        std::memset(&ia, 0, sizeof(ia));
-        ia.g = gph + (size_t)f * g->acc_freq_stride;
-        for (int i = 0; i < 6; ++i) { ia.face_off[i] = g->face_off[i]; ia.face_size[i] = g->face_size[i]; }
-        for (int ax = 0; ax < 3; ++ax) {
-            ia.dw[ax] = static_cast<const C*>(g->dw[ax]);
-            ia.h[ax][0] = g->desc.huygens_lo[ax];
-            ia.h[ax][1] = g->desc.huygens_hi[ax];
-            ia.n[ax] = g->desc.n[ax];
+    const int B = g->batch;
+    const size_t mbytes = (size_t)g->ncell * g->csize;   // one member's state
+    const size_t sbytes = (size_t)B * mbytes;             // every member's state
+    // incident phasors at r_O over each member's window (Eq. incpsiphasor): S[b][f]; blk[b]:
+    // index of member b's first block in gph and in the injection volumes
+    std::vector<std::vector<cd>> S(B);
+    std::vector<int> blk(B + 1, 0);
+    for (int b = 0; b < B; ++b) {
+        const MemberHost& m = g->mem[b];
+        S[b].assign(m.nfreq, cd(0, 0));
+        for (long long n = m.first; n < m.first + m.len; ++n) {
+            const double t = n * g->desc.dt;
+            const cd inc = incident_at_origin(m, t, g->desc.hbar, g->desc.mass);
+            for (int f = 0; f < m.nfreq; ++f) S[b][f] += inc * std::exp(cd(0.0, m.omega[f] * t));
         }
-        ia.ncell = g->ncell;
-        const cd sc = 1.0 / S[f];
-        ia.scale = make_double2(sc.real(), sc.imag());
-        ia.J = reinterpret_cast<C*>(static_cast<char*>(g->adj_J) + (size_t)f * sbytes);
-        CK(g, launch_injection<R>(ia, g->stream));
+        for (int f = 0; f < m.nfreq; ++f)
+            if (std::abs(S[b][f]) == 0.0) return fail(g, PSTD_ESTATE, "incident phasor at r_O is zero");
+        blk[b + 1] = blk[b] + m.nfreq;
     }
+    // injection volumes J_bf = (1 / S_bf) E^T conj(g_bf), one member's size each
+    pstd_status st = ensure(g, &g->adj_J, g->adj_J_cap, (size_t)blk[B] * mbytes);
+    if (st != PSTD_OK) return st;
+    for (int b = 0; b < B; ++b)
+        for (int f = 0; f < g->mem[b].nfreq; ++f) {
+            InjectionArgs<R> ia;
+            std::memset(&ia, 0, sizeof(ia));
+            ia.g = gph + (size_t)(blk[b] + f) * g->acc_freq_stride;
+            for (int i = 0; i < 6; ++i) { ia.face_off[i] = g->face_off[i]; ia.face_size[i] = g->face_size[i]; }
+            for (int ax = 0; ax < 3; ++ax) {
+                ia.dw[ax] = static_cast<const C*>(g->dw[ax]);
+                ia.h[ax][0] = g->desc.huygens_lo[ax];
+                ia.h[ax][1] = g->desc.huygens_hi[ax];
+                ia.n[ax] = g->desc.n[ax];
+            }
+            ia.ncell = g->ncell;
+            const cd sc = 1.0 / S[b][f];
+            ia.scale = make_double2(sc.real(), sc.imag());
+            ia.J = reinterpret_cast<C*>(static_cast<char*>(g->adj_J) + (size_t)(blk[b] + f) * mbytes);
+            CK(g, launch_injection<R>(ia, g->stream));
+        }
     // buffers
     if (K <= 0) K = std::max(1L, (long)std::ceil(std::sqrt((double)nsteps)));
     const long nseg = (nsteps + K - 1) / K;
@@ -1421,8 +1432,9 @@ pstd_status run_adjoint(pstd_grid* g, long nsteps, const double2* gph, const int
     st = ensure(g, &g->adj_grad, g->adj_grad_cap, (size_t)box * sizeof(double));
     if (st != PSTD_OK) return st;
     if (!g->adj_zero) {
-        CK(g, dalloc(&g->adj_zero, 16));
-        CK(g, cudaMemsetAsync(g->adj_zero, 0, 16, g->stream));
+        // zero incident time factors of every member for the adjoint steps
+        CK(g, dalloc(&g->adj_zero, sizeof(double2) * PSTD_MAX_BATCH));
+        CK(g, cudaMemsetAsync(g->adj_zero, 0, sizeof(double2) * PSTD_MAX_BATCH, g->stream));
     }
     char* seg = static_cast<char*>(g->adj_seg);
     // checkpoints: those pstd_step recorded for this run if they cover it, else a forward run
@@ -1478,23 +1490,33 @@ pstd_status run_adjoint(pstd_grid* g, long nsteps, const double2* gph, const int
                 ga.lo[ax] = lo[ax];
                 ga.hi[ax] = hi[ax];
             }
-            const cd sf = envelope_at(m, t) * std::exp(cd(0.0, -m.w0 * t));
-            ga.s = make_c<C>(R(sf.real()), R(sf.imag()));
+            for (int b = 0; b < B; ++b) {
+                const MemberHost& m = g->mem[b];
+                const cd sf = envelope_at(m, t) * std::exp(cd(0.0, -m.w0 * t));
+                ga.s[b] = make_c<C>(R(sf.real()), R(sf.imag()));
+            }
             ga.with_inc = exact ? 1 : 0;
+            ga.batch = B;
             ga.nx = g->desc.n[0];
             ga.ny = g->desc.n[1];
+            ga.nz = g->desc.n[2];
+            ga.ncell = g->ncell;
             ga.c2 = 2.0 * g->desc.dt / g->desc.hbar;
             ga.grad = g->adj_grad;
             CK(g, launch_grad<R>(ga, g->stream));
-            // observation term on the DFT-window steps: nu^{n+2} += sum_f e^{i w_f t_n} J_f
-            if (nf > 0 && n >= m.first && n < m.first + m.len)
-                for (int f = 0; f < nf; ++f) {
+            // observation term on each member's DFT-window steps: nu_b^{n+2} += sum_f e^{i w_f t_n} J_bf
+            for (int b = 0; b < B; ++b) {
+                const MemberHost& m = g->mem[b];
+                if (n < m.first || n >= m.first + m.len) continue;
+                for (int f = 0; f < m.nfreq; ++f) {
                     const cd e = std::exp(cd(0.0, m.omega[f] * t));
-                    CK(g, launch_inject<R>(nu[nc ^ 1], reinterpret_cast<const C*>(static_cast<char*>(g->adj_J) + (size_t)f * sbytes),
+                    CK(g, launch_inject<R>(nu[nc ^ 1] + (size_t)b * g->ncell,
+                                           reinterpret_cast<const C*>(static_cast<char*>(g->adj_J) + (size_t)(blk[b] + f) * mbytes),
                                            make_c<C>(R(e.real()), R(e.imag())), g->ncell, g->stream));
                 }
+            }
             // nu^n = Gamma [nu^{n+2} - (2 i dt / hbar)(eta hbar^2/2m K + V) nu^{n+1}]: the forward
-            // step with the EXACT V-term and no incident wave
+            // step of every member with the EXACT V-term and no incident wave
             StepArgs<R> a = step_args<R>(g);
             a.cur = nu[nc];
             a.prev = nu[nc ^ 1];
@@ -1502,7 +1524,11 @@ pstd_status run_adjoint(pstd_grid* g, long nsteps, const double2* gph, const int
             a.tfac = static_cast<const C*>(g->adj_zero);
             a.tfac_base = 0;
             a.step = 0;
-            a.batch = 1;
+            a.batch = B;
+            // the tensor-copy line feeds read through maps of the grid's own level buffers, not
+            // of nu: the adjoint levels take the register-fed forms
+            a.tma_z = 0;
+            if (a.pipe_y == PSTD_LINE_TMA) a.pipe_y = PSTD_LINE_PLAIN;
             st = enqueue_step<R>(g, a, 0, nullptr, nullptr, nullptr, need_src);
             if (st != PSTD_OK) return st;
             nc ^= 1;
@@ -2500,17 +2526,22 @@ pstd_status pstd_adjoint_gradient(pstd_grid* g, long nsteps, const void* dl_dpha
 {
     if (!g || !dl_dphasors || !box_lo || !box_hi || !dl_dv) return fail(g, PSTD_EINVAL, "null argument");
     if (mem != PSTD_MEM_HOST && mem != PSTD_MEM_DEVICE) return fail(g, PSTD_EINVAL, "mem");
-    if (g->batch != 1) return fail(g, PSTD_EINVAL, "the adjoint runs on grids with batch 1");
+    if (g->spinor) return fail(g, PSTD_EINVAL, "the adjoint runs on scalar grids (no spinor coupling)");
     if (nsteps <= 0 || checkpoint_interval < 0) return fail(g, PSTD_EINVAL, "nsteps / checkpoint_interval");
     DeviceGuard dg(g->dev);
-    const MemberHost& m = g->mem[0];
-    if (!m.has_inc) return fail(g, PSTD_ESTATE, "pstd_set_incidence first");
-    if (m.packet || m.aux) return fail(g, PSTD_EINVAL, "the adjoint supports the CW incidence");
-    if (m.nfreq < 1 || m.len < 1) return fail(g, PSTD_ESTATE, "pstd_huygens_dft first (the loss is a function of the phasors)");
-    if (m.first + m.len > nsteps) return fail(g, PSTD_EINVAL, "the DFT window must end within nsteps");
+    size_t blocks = 0;
+    for (int b = 0; b < g->batch; ++b) {
+        const MemberHost& m = g->mem[b];
+        if (!m.has_inc) return fail(g, PSTD_ESTATE, "pstd_set_incidence first (every member)");
+        if (m.packet || m.aux) return fail(g, PSTD_EINVAL, "the adjoint supports the CW incidence");
+        if (m.nfreq < 1 || m.len < 1)
+            return fail(g, PSTD_ESTATE, "pstd_huygens_dft first, for every member (the loss is a function of the phasors)");
+        if (m.first + m.len > nsteps) return fail(g, PSTD_EINVAL, "the DFT window must end within nsteps");
+        blocks += (size_t)m.nfreq;
+    }
     for (int a = 0; a < 3; ++a)
         if (box_lo[a] < 0 || box_hi[a] > g->desc.n[a] || box_lo[a] >= box_hi[a]) return fail(g, PSTD_EINVAL, "box");
-    const size_t count = (size_t)g->acc_freq_stride * m.nfreq;
+    const size_t count = (size_t)g->acc_freq_stride * blocks;
     pstd_status st = ensure(g, &g->adj_out, g->adj_out_cap, count * sizeof(double2));
     if (st != PSTD_OK) return st;
     CK(g, cudaMemcpyAsync(g->adj_out, dl_dphasors, count * sizeof(double2),
@@ -2534,7 +2565,6 @@ pstd_status pstd_set_checkpointing(pstd_grid* g, long interval, long max_steps)
 {
     if (!g) return fail(nullptr, PSTD_EINVAL, "null grid");
     if (interval < 0 || max_steps < 0) return fail(g, PSTD_EINVAL, "interval / max_steps");
-    if (interval > 0 && g->batch != 1) return fail(g, PSTD_EINVAL, "checkpoints are recorded on grids with batch 1");
     DeviceGuard dg(g->dev);
     ++g->config_version;      // kernel arguments change: no graph replay of earlier runs
     g->ckpt_upto = -1;
@@ -2542,7 +2572,7 @@ pstd_status pstd_set_checkpointing(pstd_grid* g, long interval, long max_steps)
         g->ckpt_record = false;
         return PSTD_OK;
     }
-    const size_t sbytes = (size_t)g->ncell * g->csize;
+    const size_t sbytes = (size_t)g->batch * g->ncell * g->csize;   // both levels of every member
     const long slots = std::max(1L, (max_steps + interval - 1) / interval);
     pstd_status st = ensure(g, &g->adj_ckpt, g->adj_ckpt_cap, (size_t)slots * 2 * sbytes);
     if (st != PSTD_OK) return st;

@@ -231,12 +231,14 @@ template <typename R> struct InjectionArgs {
 // grad[box] += c2 Im[nu (u + s phase)] over the box [lo, hi), x fastest
 template <typename R> struct GradArgs {
     using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
-    const C* nu;              // nu^{n+1}
-    const C* u;               // u^n
-    const C* phase[3];        // member 0's incident phase tables
-    C s;                      // a(t_n) e^{-i w0 t_n}
+    const C* nu;              // nu^{n+1}, every member ([member][z][y][x])
+    const C* u;               // u^n, every member
+    const C* phase[3];        // incident phase tables [member][n_axis]
+    C s[PSTD_MAX_BATCH];      // per member a(t_n) e^{-i w0 t_n}
     int with_inc;             // EXACT form: add psi_inc^n
-    int nx, ny;
+    int batch;                // members summed into the gradient (V is shared)
+    int nx, ny, nz;
+    long long ncell;          // nodes of one member
     int lo[3], hi[3];
     double c2;                // 2 dt / hbar
     double* grad;

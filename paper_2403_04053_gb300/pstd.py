@@ -369,8 +369,10 @@ class Grid:
 
     def adjoint_gradient(self, nsteps: int, dl_dphasors, box_lo, box_hi, checkpoint_interval: int = 0):
         """dL/dV on the node box [box_lo, box_hi) (x, y, z) as a [z, y, x] array
-        (pstd_adjoint_gradient).  dl_dphasors: per frequency, six plane pairs or a flat
-        array; or one flat CUDA tensor holding every frequency (then the result is a CUDA tensor)."""
+        (pstd_adjoint_gradient).  dl_dphasors: one block per (member, frequency), members in
+        order and each member's frequencies in order, each block six plane pairs or a flat
+        array; or one flat CUDA tensor holding every block (then the result is a CUDA tensor).
+        On a batch the members share V, so the gradient is the sum of their contributions."""
         lo = (c_int * 3)(*[int(v) for v in box_lo])
         hi = (c_int * 3)(*[int(v) for v in box_hi])
         shape = (int(box_hi[2]) - int(box_lo[2]), int(box_hi[1]) - int(box_lo[1]), int(box_hi[0]) - int(box_lo[0]))

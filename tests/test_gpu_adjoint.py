@@ -180,9 +180,11 @@ def test_adjoint_call_errors():
     spec = small_spec("exact")
     gph = [np.zeros(1)]
     with pstd.Grid(spec, precision=pstd.F32, batch=2) as g:
+        g.set_incidence(0, KHAT, K, 0.05)
+        g.huygens_dft(0, [E0], 5, 10)
         with pytest.raises(pstd.PstdError) as e:
-            g.adjoint_gradient(10, gph, (0, 0, 0), (4, 4, 4))
-        assert e.value.code == "EINVAL"
+            g.adjoint_gradient(20, gph, (0, 0, 0), (4, 4, 4))
+        assert e.value.code == "ESTATE"       # member 1 has no incidence
     with pstd.Grid(spec, precision=pstd.F32) as g:
         g.set_incidence(0, KHAT, K, 0.05)
         with pytest.raises(pstd.PstdError) as e:
@@ -288,3 +290,90 @@ def test_full_size_adjoint_against_finite_differences():
     fd, ad = np.array(fd), np.array(ad)
     assert np.max(np.abs(fd - ad)) < 1e-6 * np.abs(grad64).max()
     assert rel(ad, fd) < 1e-5
+
+
+# two incidences against one V, each along its own direction (the same k: the mask's rate
+# is set by member 0's energy, so members of other energies would not match one-member runs)
+MEMBERS = ((KHAT, K), ((-0.6, 0.0, 0.8), K))
+
+
+def batched_forward(spec, V, prec):
+    g = pstd.Grid(spec, precision=prec, batch=len(MEMBERS))
+    g.set_potential(V)
+    for b, (khat, k) in enumerate(MEMBERS):
+        g.set_incidence(b, khat, k, 0.05)
+        g.huygens_dft(b, [0.5 * k * k], *WIN)
+    return g
+
+
+def member_blocks(g):
+    """dL/d(scaled phasors) of every member for L = sum_b sum_p (|Psi_bp| - target_p)^2."""
+    blocks, L = [], 0.0
+    for b in range(len(MEMBERS)):
+        psi = g.transform_to_points(b, 0, PTS)
+        Lb, gpts = ao.magnitude_misfit(psi, TARGET)
+        L += Lb
+        blocks.append(g.transform_adjoint(b, 0, PTS, gpts))
+    return L, blocks
+
+
+@pytest.mark.parametrize("prec,tol", [(pstd.F64, 1e-9), (pstd.F32, 2e-3)])
+def test_batched_adjoint_gradient_is_the_sum_over_members(prec, tol):
+    # The members share V and the loss adds their misfits, so dL/dV is the sum of each
+    # member's discrete-adjoint gradient; the oracle computes each member on its own.
+    spec = small_spec("exact")
+    V = core_V(spec, 7)
+    lo, hi = box_of(spec, "exact")
+    L_ref, grad_ref = 0.0, 0.0
+    for khat, k in MEMBERS:
+        Lb, gb, _ = ao.fresnel_loss_and_gradient(spec, V, khat, k, 0.05, WIN, NSTEPS, PTS, TARGET)
+        L_ref, grad_ref = L_ref + Lb, grad_ref + gb
+    with batched_forward(spec, V, prec) as g:
+        g.step(NSTEPS)
+        L, blocks = member_blocks(g)
+        grad = g.adjoint_gradient(NSTEPS, blocks, lo, hi)
+        assert g.get_step() == 0                   # left at rest
+    assert abs(L - L_ref) < (1e-9 if prec == pstd.F64 else 1e-3) * L_ref
+    assert rel(grad, sub(grad_ref, lo, hi)) < tol
+
+
+def test_batched_adjoint_with_recorded_checkpoints():
+    # checkpoints of both members recorded by pstd_step give the gradient of the adjoint's
+    # own forward run
+    spec = small_spec("exact")
+    V = core_V(spec, 8)
+    lo, hi = box_of(spec, "exact")
+    with batched_forward(spec, V, pstd.F64) as g:
+        g.step(NSTEPS)
+        _, blocks = member_blocks(g)
+        own = g.adjoint_gradient(NSTEPS, blocks, lo, hi, 9)
+    with batched_forward(spec, V, pstd.F64) as g:
+        g.set_checkpointing(9, NSTEPS)
+        g.reset()
+        g.step(NSTEPS)
+        _, blocks = member_blocks(g)
+        recorded = g.adjoint_gradient(NSTEPS, blocks, lo, hi, 9)
+    assert rel(recorded, own) < 1e-12
+
+
+def test_adjoint_with_tensor_copy_line_passes():
+    # FP32 128-point y and z lines can be fed by tensor copies; their maps cover the grid's
+    # own level buffers, so the adjoint levels must take the register-fed passes: the
+    # gradient is the same whichever feed the forward run used
+    spec = inputs.GridSpec(n=(16, 128, 128), d=(0.25, 0.25, 0.25), dt=0.004, abc_cells=(2, 8, 8), tfsf_lo=(5, 52, 52),
+                           tfsf_hi=(11, 76, 76), taper_cells=2, huygens_lo=(3, 48, 48), huygens_hi=(13, 80, 80))
+    V = core_V(spec, 3)
+    lo, hi = box_of(spec, "paper")              # the core box
+    grads = []
+    for zmode in (pstd.LINE_PLAIN, pstd.LINE_TMA):
+        with pstd.Grid(spec, precision=pstd.F32) as g:
+            g.set_variants(pstd.XY_SEPARATE, zmode, zmode)
+            g.set_potential(V)
+            g.set_incidence(0, KHAT, K, 0.05)
+            g.huygens_dft(0, [E0], *WIN)
+            g.step(NSTEPS)
+            psi = g.transform_to_points(0, 0, PTS)
+            _, gpts = ao.magnitude_misfit(psi, TARGET)
+            grads.append(g.adjoint_gradient(NSTEPS, [g.transform_adjoint(0, 0, PTS, gpts)], lo, hi))
+    assert np.abs(grads[0]).max() > 0
+    assert rel(grads[1], grads[0]) < 1e-5
