@@ -263,8 +263,21 @@ template <typename R> cudaError_t launch_transform(const TransformArgs<R>& a, in
 // ---------------------------------------------------------------------------------
 // far field from the plane spectra
 // ---------------------------------------------------------------------------------
-constexpr int kFarDirs = 32;       // directions per CTA (one per lane)
-constexpr int kFarWarps = 8;       // warps split the j' columns in chunks of 4
+constexpr int kFarWarps = 8;       // warps of a far-field CTA; warp w takes far_dw() directions
+// directions per warp: each spectrum value read from L1 serves far_dw() directions (8 in FP32;
+// 4 in FP64, whose [i'][direction] factor table must fit shared memory at 384-point planes)
+template <typename R> __host__ __device__ constexpr int far_dw() { return sizeof(R) == 4 ? 8 : 4; }
+template <typename R> __host__ __device__ constexpr int far_dirs() { return kFarWarps * far_dw<R>(); }
+
+template <typename C> __device__ __forceinline__ C warp_sum_c(C v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    }
+    return v;
+}
 
 // n sinc(n phi / 2) e^{i psi}, phi = 2 pi m'/N - k rhat D, psi = k rhat L / 2 + phi (lo + n/2)
 // (see the header).  psi is split as base + pi ((m' (2 lo + n)) mod 2N) / N with
@@ -291,99 +304,121 @@ __device__ __forceinline__ double reduce_2pi(double x)
     return x - 6.283185307179586476925286766559 * rint(x * 0.15915494309189533576888376337251);
 }
 
+// One CTA takes DIRS = 8 DW directions through every face (face_split 1) or one face
+// (face_split 6).  Per face, with at_{i'} of the CTA's directions in shared memory ([i'][d]),
+// warp w forms for its DW directions d and lane l the column sums
+//     T_q[d][j'] = sum_{i'} at_{i'}(d) C_q[i'][j'],   j' = j0 + l and j0 + 32 + l in the sweep
+// of 64 columns from j0, q = psi and d psi
+// (a register tile of DW directions by two columns: each spectrum value read serves DW
+// directions, each at value, a broadcast read, four columns), then each sweep adds
+// sum_j' bt_{j'}(d) T_q[d][j'] by a warp reduction to lane d's sums S_q[d].  FP32 sums over
+// one face's spectrum; faces are added in double.
 template <typename R>
-__global__ void __launch_bounds__(kFarDirs * kFarWarps) farfield_kernel(const __grid_constant__ FarArgs<R> a)
+__global__ void __launch_bounds__(kFarWarps * 32, sizeof(R) == 4 ? 2 : 1) farfield_kernel(const __grid_constant__ FarArgs<R> a)
 {
     using C = typename FarArgs<R>::C;
+    constexpr int DW = far_dw<R>(), DIRS = far_dirs<R>();
     extern __shared__ __align__(16) unsigned char smraw[];
-    C* sa = reinterpret_cast<C*>(smraw);                       // [kFarDirs][Nb + 1]
-    __shared__ C red[kFarWarps][2][kFarDirs];
+    C* sa = reinterpret_cast<C*>(smraw);                       // [Nb][DIRS]
+    __shared__ double rh[DIRS][3];                             // direction unit vectors
+    __shared__ R krd_s[2][DIRS], base_s[2][DIRS];              // face-factor arguments along b, c
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long long p = (long long)blockIdx.x * kFarDirs + lane;
-    const bool valid = p < a.M;
-    const long long pc = valid ? p : 0;
-    double st, ct, sp, cp;
-    sincos(a.theta[pc], &st, &ct);
-    sincos(a.phi[pc], &sp, &cp);
-    const double rh[3] = {st * cp, st * sp, ct};
+    const long long p0 = (long long)blockIdx.x * DIRS;
     const double k = a.k;
-    double tx = 0.0, ty = 0.0;
+    if (threadIdx.x < DIRS) {
+        const long long p = p0 + threadIdx.x < a.M ? p0 + threadIdx.x : 0;
+        double st, ct, sp, cp;
+        sincos(a.theta[p], &st, &ct);
+        sincos(a.phi[p], &sp, &cp);
+        rh[threadIdx.x][0] = st * cp;
+        rh[threadIdx.x][1] = st * sp;
+        rh[threadIdx.x][2] = ct;
+    }
+    double tx = 0.0, ty = 0.0;                                 // lane dd < DW: direction DW w + dd
     const int f_first = a.face_split == 6 ? (int)blockIdx.y : 0;
     const int f_last = a.face_split == 6 ? (int)blockIdx.y + 1 : 6;
     for (int fi = f_first; fi < f_last; ++fi) {
         const FaceGeom F = a.face[fi];
-        const int pitch = F.Nb + 1;
-        const double rb = rh[F.b], rc = rh[F.c], ra = rh[F.axis];
-        // at_{i'} for this lane's direction
-        {
-            const R krd = R(k * rb * F.db);
-            const R base = R(reduce_2pi(k * rb * (0.5 * F.Nb * F.db - F.db * (F.lo_b + 0.5 * F.L))));
-            for (int m = w; m < F.Nb; m += kFarWarps)
-                sa[lane * pitch + m] = face_factor<R, C>(m, F.Nb, krd, base, F.lo_b, F.L);
+        __syncthreads();   // rh written; the previous face's table and arguments no longer read
+        if (threadIdx.x < DIRS) {
+            const int d = threadIdx.x;
+            const double rb = rh[d][F.b], rc = rh[d][F.c];
+            krd_s[0][d] = R(k * rb * F.db);
+            base_s[0][d] = R(reduce_2pi(k * rb * (0.5 * F.Nb * F.db - F.db * (F.lo_b + 0.5 * F.L))));
+            krd_s[1][d] = R(k * rc * F.dc);
+            base_s[1][d] = R(reduce_2pi(k * rc * (0.5 * F.Nc * F.dc - F.dc * (F.lo_c + 0.5 * F.M))));
         }
         __syncthreads();
-        const R krd_c = R(k * rc * F.dc);
-        const R base_c = R(reduce_2pi(k * rc * (0.5 * F.Nc * F.dc - F.dc * (F.lo_c + 0.5 * F.M))));
-        const C* ctp = a.ct + a.ct_off[fi];                        // [q][m][j]
+        for (int e = threadIdx.x; e < F.Nb * DIRS; e += kFarWarps * 32) {
+            const int d = e % DIRS, m = e / DIRS;
+            sa[e] = face_factor<R, C>(m, F.Nb, krd_s[0][d], base_s[0][d], F.lo_b, F.L);
+        }
+        __syncthreads();
+        const C* ctp = a.ct + a.ct_off[fi];                    // [q][m][j]
         const C* ctd = ctp + (long long)F.Nb * F.Nc;
-        C sp_tot = mk<C>(R(0), R(0)), sd_tot = mk<C>(R(0), R(0));
-        for (int j0 = 4 * w; j0 < F.Nc; j0 += 4 * kFarWarps) {
-            C ap[4], ad[4];
+        const C* arow = sa + DW * w;
+        C sp_l = mk<C>(R(0), R(0)), sd_l = mk<C>(R(0), R(0)); // lane dd: direction DW w + dd, this face
+        for (int j0 = 0; j0 < F.Nc; j0 += 64) {
+            const int ja = j0 + lane, jb = ja + 32;
+            const bool va = ja < F.Nc, vb = jb < F.Nc;
+            const int la = va ? ja : 0, lb = vb ? jb : 0;      // columns past the plane read column 0, unused
+            C tp[DW][2], td[DW][2];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) { ap[jj] = mk<C>(R(0), R(0)); ad[jj] = mk<C>(R(0), R(0)); }
-            const C* rp = ctp + j0;
-            const C* rd = ctd + j0;
-            const C* arow = sa + lane * pitch;
-#pragma unroll 4
+            for (int dd = 0; dd < DW; ++dd)
+#pragma unroll
+                for (int t = 0; t < 2; ++t) { tp[dd][t] = mk<C>(R(0), R(0)); td[dd][t] = mk<C>(R(0), R(0)); }
+#pragma unroll 1
             for (int m = 0; m < F.Nb; ++m) {
-                const C av = arow[m];
-                C cpv[4], cdv[4];
-                if constexpr (sizeof(R) == 4) {
-                    const float4 p0 = __ldg(reinterpret_cast<const float4*>(rp + (long long)m * F.Nc));
-                    const float4 p1 = __ldg(reinterpret_cast<const float4*>(rp + (long long)m * F.Nc) + 1);
-                    const float4 d0 = __ldg(reinterpret_cast<const float4*>(rd + (long long)m * F.Nc));
-                    const float4 d1 = __ldg(reinterpret_cast<const float4*>(rd + (long long)m * F.Nc) + 1);
-                    cpv[0] = mk<C>(p0.x, p0.y); cpv[1] = mk<C>(p0.z, p0.w); cpv[2] = mk<C>(p1.x, p1.y); cpv[3] = mk<C>(p1.z, p1.w);
-                    cdv[0] = mk<C>(d0.x, d0.y); cdv[1] = mk<C>(d0.z, d0.w); cdv[2] = mk<C>(d1.x, d1.y); cdv[3] = mk<C>(d1.z, d1.w);
-                } else {
+                const long long row = (long long)m * F.Nc;
+                const C cpa = __ldg(ctp + row + la), cpb = __ldg(ctp + row + lb);
+                const C cda = __ldg(ctd + row + la), cdb = __ldg(ctd + row + lb);
 #pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) { cpv[jj] = __ldg(rp + (long long)m * F.Nc + jj); cdv[jj] = __ldg(rd + (long long)m * F.Nc + jj); }
-                }
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    ap[jj].x += av.x * cpv[jj].x - av.y * cpv[jj].y;
-                    ap[jj].y += av.x * cpv[jj].y + av.y * cpv[jj].x;
-                    ad[jj].x += av.x * cdv[jj].x - av.y * cdv[jj].y;
-                    ad[jj].y += av.x * cdv[jj].y + av.y * cdv[jj].x;
+                for (int dd = 0; dd < DW; ++dd) {
+                    const C av = arow[m * DIRS + dd];
+                    tp[dd][0].x += av.x * cpa.x - av.y * cpa.y;
+                    tp[dd][0].y += av.x * cpa.y + av.y * cpa.x;
+                    tp[dd][1].x += av.x * cpb.x - av.y * cpb.y;
+                    tp[dd][1].y += av.x * cpb.y + av.y * cpb.x;
+                    td[dd][0].x += av.x * cda.x - av.y * cda.y;
+                    td[dd][0].y += av.x * cda.y + av.y * cda.x;
+                    td[dd][1].x += av.x * cdb.x - av.y * cdb.y;
+                    td[dd][1].y += av.x * cdb.y + av.y * cdb.x;
                 }
             }
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const C bt = face_factor<R, C>(j0 + jj, F.Nc, krd_c, base_c, F.lo_c, F.M);
-                sp_tot = cadd(sp_tot, cmul(bt, ap[jj]));
-                sd_tot = cadd(sd_tot, cmul(bt, ad[jj]));
+            for (int dd = 0; dd < DW; ++dd) {
+                const int d = DW * w + dd;
+                C vp = mk<C>(R(0), R(0)), vd = mk<C>(R(0), R(0));
+                if (va) {
+                    const C bt = face_factor<R, C>(ja, F.Nc, krd_s[1][d], base_s[1][d], F.lo_c, F.M);
+                    vp = cmul(bt, tp[dd][0]);
+                    vd = cmul(bt, td[dd][0]);
+                }
+                if (vb) {
+                    const C bt = face_factor<R, C>(jb, F.Nc, krd_s[1][d], base_s[1][d], F.lo_c, F.M);
+                    vp = cadd(vp, cmul(bt, tp[dd][1]));
+                    vd = cadd(vd, cmul(bt, td[dd][1]));
+                }
+                vp = warp_sum_c(vp);
+                vd = warp_sum_c(vd);
+                if (lane == dd) { sp_l = cadd(sp_l, vp); sd_l = cadd(sd_l, vd); }
             }
         }
-        red[w][0][lane] = sp_tot;
-        red[w][1][lane] = sd_tot;
-        __syncthreads();
-        if (w == 0) {
-            double spx = 0, spy = 0, sdx = 0, sdy = 0;
-            for (int t = 0; t < kFarWarps; ++t) {
-                spx += double(red[t][0][lane].x); spy += double(red[t][0][lane].y);
-                sdx += double(red[t][1][lane].x); sdy += double(red[t][1][lane].y);
-            }
+        if (lane < DW) {
+            const double ra = rh[DW * w + lane][F.axis];
             // -sigma D_b D_c / (4 pi) e^{-ik rhat_a a_plane} (S_d + i k rhat_a S_psi)
             double s0, c0;
             sincos(-k * ra * F.plane, &s0, &c0);
-            const double bx = sdx - k * ra * spy, by = sdy + k * ra * spx;
+            const double spx = double(sp_l.x), spy = double(sp_l.y);
+            const double bx = double(sd_l.x) - k * ra * spy, by = double(sd_l.y) + k * ra * spx;
             const double pref = -F.sigma * F.db * F.dc / (4.0 * 3.14159265358979323846);
             tx += pref * (c0 * bx - s0 * by);
             ty += pref * (c0 * by + s0 * bx);
         }
-        __syncthreads();
     }
-    if (w == 0 && valid) a.partial[(long long)(a.face_split == 6 ? blockIdx.y : 0) * a.M + p] = make_double2(tx, ty);
+    const long long p = p0 + DW * w + lane;
+    if (lane < DW && p < a.M)
+        a.partial[(long long)(a.face_split == 6 ? blockIdx.y : 0) * a.M + p] = make_double2(tx, ty);
 }
 
 template <typename R> cudaError_t launch_farfield(const FarArgs<R>& a, cudaStream_t s)
@@ -391,11 +426,11 @@ template <typename R> cudaError_t launch_farfield(const FarArgs<R>& a, cudaStrea
     using C = typename FarArgs<R>::C;
     int nbmax = 0;
     for (int f = 0; f < 6; ++f) nbmax = max(nbmax, a.face[f].Nb);
-    const size_t sm = sizeof(C) * kFarDirs * (size_t)(nbmax + 1);
+    const size_t sm = sizeof(C) * far_dirs<R>() * (size_t)nbmax;
     cudaError_t e = cudaFuncSetAttribute(farfield_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((a.M + kFarDirs - 1) / kFarDirs), a.face_split);
-    farfield_kernel<R><<<grid, kFarDirs * kFarWarps, sm, s>>>(a);
+    dim3 grid((unsigned)((a.M + far_dirs<R>() - 1) / far_dirs<R>()), a.face_split);
+    farfield_kernel<R><<<grid, kFarWarps * 32, sm, s>>>(a);
     return cudaGetLastError();
 }
 
