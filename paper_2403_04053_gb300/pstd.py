@@ -508,9 +508,11 @@ def fresnel_field(V, grid: Grid, points, nsteps: int, box_lo, box_hi, checkpoint
     """Psi at `points` after an nsteps run from rest, differentiable with respect to V.
 
     V: real CUDA tensor [z, y, x] on the grid (the whole potential); points: CUDA tensor
-    M x 3 (float64).  The grid must hold member 0's incidence and DFT window (batch 1).
-    Backward is the discrete adjoint (pstd_transform_adjoint, pstd_adjoint_gradient); the
-    gradient is computed on the node box [box_lo, box_hi) and is zero outside it."""
+    M x 3 (float64).  Every member of the grid needs its incidence and DFT window; the
+    result is Psi of member 0 ([M]) on a one-member grid and of every member ([batch, M])
+    otherwise, at the first frequency.  Backward is the discrete adjoint
+    (pstd_transform_adjoint of each member, pstd_adjoint_gradient); the gradient is computed
+    on the node box [box_lo, box_hi) and is zero outside it."""
     return _FresnelField.apply(V, grid, points, int(nsteps), tuple(box_lo), tuple(box_hi), int(checkpoint_interval))
 
 
@@ -526,7 +528,10 @@ def _make_fresnel_function():
             grid.set_checkpointing(K, nsteps)
             grid.reset()
             grid.step(nsteps)
-            psi = grid.transform_to_points(0, 0, points)
+            if grid.batch == 1:
+                psi = grid.transform_to_points(0, 0, points)
+            else:
+                psi = torch.stack([grid.transform_to_points(b, 0, points) for b in range(grid.batch)])
             ctx.grid, ctx.points, ctx.nsteps = grid, points, nsteps
             ctx.box = (box_lo, box_hi, checkpoint_interval)
             ctx.vshape, ctx.vdtype = V.shape, V.dtype
@@ -536,7 +541,11 @@ def _make_fresnel_function():
         def backward(ctx, grad_psi):
             grid = ctx.grid
             lo, hi, K = ctx.box
-            g_ph = grid.transform_adjoint(0, 0, ctx.points, grad_psi)
+            if grid.batch == 1:
+                g_ph = grid.transform_adjoint(0, 0, ctx.points, grad_psi)
+            else:
+                g_ph = torch.cat([grid.transform_adjoint(b, 0, ctx.points, grad_psi[b].contiguous())
+                                  for b in range(grid.batch)])
             gbox = grid.adjoint_gradient(ctx.nsteps, g_ph, lo, hi, K)
             gV = torch.zeros(ctx.vshape, dtype=ctx.vdtype, device=gbox.device)
             gV[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = gbox.to(ctx.vdtype)

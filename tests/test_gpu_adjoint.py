@@ -377,3 +377,29 @@ def test_adjoint_with_tensor_copy_line_passes():
             grads.append(g.adjoint_gradient(NSTEPS, [g.transform_adjoint(0, 0, PTS, gpts)], lo, hi))
     assert np.abs(grads[0]).max() > 0
     assert rel(grads[1], grads[0]) < 1e-5
+
+
+def test_autograd_function_on_a_batch():
+    # Psi of both members from one run; the loss over both members backpropagates through
+    # the batched adjoint to the sum of the oracle's one-member gradients
+    torch = pytest.importorskip("torch")
+    spec = small_spec("exact")
+    V = core_V(spec, 7)
+    lo, hi = box_of(spec, "exact")
+    with pstd.Grid(spec, precision=pstd.F64, batch=len(MEMBERS)) as g:
+        for b, (khat, k) in enumerate(MEMBERS):
+            g.set_incidence(b, khat, k, 0.05)
+            g.huygens_dft(b, [0.5 * k * k], *WIN)
+        Vt = torch.tensor(V, device="cuda", requires_grad=True)
+        pts = torch.tensor(PTS, device="cuda")
+        psi = pstd.fresnel_field(Vt, g, pts, NSTEPS, lo, hi)
+        assert tuple(psi.shape) == (len(MEMBERS), len(PTS))
+        loss = ((psi.abs() - torch.tensor(TARGET, device="cuda")) ** 2).sum()
+        loss.backward()
+        gV = Vt.grad.cpu().numpy()
+    L_ref, grad_ref = 0.0, 0.0
+    for khat, k in MEMBERS:
+        Lb, gb, _ = ao.fresnel_loss_and_gradient(spec, V, khat, k, 0.05, WIN, NSTEPS, PTS, TARGET)
+        L_ref, grad_ref = L_ref + Lb, grad_ref + gb
+    assert abs(float(loss.detach()) - L_ref) < 1e-9 * L_ref
+    assert rel(sub(gV, lo, hi), sub(grad_ref, lo, hi)) < 1e-9
