@@ -1176,11 +1176,11 @@ pstd_status run_far(pstd_grid* g, int b, int f, const double* theta, const doubl
     a.phi = phi;
     a.M = M;
     a.k = wavenumber_of(g, b, f);
-    // few directions: one CTA per (direction block, face) for parallelism; many: faces summed in-CTA
-    const long long blocks = (M + 31) / 32;
-    int nsm = 152;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, g->dev);
-    a.face_split = (blocks < 2LL * nsm && 6LL * M <= scratch_elems) ? 6 : 1;
+    // one CTA per (direction block, face) where the scratch holds six partial sums a direction:
+    // six times the CTAs of the faces-summed form, so the last wave of the grid is a small
+    // share of it (64980 directions: 20.1 waves of two CTAs an SM instead of 3.3); otherwise
+    // each CTA sums all six faces
+    a.face_split = 6LL * M <= scratch_elems ? 6 : 1;
     if ((long long)a.face_split * M > scratch_elems) return fail(g, PSTD_EINVAL, "directions exceed the scratch capacity");
     a.partial = scratch;
     {
